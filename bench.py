@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Throughput of the HPClust hot path on GB300: point-centroid distances/s.
+
+One step = one HPClust round on the benchmark workload (sample draw,
+K-means++ reseeding of degenerate centroids, Lloyd to the Section 6.5 stop
+rule, incumbent test) followed by the full-data objective of the incumbent
+(Eq. 1 over all n rows).  Distances counted per step: (Lloyd assignments) x
+s x k + n x k.  Default workload: "fp32" (n = 10^7 points in 16 dims, 25
+Gaussians, k = 25, one worker, s = 10^5).
+
+Prints one JSON line (rank 0).  Arms:
+  --impl mine       the CUDA library (default)
+  --impl reference  the CPU oracle as the reference arm (host cores)
+Multi-GPU (torchrun): independent replicas per rank (weak scaling), barrier
+and max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+from paper_2311_04517_gb300 import synth  # noqa: E402
+
+METRIC = "point-centroid distances/s"
+UNIT = "distances/s"
+FALLBACK_HBM = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    p.add_argument("--workload", default="fp32")
+    p.add_argument("--strategy", choices=["competitive", "cooperative"], default="competitive")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=None)
+    return p.parse_args()
+
+
+def peaks():
+    f = ROOT / "MEASURED_PEAKS.json"
+    if f.exists():
+        j = json.loads(f.read_text())
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted((ROOT / "paper_2311_04517_gb300" / "csrc").glob("*")):
+        h.update(p.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    f = ROOT / "profiles" / f"{kernel}_{workload}.md"
+    if not f.exists():
+        return None
+    txt = f.read_text()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    hs = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    if not m or not hs or hs.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ---------------------------------------------------------------------------
+# clock sampling (NVML through ctypes; nvidia-smi is too coarse for short runs)
+# ---------------------------------------------------------------------------
+_REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+            0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+            0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, index: int, period_s: float = 0.002):
+        self.samples = []
+        self.period = period_s
+        self.ok = False
+        self.max_mhz = None
+        try:
+            self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nv.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if self.nv.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.h)) != 0:
+                return
+            m = ctypes.c_uint()
+            if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(m)) == 0:
+                self.max_mhz = m.value
+            self.ok = True
+        except OSError:
+            pass
+
+    def _read(self):
+        mhz = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz))
+        fn = getattr(self.nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(self.h, ctypes.byref(rs))
+        return time.perf_counter(), mhz.value, rs.value
+
+    def _loop(self):
+        while not self._stop.is_set():
+            self.samples.append(self._read())
+            time.sleep(self.period)
+
+    def start(self):
+        if not self.ok:
+            return
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._loop, daemon=True)
+        self._t.start()
+
+    def stop(self):
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+
+    def summary(self, t0: float, t1: float):
+        if not self.ok:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvml unavailable"]}
+        win = [s for s in self.samples if t0 <= s[0] <= t1]
+        if not win:  # timed region shorter than the sampling period
+            win = sorted(self.samples, key=lambda s: min(abs(s[0] - t0), abs(s[0] - t1)))[:3]
+        reasons = set()
+        for _, _, r in win:
+            for bit, name in _REASONS.items():
+                if r & bit and name != "gpu_idle":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(s[1] for s in win), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(win)}
+
+
+# ---------------------------------------------------------------------------
+def dist_count(iters, s, k, n, k_best):
+    return float(sum((int(i) + 1) * int(sw) * int(kw) for i, sw, kw in zip(iters, s, k))) + n * k_best
+
+
+def workload_config(wl, strategy, args):
+    return {"workload": f"{wl.name}: {wl.notes}", "n": wl.n, "d": wl.d, "k": list(wl.k),
+            "workers": wl.W, "s": list(wl.s), "strategy": strategy,
+            "step": "one HPClust round + full-data objective of the incumbent",
+            "l2": "inputs larger than L2 (X is %.0f MB)" % (wl.n * wl.d * 4 / 1e6),
+            "lloyd_max_iter": 300, "lloyd_rel_tol": 1e-4, "kmeanspp_candidates": 3}
+
+
+def load_data(wl, device, seed):
+    # up to 2e8 floats on the CPU (same data in both arms); larger on the GPU
+    if wl.n * wl.d <= 200_000_000:
+        X = synth.make_data(wl, "cpu", seed)
+        return X.to(device) if device != "cpu" else X
+    return synth.make_data(wl, device, seed)
+
+
+def cpu_oracle_rate(X_np, wl, ws, strategy, seed, budget_s=12.0, max_rounds=5):
+    import oracle as orc
+    orc.build()
+    st = orc.RoundState(wl.d, ws.s, ws.k, ws.group)
+    strat = orc.COOPERATIVE if strategy == "cooperative" else orc.COMPETITIVE
+    dist = 0.0
+    t0 = time.perf_counter()
+    rounds = 0
+    while rounds < max_rounds:
+        res = orc.round_(X_np, st, strat, seed, rounds)
+        b = int(np.argmin(st.fhat))
+        C, deg = st.centroids(b)
+        orc.objective(X_np, C, deg)
+        dist += dist_count(res["iters"], ws.s, ws.k, wl.n, int(ws.k[b]))
+        rounds += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return dist / el, el, rounds, orc.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as orc
+    orc.build()
+    wl = synth.WORKLOADS[args.workload]
+    ws = synth.worker_setup(wl)
+    X = load_data(wl, "cpu", wl.seed).numpy()
+    strat = orc.COOPERATIVE if args.strategy == "cooperative" else orc.COMPETITIVE
+    st = orc.RoundState(wl.d, ws.s, ws.k, ws.group)
+
+    def step(r):
+        res = orc.round_(X, st, strat, wl.seed, r)
+        b = int(np.argmin(st.fhat))
+        C, deg = st.centroids(b)
+        orc.objective(X, C, deg)
+        return dist_count(res["iters"], ws.s, ws.k, wl.n, int(ws.k[b]))
+
+    for r in range(args.warmup):
+        step(r)
+    dist = 0.0
+    t0 = time.perf_counter()
+    for r in range(args.warmup, args.warmup + args.steps):
+        dist += step(r)
+    el = time.perf_counter() - t0
+    v = dist / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, args.strategy, args),
+            "cpu_baseline": {"kind": "oracle", "cores": orc.num_threads(),
+                             "sample": f"{args.steps} full oracle steps (round + full-data objective)",
+                             "value": v, "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mine(args):
+    from paper_2311_04517_gb300 import hpclust as H
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist_ok = world > 1
+    if dist_ok:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    wl = synth.WORKLOADS[args.workload]
+    ws = synth.worker_setup(wl)
+    seed = wl.seed + rank            # independent replica per rank
+    X = load_data(wl, dev, seed)
+    strategy = H.HPC_COOPERATIVE if args.strategy == "cooperative" else H.HPC_COMPETITIVE
+    ctx = H.Context(local)
+    batch = H.Batch(wl.d, ws.s, ws.k, ws.group, device=dev)
+    f_sse = torch.zeros(1, dtype=torch.float64, device=dev)
+    K, Wm = args.steps, args.warmup
+    iters_log = torch.zeros((K, wl.W), dtype=torch.int32, device=dev)
+    best = 0  # single-worker workloads: the incumbent of worker 0
+
+    def step(r, log_row=None, ev=None):
+        H.hpc_round(ctx, X, batch, strategy, seed, r)
+        if log_row is not None:
+            iters_log[log_row].copy_(batch.iters, non_blocking=True)
+        C, deg = batch.centroids(best)
+        if ev is not None:
+            ev[0].record()
+        H.hpc_objective(ctx, X, C, deg, f_out=f_sse)
+        if ev is not None:
+            ev[1].record()
+
+    for r in range(Wm):
+        step(r)
+    ctx.check_status()
+    torch.cuda.synchronize()
+    if dist_ok:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.01)
+    launches0 = ctx.launch_count()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    start.record()
+    for i in range(K):
+        step(Wm + i, i, evs[i])
+    end.record()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    clocks.stop()
+    launches = ctx.launch_count() - launches0
+    st = ctx.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st}")
+    ms = start.elapsed_time(end)
+    obj_ms = [a.elapsed_time(b) for a, b in evs]
+    iters = iters_log.cpu().numpy()
+    dist_total = sum(dist_count(iters[i], ws.s, ws.k, wl.n, int(ws.k[best])) for i in range(K))
+    if dist_ok:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dd = torch.tensor([dist_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(dd)
+        dist_total = float(dd.item())
+    value = dist_total / (ms / 1e3)
+
+    # end to end: host-resident (pinned) data copied in every step, results read back
+    E = args.e2e_steps if args.e2e_steps is not None else max(3, min(K, 20))
+    X_host = X.cpu().pin_memory()
+    res_host = torch.empty(1 + wl.W, dtype=torch.float64).pin_memory()
+    C_host = torch.empty_like(batch.C, device="cpu").pin_memory()
+    e_iters = torch.zeros((E, wl.W), dtype=torch.int32, device=dev)
+    r0 = Wm + K
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(E):
+        X.copy_(X_host, non_blocking=True)
+        H.hpc_round(ctx, X, batch, strategy, seed, r0 + i)
+        e_iters[i].copy_(batch.iters, non_blocking=True)
+        C, deg = batch.centroids(best)
+        H.hpc_objective(ctx, X, C, deg, f_out=f_sse)
+        res_host[0:1].copy_(f_sse, non_blocking=True)
+        res_host[1:].copy_(batch.fhat, non_blocking=True)
+        C_host.copy_(batch.C, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1)
+    ei = e_iters.cpu().numpy()
+    e_dist = sum(dist_count(ei[i], ws.s, ws.k, wl.n, int(ws.k[best])) for i in range(E))
+    if dist_ok:
+        t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+        dd = torch.tensor([e_dist], dtype=torch.float64, device=dev)
+        dist.all_reduce(dd)
+        e_dist = float(dd.item())
+    e_value = e_dist / (e_ms / 1e3)
+
+    hbm, src = peaks()
+    obj_avg_ms = float(np.mean(obj_ms))
+    bytes_obj = float(wl.n) * wl.d * 4
+    achieved = bytes_obj / (obj_avg_ms / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(wl, args.strategy, args),
+            "roofline": {"kernel": "objective_kernel (full-data objective, Eq. 1)",
+                         "bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "peak_source": f"{src} hbm_gbs", "unit": "GB/s",
+                         "frac": achieved / hbm,
+                         "traffic": profiled_traffic("objective", wl.name),
+                         "algorithmic_bytes_per_launch": bytes_obj,
+                         "avg_launch_ms": obj_avg_ms},
+            "e2e": {"value": e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(X_host.numel() * 4),
+                    "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4)},
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(t0, t1),
+            "lloyd_iters_mean": float(iters.mean())}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, el, rounds, cores = cpu_oracle_rate(X.cpu().numpy(), wl, ws, args.strategy, seed)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{rounds} oracle rounds from all-degenerate start "
+                                          f"(each: round + full-data objective), {el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist_ok:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * hpclust.h — C ABI of the GB300 (sm_103a) HPClust hot path.
+ *
+ * HPClust (arXiv 2311.04517) clusters very tall data by letting each worker
+ * repeatedly draw a random sample S of size s from the data X, re-seed its
+ * degenerate centroids with K-means++ on S, run K-means (Lloyd) on S from its
+ * incumbent centroids, and keep the result if the sample objective improved
+ * (Section 3; Algorithms 3-5).  This library runs those steps, and the
+ * full-data objective of Eq. 1, as CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call below
+ *  - Arrays are row-major.  X is n x d float, S is s x d float, C is k x d
+ *    float.  Unless a parameter says "host", every pointer is a DEVICE
+ *    pointer owned by the caller; the library never frees or retains it.
+ *    Float arrays must be 16-byte aligned; sizes are int64 (rows) and int32
+ *    (dimensions, clusters).  Supported dimensions: 1 <= d <= 128.
+ *  - Every call is asynchronous on the stream given to hpc_create /
+ *    hpc_set_stream; outputs are valid once that stream has synchronised.
+ *    Calls on one context must not run concurrently from several host
+ *    threads (the context's scratch memory is shared).
+ *  - Return value: HPC_OK (0) or a negative hpc_status for errors found on
+ *    the host (bad arguments, allocation or launch failure).  Errors found
+ *    on the device (non-finite input, a bounded wait that ran out) are
+ *    recorded in the context's device status word and returned by
+ *    hpc_sync_status().  hpc_last_error() describes the latest error.
+ *  - Degenerate flags are one byte per centroid, 1 = degenerate (an empty
+ *    cluster, Section 3).  Degenerate centroids take no part in any
+ *    assignment; a NULL flag array means "all live" where it is an input.
+ *  - Random draws come from Philox4x64-10 (Salmon et al., SC'11): draw j of
+ *    stream (seed, worker, round, tag) is word j mod 4 of the block at
+ *    counter (j div 4, round, tag, 0) under key (seed, worker).  Tag 0 gives
+ *    the sample rows, tag 1 the K-means++ draws.  The same arguments give the
+ *    same sample and the same seeding on every run.
+ */
+#ifndef HPCLUST_H
+#define HPCLUST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hpc_ctx hpc_ctx;
+
+typedef enum hpc_status {
+  HPC_OK = 0,
+  HPC_ERR_ARG = -1,            /* invalid argument (size, alignment, NULL) */
+  HPC_ERR_NOMEM = -2,          /* device scratch allocation failed */
+  HPC_ERR_CUDA = -3,           /* a CUDA runtime call or launch failed */
+  HPC_ERR_TIMEOUT = -4,        /* a bounded device-side wait gave up */
+  HPC_ERR_NONFINITE = -5,      /* NaN or infinity in the input rows */
+  HPC_ERR_DEGENERATE_ALL = -6, /* no live centroid to assign to */
+  HPC_ERR_UNSUPPORTED = -7     /* a valid request this build cannot run */
+} hpc_status;
+
+typedef enum hpc_precision {
+  HPC_FP32 = 0, /* FP32 distances, FP64 rescoring of near ties */
+  HPC_BF16 = 1, /* reserved: BF16 tensor-core search with rescoring */
+  HPC_FP8 = 2   /* reserved: FP8 e4m3 tensor-core search with rescoring */
+} hpc_precision;
+
+typedef enum hpc_strategy {
+  HPC_COMPETITIVE = 0, /* Algorithm 3: each worker starts from its own incumbent */
+  HPC_COOPERATIVE = 1  /* Algorithm 4: from the best incumbent of its group */
+} hpc_strategy;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` that launches on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *ctx receives the
+ * handle.  Returns HPC_ERR_ARG for a NULL ctx or a bad device. */
+int hpc_create(hpc_ctx **ctx, int device, void *stream);
+
+/* Frees the context and its scratch memory (synchronises its stream first).
+ * NULL is accepted and ignored. */
+int hpc_destroy(hpc_ctx *ctx);
+
+/* Makes later calls on `ctx` launch on `stream` (a cudaStream_t). */
+int hpc_set_stream(hpc_ctx *ctx, void *stream);
+
+/* Synchronises the context's stream, then returns and clears the device
+ * status word: HPC_OK, or the first device-side error since the last call
+ * (HPC_ERR_TIMEOUT, HPC_ERR_NONFINITE, HPC_ERR_DEGENERATE_ALL). */
+int hpc_sync_status(hpc_ctx *ctx);
+
+/* Static description of the latest error on this context ("" if none). */
+const char *hpc_last_error(hpc_ctx *ctx);
+
+/* Number of kernels this context has launched so far. */
+int64_t hpc_launch_count(hpc_ctx *ctx);
+
+/* Pre-allocates at least `bytes` of device scratch so that later calls do
+ * not allocate (useful before timing or stream capture). */
+int hpc_reserve(hpc_ctx *ctx, int64_t bytes);
+
+/* ---- the hot path ------------------------------------------------------ */
+
+/* Random sample of size s from X (Section 3: a worker starts every round by
+ * drawing a random subset of s rows of the data; Algorithms 3-5, first step
+ * of the worker loop).  Reading: with replacement; sample row i is X[floor(r_i * n / 2^64)]
+ * where r_i is draw i of stream (seed, worker, round, tag 0).
+ *   X        device, n x d float (input)
+ *   S_out    device, s x d float (output)
+ *   idx_out  device, s int64 (output, nullable): the drawn row indices
+ * Errors: HPC_ERR_ARG if s < 0, d out of range, or s > 0 with n < 1. */
+int hpc_draw_sample(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
+                    uint64_t seed, uint32_t worker, uint32_t round, int64_t s,
+                    float *S_out, int64_t *idx_out);
+
+/* Greedy K-means++ seeding of the degenerate centroids (Section 3: empty
+ * clusters are re-initialised with K-means++ on the current sample; Section
+ * 6.5: each new centroid is the best of three candidates drawn by the D^2
+ * rule).  Live centroids are left untouched; degenerate slots are filled in
+ * index order.  If no centroid is live, the lowest slot first takes sample
+ * row floor(r_0 * s / 2^64) (draw 0 of tag 1).  Each further slot draws
+ * n_candidates rows with probability proportional to D(x)^2 (draws
+ * 1 + t*n_candidates + l, t = slots seeded so far) and keeps the one with the
+ * smallest potential sum_i min(D(x_i)^2, ||x_i - cand||^2).  D^2 is the
+ * float squared distance accumulated in dimension order with one fused
+ * multiply-add per dimension; the draw and the potentials use exact 64-bit
+ * fixed-point sums of those values (grid 2^-F, F = 62 - bitlen(s) - e with
+ * 2^(e-1) <= max D^2 < 2^e).  If every row already sits on a live centroid
+ * the remaining slots stay degenerate.
+ *   S                  device, s x d float (input)
+ *   C_inout            device, k x d float (in/out)
+ *   degenerate_inout   device, k bytes (in/out); NULL = all degenerate
+ * Errors: HPC_ERR_ARG for s < 1, k < 1 or n_candidates < 1;
+ * HPC_ERR_NONFINITE (device status) for non-finite rows. */
+int hpc_kmeanspp(hpc_ctx *ctx, const float *S, int64_t s, int32_t d, int32_t k,
+                 float *C_inout, uint8_t *degenerate_inout, int32_t n_candidates,
+                 uint64_t seed, uint32_t worker, uint32_t round);
+
+/* Lloyd's K-means on one sample (Algorithm 1, iterative part) with the stop
+ * rule of Section 6.5: at most max_iter centroid updates, and stop at the
+ * first assignment whose objective improved on the previous one by less
+ * than rel_tol of it (or when the objective is zero).  Each assignment takes
+ * every row to its nearest live centroid (Eq. 1; ties to the lowest index);
+ * each update sets a centroid to the mean of its members, and a centroid
+ * left without members becomes degenerate (keeps its value, excluded from
+ * later assignments of this run).  The returned centroids are the ones last
+ * assigned, so *f_out = f(C_out, S).
+ *   S                 device, s x d float (input)
+ *   C_inout           device, k x d float (in/out)
+ *   degenerate_inout  device, k bytes (in/out, NULL = all live)
+ *   labels_out        device, s int32 (output, nullable)
+ *   f_out             device, 1 double (output): the sample objective
+ *   iters_out         device, 1 int32 (output, nullable): updates performed
+ * Errors: HPC_ERR_ARG for s < 1, k < 1, max_iter outside [0, 100000];
+ * HPC_ERR_UNSUPPORTED
+ * for prec other than HPC_FP32; device status HPC_ERR_DEGENERATE_ALL if no
+ * centroid is live, HPC_ERR_NONFINITE for non-finite rows. */
+int hpc_lloyd(hpc_ctx *ctx, const float *S, int64_t s, int32_t d, int32_t k,
+              float *C_inout, uint8_t *degenerate_inout, int32_t max_iter,
+              double rel_tol, int32_t prec, int32_t *labels_out, double *f_out,
+              int32_t *iters_out);
+
+/* Full-data objective f(C, X) = sum_i min_j ||x_i - c_j||^2 (Eq. 1) over the
+ * live centroids, accumulated in double precision, with the optional final
+ * assignment Y (Section 3, last step; Algorithms 3-5, last line).  n = 0
+ * gives 0.
+ *   X           device, n x d float (input)
+ *   C           device, k x d float (input)
+ *   degenerate  device, k bytes (input, nullable = all live)
+ *   f_out       device, 1 double (output)
+ *   labels_out  device, n int32 (output, nullable)
+ * Errors: HPC_ERR_ARG, HPC_ERR_UNSUPPORTED (prec); device status
+ * HPC_ERR_DEGENERATE_ALL (n > 0 and no live centroid). */
+int hpc_objective(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
+                  const float *C, int32_t k, const uint8_t *degenerate,
+                  int32_t prec, double *f_out, int32_t *labels_out);
+
+/* Worker set of one HPClust run.  Host arrays describe the workers; device
+ * arrays hold their state between rounds. */
+typedef struct hpc_batch {
+  int32_t W;            /* number of workers */
+  const int64_t *s;     /* host [W]: sample size of each worker (>= 1) */
+  const int32_t *k;     /* host [W]: clusters of each worker (>= 1) */
+  const int32_t *group; /* host [W]: cooperative sharing group (nullable = one group) */
+  const int64_t *C_off; /* host [W]: float offset of worker w's centroids in C */
+  const int64_t *K_off; /* host [W]: byte offset of worker w's flags in degenerate */
+  float *C;             /* device: centroid pool (incumbents C_w) */
+  uint8_t *degenerate;  /* device: flag pool; all 1 before the first round */
+  double *fhat;         /* device [W]: incumbent sample objective per point; +inf at start */
+  double *f_new;        /* device [W] (nullable): this round's Lloyd objective */
+  int32_t *iters;       /* device [W] (nullable): this round's Lloyd updates */
+  uint8_t *accepted;    /* device [W] (nullable): 1 if the incumbent was replaced */
+} hpc_batch;
+
+/* One HPClust round for every worker of `batch` (one pass of the loop body
+ * of Algorithm 3 or 4).  Worker w draws S_w (hpc_draw_sample with worker w),
+ * takes as base its own incumbent (HPC_COMPETITIVE) or that of the worker
+ * with the smallest fhat in its group and with its k (HPC_COOPERATIVE;
+ * snapshot at the start of the round, lowest index on ties), re-seeds the
+ * base's degenerate centroids (hpc_kmeanspp), runs hpc_lloyd, and replaces
+ * its incumbent when f / s_w < fhat[w] (Algorithm 3's strict test, per
+ * sample point because sample sizes may differ between workers).
+ * Errors: as the calls it makes; HPC_ERR_ARG for a malformed batch. */
+int hpc_round(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
+              const hpc_batch *batch, int32_t strategy, uint64_t seed,
+              uint32_t round, int32_t max_iter, double rel_tol,
+              int32_t n_candidates, int32_t prec);
+
+/* ---- diagnostics -------------------------------------------------------- */
+
+/* Failure-detection self-test (the paper has no counterpart).  Launches a
+ * two-block cooperative kernel in which one block never reaches the grid
+ * barrier; the other block's bounded wait gives up after limit_ns
+ * nanoseconds (1e3 .. 1e9) and records HPC_ERR_TIMEOUT in the device status
+ * word, which the next hpc_sync_status() returns.  No fault, no hang: this
+ * is how every device-side wait in the library ends when a peer block never
+ * arrives (the library's own waits give up after 4 s). */
+int hpc_selftest_wait_timeout(hpc_ctx *ctx, int64_t limit_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPCLUST_H */

@@ -1,0 +1,342 @@
+// Greedy K-means++ seeding of the degenerate centroids (Section 3: empty
+// clusters are re-initialised by K-means++ on the sample; Section 6.5: three
+// candidates per new centroid) as one persistent cooperative kernel.
+//
+// Block b owns the contiguous rows [s*b/G, s*(b+1)/G) so that "first row
+// whose running weight exceeds the target" can be answered by the block that
+// owns the target.  Weights D(x)^2 are float squared distances accumulated in
+// dimension order with one fused multiply-add per dimension; the draw and
+// the candidate potentials use exact unsigned 64-bit sums on the grid 2^-F,
+// F = 62 - bitlen(s) - e (2^(e-1) <= max weight < 2^e), so every block, and
+// any reference that follows the same definition, takes the same decisions.
+// Four bounded grid barriers per seeded centroid.
+#include "common.cuh"
+#include "kernels.h"
+
+#define HPC_MAX_CAND 8
+
+namespace {
+
+struct KppArgs {
+  const float *S;
+  int64_t s;
+  int d, k;
+  float *C;
+  uint8_t *deg;
+  int L;
+  uint64_t seed;
+  uint32_t worker, round;
+  hpc_gridbar *bar;
+  int *status;
+  float *w;
+  float *dc;
+  unsigned long long *chunkQ;
+  long long *cand;
+  unsigned long long *phi;
+  unsigned *mx;
+};
+
+template <int THREADS>
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
+                                                            unsigned long long *sh) {
+  v = hpc_warp_sum_u64(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < THREADS / 32; ++i) r += sh[i];
+  return r;  // valid in thread 0
+}
+
+// Inclusive block scan; *total receives the block total (all threads).
+template <int THREADS>
+__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long v,
+                                                             unsigned long long *sh,
+                                                             unsigned long long *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  __syncthreads();
+  if (lane == 31) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int i = 0; i < THREADS / 32; ++i) {
+      const unsigned long long t = sh[i];
+      sh[i] = run;
+      run += t;
+    }
+    sh[THREADS / 32] = run;
+  }
+  __syncthreads();
+  v += sh[wid];
+  *total = sh[THREADS / 32];
+  return v;
+}
+
+template <int D, int THREADS>
+__global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ unsigned long long s_u64[THREADS / 32 + 1];
+  __shared__ unsigned s_umax;
+  __shared__ int s_owner[HPC_MAX_CAND];
+  __shared__ unsigned long long s_tgt[HPC_MAX_CAND];
+  __shared__ int s_lstar;
+
+  const int k = a.k, d = a.d, L = a.L;
+  const int64_t s = a.s;
+  const int G = gridDim.x;
+  const int64_t lo = s * blockIdx.x / G, hi = s * (blockIdx.x + 1) / G;
+  float *cl = smem;          // k x D live centroids
+  float *cr = cl + k * D;    // L x D candidate rows
+  uint8_t *flags = reinterpret_cast<uint8_t *>(cr + L * D);  // k: 1 = to be seeded
+
+  for (int j = threadIdx.x; j < k; j += THREADS) flags[j] = a.deg ? a.deg[j] : 1;
+  __syncthreads();
+  int any_deg = 0, any_live = 0;
+  for (int j = threadIdx.x; j < k; j += THREADS) {
+    any_deg |= flags[j] != 0;
+    any_live |= flags[j] == 0;
+  }
+  any_deg = __syncthreads_or(any_deg);
+  any_live = __syncthreads_or(any_live);
+  if (!any_deg) return;  // nothing to seed (same answer in every block)
+  for (int e = threadIdx.x; e < k * D; e += THREADS) {
+    const int j = e / D, t = e - j * D;
+    cl[e] = (t < d && !flags[j]) ? a.C[(int64_t)j * d + t] : 0.0f;
+  }
+  __syncthreads();
+  if (!any_live) {  // uniform first pick into the lowest slot
+    const uint64_t r = hpc_draw(a.seed, a.worker, a.round, HPC_TAG_SEED, 0);
+    const int64_t i0 = (int64_t)hpc_scale_word(r, (uint64_t)s);
+    for (int t = threadIdx.x; t < D; t += THREADS) {
+      const float v = t < d ? a.S[i0 * d + t] : 0.0f;
+      cl[t] = v;
+      if (blockIdx.x == 0 && t < d) a.C[t] = v;
+    }
+    if (threadIdx.x == 0) {
+      flags[0] = 0;
+      if (blockIdx.x == 0) a.deg[0] = 0;
+    }
+    __syncthreads();
+  }
+  // D(x)^2 to the nearest live centroid
+  if (threadIdx.x == 0) s_umax = 0u;
+  __syncthreads();
+  {
+    unsigned m = 0u;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) {
+      float x[D];
+      hpc_load_row<D>(x, a.S + i * d, d);
+      float best = __int_as_float(0x7f800000);
+      for (int j = 0; j < k; ++j) {
+        if (flags[j]) continue;
+        best = fminf(best, hpc_dist32_seq<D>(x, cl + j * D));
+      }
+      if (!(best <= 3.4028234663852886e38f)) best = __int_as_float(0x7fc00000);  // flag non-finite
+      a.w[i] = best;
+      const unsigned b = __float_as_uint(best) & 0x7fffffffu;
+      m = b > m ? b : m;
+    }
+    atomicMax(&s_umax, m);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&a.mx[0], s_umax);
+  }
+  if (!hpc_grid_sync(a.bar, a.status)) return;
+  if (__ldcg(&a.mx[0]) >= 0x7f800000u) {
+    hpc_status_set(a.status, HPC_ERR_NONFINITE);
+    return;
+  }
+  const int B = hpc_bit_length(s);
+  int t = 0;
+  for (int j = 0; j < k; ++j) {
+    if (!flags[j]) continue;
+    const float M = __uint_as_float(__ldcg(&a.mx[t & 1]));
+    if (!(M > 0.0f)) break;  // every row sits on a live centroid
+    const int F = 62 - B - hpc_frexp_exp(M);
+    // block sums of the fixed-point weights
+    unsigned long long qs = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) qs += (unsigned long long)hpc_quant(a.w[i], F);
+    qs = block_sum_u64<THREADS>(qs, s_u64);
+    if (threadIdx.x == 0) {
+      a.chunkQ[blockIdx.x] = qs;
+      if (blockIdx.x == 0) {
+        a.mx[(t + 1) & 1] = 0u;
+        for (int l = 0; l < L; ++l) a.phi[(size_t)((t + 1) & 1) * L + l] = 0ull;
+      }
+    }
+    if (!hpc_grid_sync(a.bar, a.status)) return;
+    // targets and the block owning each
+    if (threadIdx.x < L) {
+      const int l = threadIdx.x;
+      unsigned long long Q = 0;
+      for (int g = 0; g < G; ++g) Q += __ldcg(&a.chunkQ[g]);
+      const uint64_t r = hpc_draw(a.seed, a.worker, a.round, HPC_TAG_SEED,
+                                  1ull + (uint64_t)t * (uint64_t)L + (uint64_t)l);
+      const unsigned long long target = hpc_scale_word(r, Q);
+      unsigned long long run = 0;
+      int owner = G - 1;
+      unsigned long long before = 0;
+      for (int g = 0; g < G; ++g) {
+        const unsigned long long q = __ldcg(&a.chunkQ[g]);
+        if (run + q > target) {
+          owner = g;
+          before = run;
+          break;
+        }
+        run += q;
+      }
+      s_owner[l] = owner;
+      s_tgt[l] = target - before;
+    }
+    __syncthreads();
+    for (int l = 0; l < L; ++l) {
+      if (s_owner[l] != (int)blockIdx.x) continue;
+      unsigned long long tgt = s_tgt[l];
+      long long found = -1;
+      for (int64_t base = lo; base < hi; base += THREADS) {
+        const int64_t i = base + threadIdx.x;
+        const unsigned long long q = i < hi ? (unsigned long long)hpc_quant(a.w[i], F) : 0ull;
+        unsigned long long tot;
+        const unsigned long long incl = block_scan_u64<THREADS>(q, s_u64, &tot);
+        const int cnt = __syncthreads_count(i < hi && incl <= tgt);
+        const int64_t rows = min((int64_t)THREADS, hi - base);
+        if (cnt < rows) {
+          found = base + cnt;
+          break;
+        }
+        tgt -= tot;
+      }
+      if (threadIdx.x == 0) a.cand[l] = found;
+      __syncthreads();
+    }
+    if (!hpc_grid_sync(a.bar, a.status)) return;
+    // candidate potentials phi_l = sum_i q(min(w_i, D(x_i, cand_l)^2))
+    for (int e = threadIdx.x; e < L * D; e += THREADS) {
+      const int l = e / D, tt = e - l * D;
+      const long long ci = __ldcg(&a.cand[l]);
+      cr[e] = (tt < d && ci >= 0) ? a.S[ci * d + tt] : 0.0f;
+    }
+    __syncthreads();
+    unsigned long long ph[HPC_MAX_CAND];
+#pragma unroll
+    for (int l = 0; l < HPC_MAX_CAND; ++l) ph[l] = 0ull;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) {
+      float x[D];
+      hpc_load_row<D>(x, a.S + i * d, d);
+      const float wi = a.w[i];
+#pragma unroll
+      for (int l = 0; l < HPC_MAX_CAND; ++l) {
+        if (l >= L) break;
+        const float v = hpc_dist32_seq<D>(x, cr + l * D);
+        a.dc[(int64_t)l * s + i] = v;
+        ph[l] += (unsigned long long)hpc_quant(fminf(wi, v), F);
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < HPC_MAX_CAND; ++l) {
+      if (l >= L) break;
+      const unsigned long long bs = block_sum_u64<THREADS>(ph[l], s_u64);
+      if (threadIdx.x == 0 && bs != 0ull) atomicAdd(&a.phi[(size_t)(t & 1) * L + l], bs);
+    }
+    if (!hpc_grid_sync(a.bar, a.status)) return;
+    // keep the candidate with the smallest potential (first drawn on ties)
+    if (threadIdx.x == 0) {
+      int best = 0;
+      unsigned long long bp = __ldcg(&a.phi[(size_t)(t & 1) * L]);
+      for (int l = 1; l < L; ++l) {
+        const unsigned long long p = __ldcg(&a.phi[(size_t)(t & 1) * L + l]);
+        if (p < bp) {
+          bp = p;
+          best = l;
+        }
+      }
+      s_lstar = best;
+      s_umax = 0u;
+    }
+    __syncthreads();
+    const int ls = s_lstar;
+    if (blockIdx.x == 0) {
+      for (int tt = threadIdx.x; tt < d; tt += THREADS) a.C[(int64_t)j * d + tt] = cr[ls * D + tt];
+      if (threadIdx.x == 0) a.deg[j] = 0;
+    }
+    unsigned m = 0u;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) {
+      const float v = fminf(a.w[i], a.dc[(int64_t)ls * s + i]);
+      a.w[i] = v;
+      const unsigned b = __float_as_uint(v);
+      m = b > m ? b : m;
+    }
+    atomicMax(&s_umax, m);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(&a.mx[(t + 1) & 1], s_umax);
+    if (!hpc_grid_sync(a.bar, a.status)) return;
+    ++t;
+  }
+}
+
+size_t kpp_smem_bytes(int D, int k, int L) {
+  return ((size_t)k * D + (size_t)L * D) * 4 + (size_t)k + 16;
+}
+
+template <int D>
+int kpp_launch_t(const hpc_launch &Lc, const KppArgsHost &h) {
+  constexpr int THREADS = 256;
+  auto kern = kmeanspp_kernel<D, THREADS>;
+  const size_t smem = kpp_smem_bytes(D, h.k, h.L);
+  if (smem > (size_t)Lc.smem_optin) return HPC_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return HPC_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem) != cudaSuccess ||
+      per_sm < 1)
+    return HPC_ERR_UNSUPPORTED;
+  int64_t G = (int64_t)per_sm * Lc.num_sms;
+  const int64_t want = (h.s + THREADS - 1) / THREADS;
+  if (G > want) G = want;
+  if (G < 1) G = 1;
+  if (G > h.grid_cap) G = h.grid_cap;
+  KppArgs a;
+  a.S = h.S;
+  a.s = h.s;
+  a.d = h.d;
+  a.k = h.k;
+  a.C = h.C;
+  a.deg = h.deg;
+  a.L = h.L;
+  a.seed = h.seed;
+  a.worker = h.worker;
+  a.round = h.round;
+  a.bar = h.bar;
+  a.status = h.status;
+  a.w = h.w;
+  a.dc = h.dc;
+  a.chunkQ = h.chunkQ;
+  a.cand = h.cand;
+  a.phi = h.phi;
+  a.mx = h.mx;
+  void *args[] = {&a};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)G),
+                                                    dim3(THREADS), args, smem, Lc.stream);
+  return e == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
+}
+
+}  // namespace
+
+int hpc_kmeanspp_launch(const hpc_launch &L, const KppArgsHost &h) {
+  if (h.L < 1 || h.L > HPC_MAX_CAND) return HPC_ERR_ARG;
+  switch (hpc_pad_dim(h.d)) {
+    case 2: return kpp_launch_t<2>(L, h);
+    case 4: return kpp_launch_t<4>(L, h);
+    case 8: return kpp_launch_t<8>(L, h);
+    case 16: return kpp_launch_t<16>(L, h);
+    case 32: return kpp_launch_t<32>(L, h);
+    case 64: return kpp_launch_t<64>(L, h);
+    default: return kpp_launch_t<128>(L, h);
+  }
+}

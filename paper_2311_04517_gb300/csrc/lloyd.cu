@@ -1,0 +1,376 @@
+// Lloyd's K-means on one sample (Algorithm 1; stop rule of Section 6.5) as
+// one persistent cooperative kernel, and the full-data objective of Eq. 1.
+//
+// Lloyd: one bounded grid barrier per iteration.  Phase A assigns this
+// block's rows (hpc_assign_group) and adds each row into shared-memory
+// per-centroid sums on an exact 64-bit fixed-point grid, then flushes them
+// with integer atomics into a global buffer; integer sums make the result
+// independent of the order of the additions.  After the barrier every block
+// reads the same sums and objective partials, takes the same stop decision
+// and computes the same new centroids (no second barrier).  The sum buffers
+// rotate over three slots so that zeroing never races a reader.
+#include "assign.cuh"
+#include "kernels.h"
+
+namespace {
+
+struct LloydArgs {
+  const float *S;
+  int64_t s;
+  int d, k;
+  float *C;
+  uint8_t *deg;
+  int max_iter;
+  double tol;
+  int32_t *labels;
+  double *f_out;
+  int32_t *iters_out;
+  hpc_gridbar *bar;
+  int *status;
+  unsigned *gmaxabs;
+  unsigned long long *gsum;  // 3 * k * d
+  unsigned *gcount;          // 3 * k
+  double *gpart;             // 2 * gridDim.x
+  int smem_sums;             // 1: per-block sums in shared memory
+};
+
+template <int D, int R, int THREADS>
+__global__ void __launch_bounds__(THREADS) lloyd_kernel(LloydArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float s_red[2];
+  __shared__ double s_dsum[32];
+  __shared__ double s_f;
+  __shared__ unsigned s_umax;
+
+  const int k = a.k, d = a.d;
+  const int64_t s = a.s;
+  const int G = gridDim.x;
+  hpc_cent_smem cs;
+  cs.c = reinterpret_cast<float *>(smem_raw);
+  cs.cn = cs.c + k * D;
+  unsigned long long *ssum =
+      reinterpret_cast<unsigned long long *>(smem_raw + (((size_t)k * (D + 1) * 4 + 15) & ~(size_t)15));
+  unsigned *scnt = reinterpret_cast<unsigned *>(ssum + (size_t)k * d);
+
+  const int64_t TR = (int64_t)THREADS * R;
+  const int64_t ngroups = (s + TR - 1) / TR;
+
+  // Phase 0: largest |x| of the sample (sets the fixed-point grid and
+  // detects non-finite rows: NaN/inf bit patterns compare above finite).
+  if (threadIdx.x == 0) s_umax = 0u;
+  __syncthreads();
+  {
+    unsigned m = 0u;
+    for (int64_t g = blockIdx.x; g < ngroups; g += G) {
+      for (int64_t e = g * TR * d + threadIdx.x; e < min((g + 1) * TR, s) * d; e += THREADS) {
+        const unsigned b = __float_as_uint(a.S[e]) & 0x7fffffffu;
+        m = b > m ? b : m;
+      }
+    }
+    atomicMax(&s_umax, m);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(a.gmaxabs, s_umax);
+  }
+  hpc_load_centroids<D>(cs, a.C, a.deg, k, d, s_red);
+  if (!hpc_grid_sync(a.bar, a.status)) return;
+  const unsigned mabs = __ldcg(a.gmaxabs);
+  if (mabs >= 0x7f800000u) {
+    hpc_status_set(a.status, HPC_ERR_NONFINITE);
+    return;
+  }
+  if (cs.live == 0) {
+    hpc_status_set(a.status, HPC_ERR_DEGENERATE_ALL);
+    return;
+  }
+  // grid 2^Fs with |q| < 2^(62 - bitlen(s)) so that any sum of s values fits
+  int Fs = 126;
+  if (mabs != 0u) Fs = min(126, 62 - hpc_bit_length(s) - hpc_frexp_exp(__uint_as_float(mabs)));
+  const float qscale = ldexpf(1.0f, Fs);
+  const double qinv = ldexp(1.0, -Fs);
+
+  double f_prev = 0.0;
+  for (int it = 0;; ++it) {
+    const int buf = it % 3;
+    unsigned long long *gs = a.gsum + (size_t)buf * k * d;
+    unsigned *gc = a.gcount + (size_t)buf * k;
+    unsigned long long *acc_sum = a.smem_sums ? ssum : gs;
+    unsigned *acc_cnt = a.smem_sums ? scnt : gc;
+    if (a.smem_sums) {
+      for (int e = threadIdx.x; e < k * d; e += THREADS) ssum[e] = 0ull;
+      for (int j = threadIdx.x; j < k; j += THREADS) scnt[j] = 0u;
+    }
+    __syncthreads();
+    // Phase A: assignment and accumulation
+    double fpart = 0.0;
+    for (int64_t g = blockIdx.x; g < ngroups; g += G) {
+      const int64_t base = g * TR;
+      float x[R][D];
+      int lab[R];
+      bool valid[R];
+      fpart += (double)hpc_assign_group<D, R, THREADS>(a.S, s, d, base, cs, k, x, lab, valid, a.status);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!valid[r]) continue;
+        const int64_t i = base + (int64_t)r * THREADS + threadIdx.x;
+        const int j = lab[r];
+        if (a.labels) a.labels[i] = j;
+        atomicAdd(&acc_cnt[j], 1u);
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+          if (t < d) {
+            const long long q = __float2ll_rn(x[r][t] * qscale);
+            atomicAdd(&acc_sum[(size_t)j * d + t], (unsigned long long)q);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (a.smem_sums) {
+      for (int e = threadIdx.x; e < k * d; e += THREADS)
+        if (ssum[e] != 0ull) atomicAdd(&gs[e], ssum[e]);
+      for (int j = threadIdx.x; j < k; j += THREADS)
+        if (scnt[j] != 0u) atomicAdd(&gc[j], scnt[j]);
+    }
+    const double bsum = hpc_block_sum(fpart, s_dsum);
+    if (threadIdx.x == 0) a.gpart[(size_t)(it & 1) * G + blockIdx.x] = bsum;
+    if (!hpc_grid_sync(a.bar, a.status)) return;
+
+    // Phase B (every block): objective, stop test, new centroids
+    if (threadIdx.x == 0) {
+      double f = 0.0;
+      const double *gp = a.gpart + (size_t)(it & 1) * G;
+      for (int b = 0; b < G; ++b) f += __ldcg(gp + b);
+      s_f = f;
+    }
+    __syncthreads();
+    const double f = s_f;
+    const bool done = (it > 0 && (f_prev == 0.0 || (f_prev - f) < a.tol * f_prev)) || it == a.max_iter;
+    if (done) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.f_out = f;
+        if (a.iters_out) *a.iters_out = it;
+      }
+      return;
+    }
+    for (int e = threadIdx.x; e < k * D; e += THREADS) {
+      const int j = e / D, t = e - j * D;
+      if (isinf(cs.cn[j]) || t >= d) continue;
+      const unsigned cnt = __ldcg(gc + j);
+      if (cnt == 0u) continue;
+      const long long q = (long long)__ldcg(gs + (size_t)j * d + t);
+      const float v = (float)(((double)q * qinv) / (double)cnt);
+      cs.c[e] = v;
+      if (blockIdx.x == 0) a.C[(int64_t)j * d + t] = v;
+    }
+    if (blockIdx.x == 0) {  // recycle the slot read two iterations ago
+      const int zb = (it + 2) % 3;
+      for (int e = threadIdx.x; e < k * d; e += THREADS) a.gsum[(size_t)zb * k * d + e] = 0ull;
+      for (int j = threadIdx.x; j < k; j += THREADS) a.gcount[(size_t)zb * k + j] = 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_red[0] = 0.0f;
+      s_red[1] = 0.0f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += THREADS) {
+      if (isinf(cs.cn[j])) continue;
+      if (__ldcg(gc + j) == 0u) {  // emptied: degenerate for the rest of the run
+        cs.cn[j] = __int_as_float(0x7f800000);
+        if (blockIdx.x == 0) a.deg[j] = 1;
+        continue;
+      }
+      float nn = 0.0f;
+#pragma unroll 8
+      for (int t = 0; t < D; ++t) nn = fmaf(cs.c[j * D + t], cs.c[j * D + t], nn);
+      cs.cn[j] = nn;
+      atomicMax(reinterpret_cast<unsigned *>(&s_red[0]), __float_as_uint(nn));
+      atomicAdd(reinterpret_cast<unsigned *>(&s_red[1]), 1u);
+    }
+    __syncthreads();
+    cs.cmax = sqrtf(s_red[0]);
+    cs.live = (int)__float_as_uint(s_red[1]);
+    f_prev = f;
+    __syncthreads();
+  }
+}
+
+// Full-data objective: grid-stride over row groups, FP64 per-block partial,
+// the last block to finish sums the partials in block order.
+struct ObjArgs {
+  const float *X;
+  int64_t n;
+  int d, k;
+  const float *C;
+  const uint8_t *deg;
+  double *f_out;
+  int32_t *labels;
+  int *status;
+  double *part;
+  unsigned *done_count;
+};
+
+template <int D, int R, int THREADS>
+__global__ void __launch_bounds__(THREADS) objective_kernel(ObjArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float s_red[2];
+  __shared__ double s_dsum[32];
+  __shared__ bool s_last;
+  hpc_cent_smem cs;
+  cs.c = reinterpret_cast<float *>(smem_raw);
+  cs.cn = cs.c + a.k * D;
+  hpc_load_centroids<D>(cs, a.C, a.deg, a.k, a.d, s_red);
+  const int64_t TR = (int64_t)THREADS * R;
+  const int64_t ngroups = (a.n + TR - 1) / TR;
+  double fpart = 0.0;
+  if (cs.live == 0) {
+    if (a.n > 0) hpc_status_set(a.status, HPC_ERR_DEGENERATE_ALL);
+  } else {
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+      const int64_t base = g * TR;
+      float x[R][D];
+      int lab[R];
+      bool valid[R];
+      fpart += (double)hpc_assign_group<D, R, THREADS>(a.X, a.n, a.d, base, cs, a.k, x, lab, valid,
+                                                       a.status);
+      if (a.labels) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (valid[r]) a.labels[base + (int64_t)r * THREADS + threadIdx.x] = lab[r];
+      }
+    }
+  }
+  const double bsum = hpc_block_sum(fpart, s_dsum);
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x] = bsum;
+    __threadfence();
+    const unsigned prev = atomicAdd(a.done_count, 1u);
+    s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    double f = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) f += __ldcg(a.part + b);
+    *a.f_out = (cs.live == 0 && a.n > 0) ? __longlong_as_double(0x7ff8000000000000ll) : f;
+    *a.done_count = 0u;
+  }
+}
+
+template <int D>
+struct Tile {
+  static constexpr int R = D <= 4 ? 8 : D <= 16 ? 4 : D <= 32 ? 2 : 1;
+  static constexpr int THREADS = 256;
+};
+
+size_t lloyd_smem_bytes(int D, int k, int d, bool smem_sums) {
+  size_t b = (((size_t)k * (D + 1) * 4 + 15) & ~(size_t)15);
+  if (smem_sums) b += (size_t)k * d * 8 + (size_t)k * 4;
+  return b;
+}
+
+template <int D>
+int lloyd_launch_t(const hpc_launch &L, const LloydArgsHost &h) {
+  using T = Tile<D>;
+  auto kern = lloyd_kernel<D, T::R, T::THREADS>;
+  const size_t cent_only = lloyd_smem_bytes(D, h.k, h.d, false);
+  const size_t with_sums = lloyd_smem_bytes(D, h.k, h.d, true);
+  const bool smem_sums = with_sums <= (size_t)L.smem_optin;
+  const size_t smem = smem_sums ? with_sums : cent_only;
+  if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return HPC_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T::THREADS, smem) != cudaSuccess ||
+      per_sm < 1)
+    return HPC_ERR_UNSUPPORTED;
+  const int64_t TR = (int64_t)T::THREADS * T::R;
+  const int64_t groups = (h.s + TR - 1) / TR;
+  int64_t G = (int64_t)per_sm * L.num_sms;
+  if (G > groups) G = groups;
+  if (G < 1) G = 1;
+  if (h.grid_cap > 0 && G > h.grid_cap) G = h.grid_cap;
+  LloydArgs a;
+  a.S = h.S;
+  a.s = h.s;
+  a.d = h.d;
+  a.k = h.k;
+  a.C = h.C;
+  a.deg = h.deg;
+  a.max_iter = h.max_iter;
+  a.tol = h.tol;
+  a.labels = h.labels;
+  a.f_out = h.f_out;
+  a.iters_out = h.iters_out;
+  a.bar = h.bar;
+  a.status = h.status;
+  a.gmaxabs = h.gmaxabs;
+  a.gsum = h.gsum;
+  a.gcount = h.gcount;
+  a.gpart = h.gpart;
+  a.smem_sums = smem_sums ? 1 : 0;
+  void *args[] = {&a};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)G),
+                                                    dim3(T::THREADS), args, smem, L.stream);
+  return e == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
+}
+
+template <int D>
+int objective_launch_t(const hpc_launch &L, const ObjArgsHost &h) {
+  using T = Tile<D>;
+  auto kern = objective_kernel<D, T::R, T::THREADS>;
+  const size_t smem = (((size_t)h.k * (D + 1) * 4 + 15) & ~(size_t)15);
+  if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return HPC_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T::THREADS, smem) != cudaSuccess ||
+      per_sm < 1)
+    return HPC_ERR_UNSUPPORTED;
+  const int64_t TR = (int64_t)T::THREADS * T::R;
+  const int64_t groups = (h.n + TR - 1) / TR;
+  int64_t G = (int64_t)per_sm * L.num_sms;
+  if (G > groups) G = groups;
+  if (G < 1) G = 1;
+  if (G > h.max_blocks) G = h.max_blocks;
+  ObjArgs a;
+  a.X = h.X;
+  a.n = h.n;
+  a.d = h.d;
+  a.k = h.k;
+  a.C = h.C;
+  a.deg = h.deg;
+  a.f_out = h.f_out;
+  a.labels = h.labels;
+  a.status = h.status;
+  a.part = h.part;
+  a.done_count = h.done_count;
+  kern<<<(unsigned)G, T::THREADS, smem, L.stream>>>(a);
+  return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
+}
+
+}  // namespace
+
+int hpc_lloyd_launch(const hpc_launch &L, const LloydArgsHost &h) {
+  switch (hpc_pad_dim(h.d)) {
+    case 2: return lloyd_launch_t<2>(L, h);
+    case 4: return lloyd_launch_t<4>(L, h);
+    case 8: return lloyd_launch_t<8>(L, h);
+    case 16: return lloyd_launch_t<16>(L, h);
+    case 32: return lloyd_launch_t<32>(L, h);
+    case 64: return lloyd_launch_t<64>(L, h);
+    default: return lloyd_launch_t<128>(L, h);
+  }
+}
+
+int hpc_objective_launch(const hpc_launch &L, const ObjArgsHost &h) {
+  switch (hpc_pad_dim(h.d)) {
+    case 2: return objective_launch_t<2>(L, h);
+    case 4: return objective_launch_t<4>(L, h);
+    case 8: return objective_launch_t<8>(L, h);
+    case 16: return objective_launch_t<16>(L, h);
+    case 32: return objective_launch_t<32>(L, h);
+    case 64: return objective_launch_t<64>(L, h);
+    default: return objective_launch_t<128>(L, h);
+  }
+}

@@ -1,0 +1,60 @@
+// Sampling (Section 3: each worker draws a random sample S of size s from X;
+// Algorithms 3-5, first step of the worker loop).  Row i of the sample is
+// X[floor(r_i * n / 2^64)], r_i = draw i of stream (seed, worker, round, 0):
+// one thread turns one Philox block into four row indices, then the rows are
+// gathered with 16-byte accesses where the row width allows it.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace {
+
+__global__ void sample_index_kernel(int64_t n, uint64_t seed, uint32_t worker, uint32_t round,
+                                    int64_t s, int64_t *__restrict__ idx) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b * 4 >= s) return;
+  uint64_t v[4];
+  hpc_draw_block(seed, worker, round, HPC_TAG_SAMPLE, (uint64_t)b, v);
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const int64_t i = b * 4 + w;
+    if (i < s) idx[i] = (int64_t)hpc_scale_word(v[w], (uint64_t)n);
+  }
+}
+
+// One thread per 16-byte chunk of a sample row (d % 4 == 0).
+__global__ void gather4_kernel(const float4 *__restrict__ X, int d4, int64_t s,
+                               const int64_t *__restrict__ idx, float4 *__restrict__ S) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= s * d4) return;
+  const int64_t i = e / d4;
+  const int c = (int)(e - i * d4);
+  S[e] = __ldg(X + idx[i] * d4 + c);
+}
+
+__global__ void gather1_kernel(const float *__restrict__ X, int d, int64_t s,
+                               const int64_t *__restrict__ idx, float *__restrict__ S) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= s * d) return;
+  const int64_t i = e / d;
+  const int t = (int)(e - i * d);
+  S[e] = __ldg(X + idx[i] * d + t);
+}
+
+}  // namespace
+
+int hpc_sample_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
+                      uint32_t worker, uint32_t round, int64_t s, float *S, int64_t *idx) {
+  if (s == 0) return HPC_OK;
+  const int T = 256;
+  const int64_t blocks_idx = ((s + 3) / 4 + T - 1) / T;
+  sample_index_kernel<<<(unsigned)blocks_idx, T, 0, L.stream>>>(n, seed, worker, round, s, idx);
+  if (d % 4 == 0) {
+    const int64_t tot = s * (d / 4);
+    gather4_kernel<<<(unsigned)((tot + T - 1) / T), T, 0, L.stream>>>(
+        reinterpret_cast<const float4 *>(X), d / 4, s, idx, reinterpret_cast<float4 *>(S));
+  } else {
+    const int64_t tot = s * d;
+    gather1_kernel<<<(unsigned)((tot + T - 1) / T), T, 0, L.stream>>>(X, d, s, idx, S);
+  }
+  return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
+}

@@ -1,0 +1,273 @@
+"""Thin Python binding of ``libhpclust.so`` (the C ABI in include/hpclust.h).
+
+Argument marshalling only: every step runs in the CUDA kernels behind the C
+ABI.  Tensors are torch CUDA tensors (PyTorch provides device memory and
+streams); pointers, sizes and the current stream are passed through ctypes.
+There is no CPU fallback: loading fails loudly when the library is missing
+and cannot be built, and every call raises on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from pathlib import Path
+
+import torch
+
+from . import _build
+
+HPC_OK = 0
+HPC_ERR_ARG = -1
+HPC_ERR_NOMEM = -2
+HPC_ERR_CUDA = -3
+HPC_ERR_TIMEOUT = -4
+HPC_ERR_NONFINITE = -5
+HPC_ERR_DEGENERATE_ALL = -6
+HPC_ERR_UNSUPPORTED = -7
+HPC_FP32, HPC_BF16, HPC_FP8 = 0, 1, 2
+HPC_COMPETITIVE, HPC_COOPERATIVE = 0, 1
+
+# The paper's hyperparameters (Section 6.5).
+MAX_ITER = 300
+REL_TOL = 1e-4
+N_CANDIDATES = 3
+
+_STATUS_NAMES = {v: k for k, v in dict(
+    HPC_ERR_ARG=HPC_ERR_ARG, HPC_ERR_NOMEM=HPC_ERR_NOMEM, HPC_ERR_CUDA=HPC_ERR_CUDA,
+    HPC_ERR_TIMEOUT=HPC_ERR_TIMEOUT, HPC_ERR_NONFINITE=HPC_ERR_NONFINITE,
+    HPC_ERR_DEGENERATE_ALL=HPC_ERR_DEGENERATE_ALL,
+    HPC_ERR_UNSUPPORTED=HPC_ERR_UNSUPPORTED).items()}
+
+
+class HPCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hpc_batch(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int32), ("s", ctypes.c_void_p), ("k", ctypes.c_void_p),
+                ("group", ctypes.c_void_p), ("C_off", ctypes.c_void_p),
+                ("K_off", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("degenerate", ctypes.c_void_p), ("fhat", ctypes.c_void_p),
+                ("f_new", ctypes.c_void_p), ("iters", ctypes.c_void_p),
+                ("accepted", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> Path:
+    return _build.OUT
+
+
+def load() -> ctypes.CDLL:
+    """Loads (building in-tree first if needed) the CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if _build.stale():
+        _build.build()
+    L = ctypes.CDLL(str(_build.OUT))
+    P, i32, i64, u32, u64, f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                  ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double)
+    sig = {
+        "hpc_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, P], ctypes.c_int),
+        "hpc_destroy": ([P], ctypes.c_int),
+        "hpc_set_stream": ([P, P], ctypes.c_int),
+        "hpc_sync_status": ([P], ctypes.c_int),
+        "hpc_last_error": ([P], ctypes.c_char_p),
+        "hpc_launch_count": ([P], i64),
+        "hpc_reserve": ([P, i64], ctypes.c_int),
+        "hpc_draw_sample": ([P, P, i64, i32, u64, u32, u32, i64, P, P], ctypes.c_int),
+        "hpc_kmeanspp": ([P, P, i64, i32, i32, P, P, i32, u64, u32, u32], ctypes.c_int),
+        "hpc_lloyd": ([P, P, i64, i32, i32, P, P, i32, f64, i32, P, P, P], ctypes.c_int),
+        "hpc_objective": ([P, P, i64, i32, P, i32, P, i32, P, P], ctypes.c_int),
+        "hpc_selftest_wait_timeout": ([P, i64], ctypes.c_int),
+        "hpc_round": ([P, P, i64, i32, ctypes.POINTER(hpc_batch), i32, u64, u32, i32, f64,
+                       i32, i32], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, name, device):
+    if t is None:
+        return
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name}: expected a tensor on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+
+
+class Context:
+    """An ``hpc_ctx`` bound to one CUDA device and (by default) torch's
+    current stream on that device."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.lib = load()
+        self.device = torch.device("cuda", device)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = st
+        h = ctypes.c_void_p()
+        rc = self.lib.hpc_create(ctypes.byref(h), device, ctypes.c_void_p(st.cuda_stream))
+        if rc != HPC_OK:
+            raise HPCError(rc, "hpc_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hpc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self._check(self.lib.hpc_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def _check(self, rc: int):
+        if rc != HPC_OK:
+            raise HPCError(rc, self.lib.hpc_last_error(self.h).decode())
+
+    def sync_status(self) -> int:
+        return int(self.lib.hpc_sync_status(self.h))
+
+    def check_status(self):
+        """Synchronise and raise if a device-side error was recorded."""
+        self._check(self.sync_status())
+
+    def launch_count(self) -> int:
+        return int(self.lib.hpc_launch_count(self.h))
+
+    def reserve(self, nbytes: int):
+        self._check(self.lib.hpc_reserve(self.h, int(nbytes)))
+
+    def selftest_wait_timeout(self, limit_ns: int):
+        """Launches the bounded-wait self-test (see include/hpclust.h)."""
+        self._check(self.lib.hpc_selftest_wait_timeout(self.h, int(limit_ns)))
+
+
+def hpc_draw_sample(ctx: Context, X, seed: int, worker: int, round_: int, s: int,
+                    S_out=None, idx_out=None):
+    n, d = X.shape
+    _need(X, torch.float32, "X", ctx.device)
+    if S_out is None:
+        S_out = torch.empty((s, d), dtype=torch.float32, device=ctx.device)
+    _need(S_out, torch.float32, "S_out", ctx.device)
+    _need(idx_out, torch.int64, "idx_out", ctx.device)
+    ctx._check(ctx.lib.hpc_draw_sample(ctx.h, _ptr(X), n, d, seed, worker, round_, s,
+                                       _ptr(S_out), _ptr(idx_out)))
+    return S_out, idx_out
+
+
+def hpc_kmeanspp(ctx: Context, S, C, degenerate=None, n_candidates: int = N_CANDIDATES,
+                 seed: int = 0, worker: int = 0, round_: int = 0):
+    """Seeds (in place) the degenerate rows of C; returns (C, degenerate)."""
+    s, d = S.shape
+    k = C.shape[0]
+    _need(S, torch.float32, "S", ctx.device)
+    _need(C, torch.float32, "C", ctx.device)
+    _need(degenerate, torch.uint8, "degenerate", ctx.device)
+    ctx._check(ctx.lib.hpc_kmeanspp(ctx.h, _ptr(S), s, d, k, _ptr(C), _ptr(degenerate),
+                                    n_candidates, seed, worker, round_))
+    return C, degenerate
+
+
+def hpc_lloyd(ctx: Context, S, C, degenerate=None, max_iter: int = MAX_ITER,
+              rel_tol: float = REL_TOL, prec: int = HPC_FP32, labels_out=None,
+              f_out=None, iters_out=None):
+    """Runs Lloyd in place on C / degenerate; returns (f_out, iters_out) device tensors."""
+    s, d = S.shape
+    k = C.shape[0]
+    _need(S, torch.float32, "S", ctx.device)
+    _need(C, torch.float32, "C", ctx.device)
+    _need(degenerate, torch.uint8, "degenerate", ctx.device)
+    _need(labels_out, torch.int32, "labels_out", ctx.device)
+    if f_out is None:
+        f_out = torch.empty(1, dtype=torch.float64, device=ctx.device)
+    if iters_out is None:
+        iters_out = torch.empty(1, dtype=torch.int32, device=ctx.device)
+    ctx._check(ctx.lib.hpc_lloyd(ctx.h, _ptr(S), s, d, k, _ptr(C), _ptr(degenerate), max_iter,
+                                 rel_tol, prec, _ptr(labels_out), _ptr(f_out), _ptr(iters_out)))
+    return f_out, iters_out
+
+
+def hpc_objective(ctx: Context, X, C, degenerate=None, prec: int = HPC_FP32, f_out=None,
+                  labels_out=None):
+    n, d = X.shape
+    k = C.shape[0]
+    _need(X, torch.float32, "X", ctx.device)
+    _need(C, torch.float32, "C", ctx.device)
+    _need(degenerate, torch.uint8, "degenerate", ctx.device)
+    _need(labels_out, torch.int32, "labels_out", ctx.device)
+    if f_out is None:
+        f_out = torch.empty(1, dtype=torch.float64, device=ctx.device)
+    ctx._check(ctx.lib.hpc_objective(ctx.h, _ptr(X) if n > 0 else None, n, d, _ptr(C), k,
+                                     _ptr(degenerate), prec, _ptr(f_out), _ptr(labels_out)))
+    return f_out
+
+
+class Batch:
+    """Worker set for hpc_round: host descriptors plus device state."""
+
+    def __init__(self, d: int, s, k, group=None, device=None):
+        import numpy as np
+        self.d = d
+        self.device = device or torch.device("cuda", 0)
+        self.s = np.ascontiguousarray(s, dtype=np.int64)
+        self.k = np.ascontiguousarray(k, dtype=np.int32)
+        self.W = len(self.s)
+        self.group = (np.zeros(self.W, np.int32) if group is None
+                      else np.ascontiguousarray(group, dtype=np.int32))
+        self.C_off = np.zeros(self.W, np.int64)
+        self.K_off = np.zeros(self.W, np.int64)
+        nf = nk = 0
+        for w in range(self.W):
+            self.C_off[w] = nf
+            self.K_off[w] = nk
+            nf += int(self.k[w]) * d
+            nf = (nf + 3) // 4 * 4      # keep every worker's centroids 16-byte aligned
+            nk += int(self.k[w])
+        self.C = torch.zeros(nf, dtype=torch.float32, device=self.device)
+        self.degenerate = torch.ones(nk, dtype=torch.uint8, device=self.device)
+        self.fhat = torch.full((self.W,), math.inf, dtype=torch.float64, device=self.device)
+        self.f_new = torch.zeros(self.W, dtype=torch.float64, device=self.device)
+        self.iters = torch.zeros(self.W, dtype=torch.int32, device=self.device)
+        self.accepted = torch.zeros(self.W, dtype=torch.uint8, device=self.device)
+
+    def struct(self) -> hpc_batch:
+        return hpc_batch(self.W, self.s.ctypes.data, self.k.ctypes.data, self.group.ctypes.data,
+                         self.C_off.ctypes.data, self.K_off.ctypes.data, self.C.data_ptr(),
+                         self.degenerate.data_ptr(), self.fhat.data_ptr(), self.f_new.data_ptr(),
+                         self.iters.data_ptr(), self.accepted.data_ptr())
+
+    def centroids(self, w: int):
+        k = int(self.k[w])
+        o = int(self.C_off[w])
+        return (self.C[o: o + k * self.d].view(k, self.d),
+                self.degenerate[int(self.K_off[w]): int(self.K_off[w]) + k])
+
+
+def hpc_round(ctx: Context, X, batch: Batch, strategy: int, seed: int, round_: int,
+              max_iter: int = MAX_ITER, rel_tol: float = REL_TOL,
+              n_candidates: int = N_CANDIDATES, prec: int = HPC_FP32):
+    n, d = X.shape
+    _need(X, torch.float32, "X", ctx.device)
+    b = batch.struct()
+    ctx._check(ctx.lib.hpc_round(ctx.h, _ptr(X), n, d, ctypes.byref(b), strategy, seed, round_,
+                                 max_iter, rel_tol, n_candidates, prec))

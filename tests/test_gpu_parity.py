@@ -1,0 +1,384 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (from the arithmetic, see each test):
+  * sample rows / indices and K-means++ seeding: bit-exact (integer and
+    exact-fixed-point decisions taken in the same precision on both sides);
+  * labels: equal, except rows whose two nearest double-precision distances
+    differ by less than 1e-6 relative (a near tie);
+  * objectives: within 1e-6 relative; centroids: within 1e-6 of the largest
+    centroid coordinate.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from paper_2311_04517_gb300 import hpclust as H
+from paper_2311_04517_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-6
+TIE = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = H.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def mixture(n, d, comps, seed, spread=10.0, sd=1.0):
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(-spread, spread, (comps, d))
+    z = rng.integers(0, comps, n)
+    return (mu[z] + sd * rng.standard_normal((n, d))).astype(np.float32)
+
+
+def assert_labels(lab_g, S, C, deg, what=""):
+    lab_o, d1, d2, _ = orc.assign(S, C, deg)
+    diff = np.flatnonzero(lab_g != lab_o)
+    if diff.size:
+        near = (d2[diff] - d1[diff]) <= TIE * d1[diff]
+        assert near.all(), f"{what}: {np.count_nonzero(~near)} labels differ away from ties"
+        # the GPU's pick is then as near as the oracle's within the tie bound
+        Cd = C.astype(np.float64)
+        dg = ((S[diff].astype(np.float64) - Cd[lab_g[diff]]) ** 2).sum(1)
+        assert np.all(dg <= d1[diff] * (1 + TIE))
+    return diff.size
+
+
+def assert_centroids(Cg, Co, what=""):
+    scale = max(1.0, float(np.abs(Co).max()))
+    err = float(np.abs(Cg.astype(np.float64) - Co.astype(np.float64)).max())
+    assert err <= RTOL * scale, f"{what}: centroid error {err} > {RTOL * scale}"
+
+
+# ---------------------------------------------------------------------------
+# Sampling (Section 3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,d,s", [(1000, 16, 777), (5, 3, 64), (1, 2, 10), (12345, 128, 3001),
+                                   (70000, 1, 5000), (1000, 5, 0)])
+def test_draw_sample_bit_exact(ctx, n, d, s):
+    X = mixture(n, d, 3, 1)
+    S_o, idx_o = orc.draw_sample(X, seed=77, worker=5, round_=3, s=s)
+    idx = torch.empty(s, dtype=torch.int64, device="cuda")
+    S_g, _ = H.hpc_draw_sample(ctx, dev(X), 77, 5, 3, s, idx_out=idx)
+    ctx.check_status()
+    np.testing.assert_array_equal(host(idx), idx_o)
+    np.testing.assert_array_equal(host(S_g), S_o)
+
+
+# ---------------------------------------------------------------------------
+# Full-data objective (Eq. 1) and assignment
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,d,k", [(20000, 2, 5), (100003, 16, 25), (4099, 1, 3), (3001, 3, 7),
+                                   (50001, 32, 50), (20011, 64, 100), (9001, 128, 100),
+                                   (7777, 17, 9), (2048, 5, 1)])
+def test_objective_parity(ctx, n, d, k):
+    X = mixture(n, d, max(k, 2), seed=n + d)
+    rng = np.random.default_rng(k)
+    C = X[rng.choice(n, k, replace=False)] + 0.1 * rng.standard_normal((k, d)).astype(np.float32)
+    C = C.astype(np.float32)
+    deg = np.zeros(k, np.uint8)
+    if k >= 5:
+        deg[[1, k // 2]] = 1
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    f_g = H.hpc_objective(ctx, dev(X), dev(C), dev(deg), labels_out=lab)
+    ctx.check_status()
+    f_o = orc.objective(X, C, deg)
+    assert float(host(f_g)[0]) == pytest.approx(f_o, rel=RTOL)
+    assert_labels(host(lab), X, C, deg, "objective")
+    # deterministic: a second run gives the same bits
+    f_g2 = H.hpc_objective(ctx, dev(X), dev(C), dev(deg))
+    ctx.check_status()
+    assert float(host(f_g2)[0]) == float(host(f_g)[0])
+
+
+def test_objective_edge_cases(ctx):
+    C = dev(np.array([[0, 0], [1, 0], [1, 0], [-1, 0]], np.float32))
+    # empty input
+    f = H.hpc_objective(ctx, torch.empty((0, 2), dtype=torch.float32, device="cuda"), C)
+    ctx.check_status()
+    assert float(host(f)[0]) == 0.0
+    # exact ties go to the lowest index (centroids 1 and 2 coincide)
+    X = dev(np.array([[2, 0], [0.5, 0], [-0.5, 0], [3, 0]], np.float32))
+    lab = torch.empty(4, dtype=torch.int32, device="cuda")
+    H.hpc_objective(ctx, X, C, labels_out=lab)
+    ctx.check_status()
+    assert list(host(lab)) == [1, 0, 0, 1]
+    # no live centroid
+    H.hpc_objective(ctx, X, C, dev(np.ones(4, np.uint8)))
+    assert ctx.sync_status() == H.HPC_ERR_DEGENERATE_ALL
+    # non-finite row
+    Xn = np.array([[1, 1], [np.nan, 0]], np.float32)
+    H.hpc_objective(ctx, dev(Xn), C)
+    assert ctx.sync_status() == H.HPC_ERR_NONFINITE
+    # host-side argument errors
+    with pytest.raises(H.HPCError):
+        H.hpc_objective(ctx, torch.zeros((4, 129), device="cuda"), torch.zeros((2, 129), device="cuda"))
+    with pytest.raises(H.HPCError):
+        H.hpc_objective(ctx, X, C, prec=H.HPC_BF16)
+
+
+def test_objective_near_ties_are_resolved_exactly(ctx):
+    # rows placed (almost) on the bisector of two centroids far from the
+    # origin: the FP32 expanded form cannot separate them, rescoring must
+    rng = np.random.default_rng(3)
+    d = 16
+    c0 = rng.uniform(50, 60, d)
+    c1 = c0 + rng.uniform(-1, 1, d) * 0.5
+    mid = (c0 + c1) / 2
+    n = 4096
+    X = (mid + rng.standard_normal((n, d)) * 1e-4 + np.outer(rng.uniform(-1e-3, 1e-3, n), c1 - c0))
+    X = X.astype(np.float32)
+    C = np.stack([c0, c1]).astype(np.float32)
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    H.hpc_objective(ctx, dev(X), dev(C), labels_out=lab)
+    ctx.check_status()
+    lab_o, d1, d2, _ = orc.assign(X, C)
+    g = host(lab)
+    # double-precision rescoring: equal wherever the FP64 distances differ at all
+    strict = (d2 - d1) > 1e-12 * d1
+    np.testing.assert_array_equal(g[strict], lab_o[strict])
+
+
+@pytest.mark.parametrize("n", [2**25 + 3])
+def test_objective_large_index_range(ctx, n):
+    # n * d > 2^31 elements: 64-bit row addressing
+    d, k = 64, 8
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn((n, d), generator=g, device="cuda") * 3
+    Cn = np.random.default_rng(1).standard_normal((k, d)).astype(np.float32) * 3
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    f = H.hpc_objective(ctx, X, dev(Cn), labels_out=lab)
+    ctx.check_status()
+    idx = np.concatenate([np.arange(1000), np.arange(n - 5000, n),
+                          np.random.default_rng(2).integers(0, n, 20000)])
+    Xs = host(X[torch.from_numpy(idx).cuda()])
+    assert_labels(host(lab)[idx], Xs, Cn, None, "large")
+    f_o = orc.objective(host(X), Cn)
+    assert float(host(f)[0]) == pytest.approx(f_o, rel=RTOL)
+    del X
+
+
+# ---------------------------------------------------------------------------
+# K-means++ seeding: bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("s,d,k,L,seed", [(2000, 2, 5, 3, 0), (100000, 16, 25, 3, 1),
+                                          (3001, 17, 12, 1, 2), (5000, 128, 20, 3, 3),
+                                          (777, 3, 40, 8, 4), (1, 4, 1, 3, 5)])
+def test_kmeanspp_bit_exact(ctx, s, d, k, L, seed):
+    S = mixture(s, d, max(2, k // 2), seed)
+    C0 = np.zeros((k, d), np.float32)
+    deg0 = np.ones(k, np.uint8)
+    o = orc.kmeanspp(S, C0, deg0, L=L, seed=seed, worker=2, round_=7)
+    Cg, dg = dev(C0), dev(deg0)
+    H.hpc_kmeanspp(ctx, dev(S), Cg, dg, n_candidates=L, seed=seed, worker=2, round_=7)
+    ctx.check_status()
+    np.testing.assert_array_equal(host(dg), o["degenerate"])
+    np.testing.assert_array_equal(host(Cg), o["C"])
+
+
+def test_kmeanspp_partial_reseed_and_exhaustion(ctx):
+    rng = np.random.default_rng(9)
+    S = mixture(4000, 8, 6, 9)
+    C0 = rng.standard_normal((10, 8)).astype(np.float32)
+    deg0 = np.array([0, 1, 1, 0, 0, 1, 0, 1, 1, 0], np.uint8)
+    o = orc.kmeanspp(S, C0, deg0, seed=11, worker=1, round_=2)
+    Cg, dg = dev(C0), dev(deg0)
+    H.hpc_kmeanspp(ctx, dev(S), Cg, dg, seed=11, worker=1, round_=2)
+    ctx.check_status()
+    np.testing.assert_array_equal(host(Cg), o["C"])
+    np.testing.assert_array_equal(host(dg), o["degenerate"])
+    # fewer distinct rows than centroids: the rest stay degenerate
+    S2 = np.repeat(np.array([[0, 0], [1, 1], [5, 5]], np.float32), 50, axis=0)
+    o2 = orc.kmeanspp(S2, np.zeros((6, 2), np.float32), np.ones(6, np.uint8), seed=3)
+    Cg, dg = dev(np.zeros((6, 2), np.float32)), dev(np.ones(6, np.uint8))
+    H.hpc_kmeanspp(ctx, dev(S2), Cg, dg, seed=3)
+    ctx.check_status()
+    np.testing.assert_array_equal(host(dg), o2["degenerate"])
+    np.testing.assert_array_equal(host(Cg), o2["C"])
+    # nothing to seed: untouched
+    Cg = dev(C0)
+    dg = dev(np.zeros(10, np.uint8))
+    H.hpc_kmeanspp(ctx, dev(S), Cg, dg, seed=3)
+    ctx.check_status()
+    np.testing.assert_array_equal(host(Cg), C0)
+
+
+# ---------------------------------------------------------------------------
+# Lloyd (Algorithm 1, Section 6.5 stop rule)
+# ---------------------------------------------------------------------------
+def gpu_lloyd(ctx, S, C0, deg0, **kw):
+    Cg, dg = dev(C0), dev(deg0)
+    lab = torch.empty(S.shape[0], dtype=torch.int32, device="cuda")
+    f, it = H.hpc_lloyd(ctx, dev(S), Cg, dg, labels_out=lab, **kw)
+    ctx.check_status()
+    return dict(C=host(Cg), degenerate=host(dg), labels=host(lab), f=float(host(f)[0]),
+                iters=int(host(it)[0]))
+
+
+def lockstep_divergence(ctx, S, C0, deg0, iters):
+    """Steps the oracle and the GPU one update at a time from the same state.
+    Returns the first step where the labels differ (only near ties allowed),
+    or None; any centroid difference beyond tolerance fails."""
+    C, deg = C0.copy(), deg0.copy()
+    Sd = dev(S)
+    for it in range(iters + 1):
+        lab_o, d1, d2, _ = orc.assign(S, C, deg)
+        lab = torch.empty(S.shape[0], dtype=torch.int32, device="cuda")
+        H.hpc_objective(ctx, Sd, dev(C), dev(deg), labels_out=lab)
+        ctx.check_status()
+        diff = np.flatnonzero(host(lab) != lab_o)
+        if diff.size:
+            assert ((d2[diff] - d1[diff]) <= TIE * d1[diff]).all(), "labels differ away from ties"
+            return it
+        Co, dego = orc.update(S, lab_o, C, deg)
+        g = gpu_lloyd(ctx, S, C, deg, max_iter=1, rel_tol=0.0)
+        assert_centroids(g["C"], Co, f"lockstep step {it}")
+        np.testing.assert_array_equal(g["degenerate"], dego)
+        C, deg = Co, dego
+    return None
+
+
+@pytest.mark.parametrize("s,d,k,seed", [(2000, 2, 5, 0), (100000, 16, 25, 1), (20000, 32, 50, 2),
+                                        (9001, 64, 30, 3), (5000, 128, 10, 4), (30011, 5, 8, 5)])
+def test_lloyd_parity(ctx, s, d, k, seed):
+    S = mixture(s, d, k, seed, sd=1.5)
+    init = orc.kmeanspp(S, np.zeros((k, d), np.float32), np.ones(k, np.uint8), seed=seed)
+    C0, deg0 = init["C"], init["degenerate"]
+    o = orc.lloyd(S, C0, deg0)
+    g = gpu_lloyd(ctx, S, C0, deg0)
+    same = (g["iters"] == o["iters"] and (g["degenerate"] == o["degenerate"]).all()
+            and abs(g["f"] - o["f"]) <= RTOL * o["f"])
+    if same:
+        assert_centroids(g["C"], o["C"], "lloyd")
+        assert_labels(g["labels"], S, o["C"], o["degenerate"], "lloyd")
+    else:
+        # only a near tie (in a label or in the stop test) may explain it
+        step = lockstep_divergence(ctx, S, C0, deg0, max(g["iters"], o["iters"]))
+        if step is None:
+            tr = o["f_trace"]
+            it = min(g["iters"], o["iters"])
+            ratio = (tr[it - 1] - tr[it]) / tr[it - 1]
+            assert abs(ratio - 1e-4) <= 1e-6, "trajectories differ without a near tie"
+    # the reported objective is the objective of the returned centroids
+    assert g["f"] == pytest.approx(orc.objective(S, g["C"], g["degenerate"]), rel=RTOL)
+
+
+def test_lloyd_edge_cases(ctx):
+    # k > distinct rows: empty clusters become degenerate, keep their values
+    S = np.array([[0, 0], [0.1, 0], [5, 5], [5.1, 5]], np.float32)
+    C0 = np.array([[0, 0], [5, 5], [100, 100]], np.float32)
+    o = orc.lloyd(S, C0, np.zeros(3, np.uint8))
+    g = gpu_lloyd(ctx, S, C0, np.zeros(3, np.uint8))
+    np.testing.assert_array_equal(g["degenerate"], o["degenerate"])
+    assert_centroids(g["C"], o["C"])
+    assert g["iters"] == o["iters"]
+    # one row
+    g = gpu_lloyd(ctx, S[:1], C0[:1], np.zeros(1, np.uint8))
+    assert g["f"] == 0.0 and g["iters"] == 1
+    # zero iterations: only the assignment
+    S2 = mixture(3000, 4, 3, 8)
+    g = gpu_lloyd(ctx, S2, S2[:3].copy(), np.zeros(3, np.uint8), max_iter=0)
+    assert g["iters"] == 0
+    np.testing.assert_array_equal(g["C"], S2[:3])
+    assert g["f"] == pytest.approx(orc.objective(S2, S2[:3]), rel=RTOL)
+    # every centroid degenerate
+    Cg, dg = dev(C0), dev(np.ones(3, np.uint8))
+    H.hpc_lloyd(ctx, dev(S), Cg, dg)
+    assert ctx.sync_status() == H.HPC_ERR_DEGENERATE_ALL
+    # non-finite sample
+    Sn = S.copy()
+    Sn[2, 1] = np.inf
+    H.hpc_lloyd(ctx, dev(Sn), dev(C0), dev(np.zeros(3, np.uint8)))
+    assert ctx.sync_status() == H.HPC_ERR_NONFINITE
+
+
+def test_lloyd_is_deterministic(ctx):
+    S = mixture(50000, 16, 20, 12, sd=2.0)
+    C0 = S[:20].copy()
+    a = gpu_lloyd(ctx, S, C0, np.zeros(20, np.uint8))
+    b = gpu_lloyd(ctx, S, C0, np.zeros(20, np.uint8))
+    np.testing.assert_array_equal(a["C"], b["C"])
+    np.testing.assert_array_equal(a["labels"], b["labels"])
+    assert a["f"] == b["f"] and a["iters"] == b["iters"]
+
+
+# ---------------------------------------------------------------------------
+# Rounds (Algorithms 3 and 4), re-synchronised to the GPU state every round
+# ---------------------------------------------------------------------------
+def oracle_state_from(batch):
+    st = orc.RoundState(batch.d, batch.s, batch.k, batch.group)
+    for w in range(batch.W):
+        k = int(batch.k[w])
+        C, deg = batch.centroids(w)
+        st.C_pool[st.C_off[w]: st.C_off[w] + k * batch.d] = host(C).ravel()
+        st.deg_pool[st.K_off[w]: st.K_off[w] + k] = host(deg)
+    st.fhat[:] = host(batch.fhat)
+    return st
+
+
+def check_round(ctx, X, Xd, batch, strategy, seed, rnd):
+    st = oracle_state_from(batch)
+    res = orc.round_(X, st, strategy, seed, rnd)
+    H.hpc_round(ctx, Xd, batch, strategy, seed, rnd)
+    ctx.check_status()
+    for w in range(batch.W):
+        C, deg = batch.centroids(w)
+        Co, dego = st.centroids(w)
+        np.testing.assert_array_equal(host(deg), dego)
+        assert_centroids(host(C), Co, f"round {rnd} worker {w}")
+        assert int(host(batch.iters)[w]) == res["iters"][w]
+        assert float(host(batch.f_new)[w]) == pytest.approx(res["f_new"][w], rel=RTOL)
+    np.testing.assert_allclose(host(batch.fhat), st.fhat, rtol=RTOL)
+    np.testing.assert_array_equal(host(batch.accepted).astype(bool), res["accepted"])
+
+
+def test_round_tiny_workload_20_rounds(ctx):
+    wl = synth.WORKLOADS["tiny"]
+    X = host(synth.make_data(wl))
+    Xd = dev(X)
+    ws = synth.worker_setup(wl)
+    batch = H.Batch(wl.d, ws.s, ws.k, ws.group)
+    for rnd in range(wl.rounds):
+        check_round(ctx, X, Xd, batch, H.HPC_COMPETITIVE, wl.seed, rnd)
+        f = H.hpc_objective(ctx, Xd, batch.centroids(0)[0], batch.centroids(0)[1])
+        ctx.check_status()
+        C, deg = batch.centroids(0)
+        assert float(host(f)[0]) == pytest.approx(orc.objective(X, host(C), host(deg)), rel=RTOL)
+
+
+@pytest.mark.parametrize("strategy", [0, 1])
+def test_round_several_workers(ctx, strategy):
+    X = mixture(30000, 8, 12, 21, sd=1.2)
+    Xd = dev(X)
+    batch = H.Batch(8, [3000, 5000, 4000, 2500], [6, 6, 9, 6], [0, 0, 1, 0])
+    for rnd in range(4):
+        check_round(ctx, X, Xd, batch, strategy, 3, rnd)
+
+
+# ---------------------------------------------------------------------------
+# Failure detection: a bounded device wait that runs out reports an error
+# ---------------------------------------------------------------------------
+def test_bounded_wait_reports_timeout(ctx):
+    ctx.selftest_wait_timeout(20_000_000)     # 20 ms
+    assert ctx.sync_status() == H.HPC_ERR_TIMEOUT
+    # the context stays usable afterwards
+    X = mixture(1000, 4, 3, 1)
+    f = H.hpc_objective(ctx, dev(X), dev(X[:3].copy()))
+    ctx.check_status()
+    assert float(host(f)[0]) == pytest.approx(orc.objective(X, X[:3]), rel=RTOL)
