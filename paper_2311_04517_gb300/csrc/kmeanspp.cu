@@ -171,28 +171,34 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
       }
     }
     if (!hpc_grid_sync(a.bar, a.status)) return;
-    // targets and the block owning each
-    if (threadIdx.x < L) {
-      const int l = threadIdx.x;
-      unsigned long long Q = 0;
-      for (int g = 0; g < G; ++g) Q += __ldcg(&a.chunkQ[g]);
-      const uint64_t r = hpc_draw(a.seed, a.worker, a.round, HPC_TAG_SEED,
-                                  1ull + (uint64_t)t * (uint64_t)L + (uint64_t)l);
-      const unsigned long long target = hpc_scale_word(r, Q);
-      unsigned long long run = 0;
-      int owner = G - 1;
-      unsigned long long before = 0;
-      for (int g = 0; g < G; ++g) {
-        const unsigned long long q = __ldcg(&a.chunkQ[g]);
-        if (run + q > target) {
-          owner = g;
-          before = run;
-          break;
+    // targets and the block owning each: every block scans the per-block
+    // sums in parallel (segments of ceil(G / THREADS) blocks per thread)
+    if (threadIdx.x < L) s_owner[threadIdx.x] = -1;
+    {
+      const int seg = (G + THREADS - 1) / THREADS;
+      const int g0 = threadIdx.x * seg, g1 = min(G, g0 + seg);
+      unsigned long long loc = 0;
+      for (int g = g0; g < g1; ++g) loc += __ldcg(&a.chunkQ[g]);
+      unsigned long long Q;
+      const unsigned long long incl = block_scan_u64<THREADS>(loc, s_u64, &Q);
+      const unsigned long long excl = incl - loc;
+      for (int l = 0; l < L; ++l) {
+        const uint64_t r = hpc_draw(a.seed, a.worker, a.round, HPC_TAG_SEED,
+                                    1ull + (uint64_t)t * (uint64_t)L + (uint64_t)l);
+        const unsigned long long target = hpc_scale_word(r, Q);
+        if (excl <= target && target < incl) {  // exactly one thread: its segment holds it
+          unsigned long long run = excl;
+          for (int g = g0; g < g1; ++g) {
+            const unsigned long long q = __ldcg(&a.chunkQ[g]);
+            if (run + q > target) {
+              s_owner[l] = g;
+              s_tgt[l] = target - run;
+              break;
+            }
+            run += q;
+          }
         }
-        run += q;
       }
-      s_owner[l] = owner;
-      s_tgt[l] = target - before;
     }
     __syncthreads();
     for (int l = 0; l < L; ++l) {

@@ -2,13 +2,15 @@
 // one persistent cooperative kernel, and the full-data objective of Eq. 1.
 //
 // Lloyd: one bounded grid barrier per iteration.  Phase A assigns this
-// block's rows (hpc_assign_group) and adds each row into shared-memory
-// per-centroid sums on an exact 64-bit fixed-point grid, then flushes them
-// with integer atomics into a global buffer; integer sums make the result
+// block's rows (hpc_assign_group), then the warp re-reads its rows with lanes
+// mapped to dimensions and adds every coordinate, on an exact 64-bit
+// fixed-point grid, into per-block shared-memory sums (lanes of one pass hit
+// different dimensions, so they do not collide); the block flushes its sums
+// with integer atomics into a global buffer.  Integer sums make the result
 // independent of the order of the additions.  After the barrier every block
 // reads the same sums and objective partials, takes the same stop decision
-// and computes the same new centroids (no second barrier).  The sum buffers
-// rotate over three slots so that zeroing never races a reader.
+// and computes the same new centroids (no second barrier).  The global sum
+// buffers rotate over three slots so that zeroing never races a reader.
 #include "assign.cuh"
 #include "kernels.h"
 
@@ -34,35 +36,76 @@ struct LloydArgs {
   int smem_sums;             // 1: per-block sums in shared memory
 };
 
-template <int D, int R, int THREADS>
-__global__ void __launch_bounds__(THREADS) lloyd_kernel(LloydArgs a) {
+// Objective: several rows per thread amortise the centroid reads.
+template <int D>
+struct Tile {
+  static constexpr int R = D <= 4 ? 8 : D <= 16 ? 4 : D <= 32 ? 2 : 1;
+  static constexpr int THREADS = 256;
+};
+
+// Lloyd: samples are small (10^4 - 10^6 rows), so one row per thread spreads
+// an iteration over every SM; the accumulation maps lanes to dimensions.
+template <int D>
+struct LTile {
+  static constexpr int R = 1;
+  static constexpr int THREADS = 256;
+  static constexpr int MINB = D <= 16 ? 2 : 1;
+  static constexpr int LPR = D < 32 ? D : 32;          // lanes per row
+  static constexpr int RPP = 32 / LPR;                 // rows per pass
+  static constexpr int TPL = (D + LPR - 1) / LPR;      // dimensions per lane
+  static constexpr int NB = TPL >= 4 ? 4 : 8;          // rows per batch of loads
+};
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Shared-memory layout of the Lloyd kernel.
+struct LloydSmem {
+  size_t cent, dead, lab, sums, cnt, total;
+  __host__ __device__ LloydSmem(int D, int R, int THREADS, int k, int d, bool smem_sums) {
+    const int kp = (k + 1) & ~1;
+    cent = 0;
+    dead = align16((size_t)kp * D * 4 + (size_t)kp * 8);
+    lab = dead + align16((size_t)kp);
+    sums = lab + align16((size_t)R * THREADS * 4);
+    cnt = sums + (smem_sums ? align16((size_t)k * d * 8) : 0);
+    total = cnt + (smem_sums ? align16((size_t)k * 4) : 0);
+  }
+};
+
+template <int D, int R, int THREADS, bool PACKED>
+__global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_red[2];
   __shared__ double s_dsum[32];
   __shared__ double s_f;
   __shared__ unsigned s_umax;
+  constexpr int LPR = LTile<D>::LPR, RPP = LTile<D>::RPP, TPL = LTile<D>::TPL, NB = LTile<D>::NB;
 
   const int k = a.k, d = a.d;
   const int64_t s = a.s;
   const int G = gridDim.x;
+  const LloydSmem L(D, R, THREADS, k, d, a.smem_sums != 0);
   hpc_cent_smem cs;
-  cs.c = reinterpret_cast<float *>(smem_raw);
-  cs.cn = cs.c + k * D;
-  unsigned long long *ssum =
-      reinterpret_cast<unsigned long long *>(smem_raw + (((size_t)k * (D + 1) * 4 + 15) & ~(size_t)15));
-  unsigned *scnt = reinterpret_cast<unsigned *>(ssum + (size_t)k * d);
+  hpc_cent_bind(cs, smem_raw, D, k);
+  uint8_t *dead = smem_raw + L.dead;
+  int *wlab = reinterpret_cast<int *>(smem_raw + L.lab);
+  unsigned long long *ssum = reinterpret_cast<unsigned long long *>(smem_raw + L.sums);
+  unsigned *scnt = reinterpret_cast<unsigned *>(smem_raw + L.cnt);
 
   const int64_t TR = (int64_t)THREADS * R;
   const int64_t ngroups = (s + TR - 1) / TR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   // Phase 0: largest |x| of the sample (sets the fixed-point grid and
   // detects non-finite rows: NaN/inf bit patterns compare above finite).
   if (threadIdx.x == 0) s_umax = 0u;
+  for (int j = threadIdx.x; j < cs.kp; j += THREADS) dead[j] = (j >= k) || (a.deg && a.deg[j]);
   __syncthreads();
   {
     unsigned m = 0u;
     for (int64_t g = blockIdx.x; g < ngroups; g += G) {
-      for (int64_t e = g * TR * d + threadIdx.x; e < min((g + 1) * TR, s) * d; e += THREADS) {
+      const int64_t e1 = min((g + 1) * TR, s) * d;
+      for (int64_t e = g * TR * d + threadIdx.x; e < e1; e += THREADS) {
         const unsigned b = __float_as_uint(a.S[e]) & 0x7fffffffu;
         m = b > m ? b : m;
       }
@@ -71,7 +114,12 @@ __global__ void __launch_bounds__(THREADS) lloyd_kernel(LloydArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(a.gmaxabs, s_umax);
   }
-  hpc_load_centroids<D>(cs, a.C, a.deg, k, d, s_red);
+  for (int e = threadIdx.x; e < cs.kp * D; e += THREADS) {
+    const int j = e / D, t = e - j * D;
+    cs.cm[e] = (j < k && t < d) ? -2.0f * a.C[(int64_t)j * d + t] : 0.0f;
+  }
+  __syncthreads();
+  hpc_cent_finish<D>(cs, k, s_red, [&](int j) { return dead[j] != 0; });
   if (!hpc_grid_sync(a.bar, a.status)) return;
   const unsigned mabs = __ldcg(a.gmaxabs);
   if (mabs >= 0x7f800000u) {
@@ -100,29 +148,58 @@ __global__ void __launch_bounds__(THREADS) lloyd_kernel(LloydArgs a) {
       for (int j = threadIdx.x; j < k; j += THREADS) scnt[j] = 0u;
     }
     __syncthreads();
-    // Phase A: assignment and accumulation
+    // Phase A: assignment, then accumulation with lanes over dimensions
     double fpart = 0.0;
     for (int64_t g = blockIdx.x; g < ngroups; g += G) {
       const int64_t base = g * TR;
-      float x[R][D];
       int lab[R];
       bool valid[R];
-      fpart += (double)hpc_assign_group<D, R, THREADS>(a.S, s, d, base, cs, k, x, lab, valid, a.status);
+      fpart += (double)hpc_assign_group<D, R, THREADS, PACKED>(a.S, s, d, base, cs, lab, valid,
+                                                               a.status);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        if (!valid[r]) continue;
-        const int64_t i = base + (int64_t)r * THREADS + threadIdx.x;
-        const int j = lab[r];
-        if (a.labels) a.labels[i] = j;
-        atomicAdd(&acc_cnt[j], 1u);
+        wlab[r * THREADS + threadIdx.x] = valid[r] ? lab[r] : -1;
+        if (valid[r] && a.labels) a.labels[base + (int64_t)r * THREADS + threadIdx.x] = lab[r];
+      }
+      __syncwarp();
+      // lane (rsub, t0) takes dimensions t0, t0 + LPR, ... of rows
+      // rsub, rsub + RPP, ...; NB rows' loads are issued before their atomics
+      const int t0 = lane % LPR, rsub = lane / LPR;
+#pragma unroll 1
+      for (int r = 0; r < R; ++r) {
+        const int64_t row0 = base + (int64_t)r * THREADS + warp * 32;
+        const int *wl = wlab + r * THREADS + warp * 32;
+#pragma unroll 1
+        for (int b0 = 0; b0 < 32 / RPP; b0 += NB) {
+          int jj[NB];
+          float v[NB][TPL];
 #pragma unroll
-        for (int t = 0; t < D; ++t) {
-          if (t < d) {
-            const long long q = __float2ll_rn(x[r][t] * qscale);
-            atomicAdd(&acc_sum[(size_t)j * d + t], (unsigned long long)q);
+          for (int i = 0; i < NB; ++i) {
+            const int rr = rsub + RPP * (b0 + i);
+            jj[i] = (b0 + i < 32 / RPP) ? wl[rr] : -1;
+            const float *xr = a.S + (row0 + rr) * d;
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+              const int t = t0 + u * LPR;
+              v[i][u] = (jj[i] >= 0 && jj[i] < k && t < d) ? xr[t] : 0.0f;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < NB; ++i) {
+            const int j = jj[i];
+            if (j < 0 || j >= k) continue;
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) {
+              const int t = t0 + u * LPR;
+              if (t < d)
+                atomicAdd(&acc_sum[(size_t)j * d + t],
+                          (unsigned long long)__float2ll_rn(v[i][u] * qscale));
+            }
+            if (t0 == 0) atomicAdd(&acc_cnt[j], 1u);
           }
         }
       }
+      __syncwarp();
     }
     __syncthreads();
     if (a.smem_sums) {
@@ -136,11 +213,9 @@ __global__ void __launch_bounds__(THREADS) lloyd_kernel(LloydArgs a) {
     if (!hpc_grid_sync(a.bar, a.status)) return;
 
     // Phase B (every block): objective, stop test, new centroids
-    if (threadIdx.x == 0) {
-      double f = 0.0;
-      const double *gp = a.gpart + (size_t)(it & 1) * G;
-      for (int b = 0; b < G; ++b) f += __ldcg(gp + b);
-      s_f = f;
+    {
+      const double f = hpc_block_sum_array(a.gpart + (size_t)(it & 1) * G, G, s_dsum);
+      if (threadIdx.x == 0) s_f = f;
     }
     __syncthreads();
     const double f = s_f;
@@ -154,12 +229,12 @@ __global__ void __launch_bounds__(THREADS) lloyd_kernel(LloydArgs a) {
     }
     for (int e = threadIdx.x; e < k * D; e += THREADS) {
       const int j = e / D, t = e - j * D;
-      if (isinf(cs.cn[j]) || t >= d) continue;
+      if (dead[j] || t >= d) continue;
       const unsigned cnt = __ldcg(gc + j);
       if (cnt == 0u) continue;
       const long long q = (long long)__ldcg(gs + (size_t)j * d + t);
       const float v = (float)(((double)q * qinv) / (double)cnt);
-      cs.c[e] = v;
+      cs.cm[e] = -2.0f * v;
       if (blockIdx.x == 0) a.C[(int64_t)j * d + t] = v;
     }
     if (blockIdx.x == 0) {  // recycle the slot read two iterations ago
@@ -168,35 +243,20 @@ __global__ void __launch_bounds__(THREADS) lloyd_kernel(LloydArgs a) {
       for (int j = threadIdx.x; j < k; j += THREADS) a.gcount[(size_t)zb * k + j] = 0u;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      s_red[0] = 0.0f;
-      s_red[1] = 0.0f;
-    }
-    __syncthreads();
     for (int j = threadIdx.x; j < k; j += THREADS) {
-      if (isinf(cs.cn[j])) continue;
-      if (__ldcg(gc + j) == 0u) {  // emptied: degenerate for the rest of the run
-        cs.cn[j] = __int_as_float(0x7f800000);
+      if (!dead[j] && __ldcg(gc + j) == 0u) {  // emptied: degenerate for the rest of the run
+        dead[j] = 1;
         if (blockIdx.x == 0) a.deg[j] = 1;
-        continue;
       }
-      float nn = 0.0f;
-#pragma unroll 8
-      for (int t = 0; t < D; ++t) nn = fmaf(cs.c[j * D + t], cs.c[j * D + t], nn);
-      cs.cn[j] = nn;
-      atomicMax(reinterpret_cast<unsigned *>(&s_red[0]), __float_as_uint(nn));
-      atomicAdd(reinterpret_cast<unsigned *>(&s_red[1]), 1u);
     }
     __syncthreads();
-    cs.cmax = sqrtf(s_red[0]);
-    cs.live = (int)__float_as_uint(s_red[1]);
+    hpc_cent_finish<D>(cs, k, s_red, [&](int j) { return dead[j] != 0; });
     f_prev = f;
-    __syncthreads();
   }
 }
 
 // Full-data objective: grid-stride over row groups, FP64 per-block partial,
-// the last block to finish sums the partials in block order.
+// the last block to finish sums the partials in a fixed order.
 struct ObjArgs {
   const float *X;
   int64_t n;
@@ -210,15 +270,14 @@ struct ObjArgs {
   unsigned *done_count;
 };
 
-template <int D, int R, int THREADS>
-__global__ void __launch_bounds__(THREADS) objective_kernel(ObjArgs a) {
+template <int D, int R, int THREADS, bool PACKED>
+__global__ void __launch_bounds__(THREADS, D <= 16 ? 2 : 1) objective_kernel(ObjArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_red[2];
   __shared__ double s_dsum[32];
   __shared__ bool s_last;
   hpc_cent_smem cs;
-  cs.c = reinterpret_cast<float *>(smem_raw);
-  cs.cn = cs.c + a.k * D;
+  hpc_cent_bind(cs, smem_raw, D, a.k);
   hpc_load_centroids<D>(cs, a.C, a.deg, a.k, a.d, s_red);
   const int64_t TR = (int64_t)THREADS * R;
   const int64_t ngroups = (a.n + TR - 1) / TR;
@@ -228,11 +287,10 @@ __global__ void __launch_bounds__(THREADS) objective_kernel(ObjArgs a) {
   } else {
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
       const int64_t base = g * TR;
-      float x[R][D];
       int lab[R];
       bool valid[R];
-      fpart += (double)hpc_assign_group<D, R, THREADS>(a.X, a.n, a.d, base, cs, a.k, x, lab, valid,
-                                                       a.status);
+      fpart += (double)hpc_assign_group<D, R, THREADS, PACKED>(a.X, a.n, a.d, base, cs, lab, valid,
+                                                               a.status);
       if (a.labels) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -248,35 +306,24 @@ __global__ void __launch_bounds__(THREADS) objective_kernel(ObjArgs a) {
     s_last = prev == gridDim.x - 1;
   }
   __syncthreads();
-  if (s_last && threadIdx.x == 0) {
+  if (s_last) {
     __threadfence();
-    double f = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) f += __ldcg(a.part + b);
-    *a.f_out = (cs.live == 0 && a.n > 0) ? __longlong_as_double(0x7ff8000000000000ll) : f;
-    *a.done_count = 0u;
+    const double f = hpc_block_sum_array(a.part, (int)gridDim.x, s_dsum);
+    if (threadIdx.x == 0) {
+      *a.f_out = (cs.live == 0 && a.n > 0) ? __longlong_as_double(0x7ff8000000000000ll) : f;
+      *a.done_count = 0u;
+    }
   }
 }
 
-template <int D>
-struct Tile {
-  static constexpr int R = D <= 4 ? 8 : D <= 16 ? 4 : D <= 32 ? 2 : 1;
-  static constexpr int THREADS = 256;
-};
-
-size_t lloyd_smem_bytes(int D, int k, int d, bool smem_sums) {
-  size_t b = (((size_t)k * (D + 1) * 4 + 15) & ~(size_t)15);
-  if (smem_sums) b += (size_t)k * d * 8 + (size_t)k * 4;
-  return b;
-}
-
-template <int D>
+template <int D, bool PACKED>
 int lloyd_launch_t(const hpc_launch &L, const LloydArgsHost &h) {
-  using T = Tile<D>;
-  auto kern = lloyd_kernel<D, T::R, T::THREADS>;
-  const size_t cent_only = lloyd_smem_bytes(D, h.k, h.d, false);
-  const size_t with_sums = lloyd_smem_bytes(D, h.k, h.d, true);
-  const bool smem_sums = with_sums <= (size_t)L.smem_optin;
-  const size_t smem = smem_sums ? with_sums : cent_only;
+  using T = LTile<D>;
+  auto kern = lloyd_kernel<D, T::R, T::THREADS, PACKED>;
+  const LloydSmem with(D, T::R, T::THREADS, h.k, h.d, true);
+  const LloydSmem without(D, T::R, T::THREADS, h.k, h.d, false);
+  const bool smem_sums = with.total <= (size_t)L.smem_optin;
+  const size_t smem = smem_sums ? with.total : without.total;
   if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HPC_ERR_CUDA;
@@ -315,11 +362,12 @@ int lloyd_launch_t(const hpc_launch &L, const LloydArgsHost &h) {
   return e == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 
-template <int D>
+template <int D, bool PACKED>
 int objective_launch_t(const hpc_launch &L, const ObjArgsHost &h) {
   using T = Tile<D>;
-  auto kern = objective_kernel<D, T::R, T::THREADS>;
-  const size_t smem = (((size_t)h.k * (D + 1) * 4 + 15) & ~(size_t)15);
+  auto kern = objective_kernel<D, T::R, T::THREADS, PACKED>;
+  const int kp = (h.k + 1) & ~1;
+  const size_t smem = (size_t)kp * D * 4 + (size_t)kp * 8;
   if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HPC_ERR_CUDA;
@@ -349,28 +397,38 @@ int objective_launch_t(const hpc_launch &L, const ObjArgsHost &h) {
   return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 
+template <int D>
+int lloyd_dispatch(const hpc_launch &L, const LloydArgsHost &h) {
+  return h.k <= 32 ? lloyd_launch_t<D, true>(L, h) : lloyd_launch_t<D, false>(L, h);
+}
+
+template <int D>
+int objective_dispatch(const hpc_launch &L, const ObjArgsHost &h) {
+  return h.k <= 32 ? objective_launch_t<D, true>(L, h) : objective_launch_t<D, false>(L, h);
+}
+
 }  // namespace
 
 int hpc_lloyd_launch(const hpc_launch &L, const LloydArgsHost &h) {
   switch (hpc_pad_dim(h.d)) {
-    case 2: return lloyd_launch_t<2>(L, h);
-    case 4: return lloyd_launch_t<4>(L, h);
-    case 8: return lloyd_launch_t<8>(L, h);
-    case 16: return lloyd_launch_t<16>(L, h);
-    case 32: return lloyd_launch_t<32>(L, h);
-    case 64: return lloyd_launch_t<64>(L, h);
-    default: return lloyd_launch_t<128>(L, h);
+    case 2: return lloyd_dispatch<2>(L, h);
+    case 4: return lloyd_dispatch<4>(L, h);
+    case 8: return lloyd_dispatch<8>(L, h);
+    case 16: return lloyd_dispatch<16>(L, h);
+    case 32: return lloyd_dispatch<32>(L, h);
+    case 64: return lloyd_dispatch<64>(L, h);
+    default: return lloyd_dispatch<128>(L, h);
   }
 }
 
 int hpc_objective_launch(const hpc_launch &L, const ObjArgsHost &h) {
   switch (hpc_pad_dim(h.d)) {
-    case 2: return objective_launch_t<2>(L, h);
-    case 4: return objective_launch_t<4>(L, h);
-    case 8: return objective_launch_t<8>(L, h);
-    case 16: return objective_launch_t<16>(L, h);
-    case 32: return objective_launch_t<32>(L, h);
-    case 64: return objective_launch_t<64>(L, h);
-    default: return objective_launch_t<128>(L, h);
+    case 2: return objective_dispatch<2>(L, h);
+    case 4: return objective_dispatch<4>(L, h);
+    case 8: return objective_dispatch<8>(L, h);
+    case 16: return objective_dispatch<16>(L, h);
+    case 32: return objective_dispatch<32>(L, h);
+    case 64: return objective_dispatch<64>(L, h);
+    default: return objective_dispatch<128>(L, h);
   }
 }
