@@ -23,24 +23,28 @@
 #define HPC_U32 5.9604644775390625e-08f  // 2^-24
 #define HPC_DEAD 1.0e38f                 // norm given to degenerate / padding centroids
 
+// Row stride (floats) of the centroid block: rows are padded by 16 bytes so
+// that lanes gathering different centroids hit different banks.
+__host__ __device__ constexpr int hpc_cstride(int D) { return D >= 4 ? D + 4 : D; }
+
 // Centroid block in shared memory.
 struct hpc_cent_smem {
-  float *cm;    // kp x D: -2 c (zero padded beyond d)
+  float *cm;    // kp rows of hpc_cstride(D) floats: -2 c (zero padded beyond d)
   float2 *cnz;  // kp: (||c||^2, 0), HPC_DEAD for degenerate and padding slots
   float cmax;   // max ||c_j|| over live centroids
   int live;     // number of live centroids
   int kp;       // k rounded up to even
 };
 
-__device__ __forceinline__ size_t hpc_cent_smem_bytes(int D, int k) {
+__host__ __device__ __forceinline__ size_t hpc_cent_smem_bytes(int D, int k) {
   const int kp = (k + 1) & ~1;
-  return (size_t)kp * D * 4 + (size_t)kp * 8;
+  return (size_t)kp * hpc_cstride(D) * 4 + (size_t)kp * 8;
 }
 
 __device__ __forceinline__ void hpc_cent_bind(hpc_cent_smem &cs, unsigned char *base, int D, int k) {
   cs.kp = (k + 1) & ~1;
   cs.cm = reinterpret_cast<float *>(base);
-  cs.cnz = reinterpret_cast<float2 *>(base + (size_t)cs.kp * D * 4);
+  cs.cnz = reinterpret_cast<float2 *>(base + (size_t)cs.kp * hpc_cstride(D) * 4);
 }
 
 // Recomputes norms, cmax and the live count from cs.cm (all threads).
@@ -60,7 +64,7 @@ __device__ void hpc_cent_finish(hpc_cent_smem &cs, int k, float *s_red, Dead dea
     float nn = 0.0f;
 #pragma unroll 8
     for (int t = 0; t < D; ++t) {
-      const float c = -0.5f * cs.cm[j * D + t];
+      const float c = -0.5f * cs.cm[j * hpc_cstride(D) + t];
       nn = fmaf(c, c, nn);
     }
     cs.cnz[j] = make_float2(nn, 0.0f);
@@ -77,8 +81,9 @@ __device__ void hpc_cent_finish(hpc_cent_smem &cs, int k, float *s_red, Dead dea
 template <int D>
 __device__ void hpc_load_centroids(hpc_cent_smem &cs, const float *__restrict__ C,
                                    const uint8_t *__restrict__ deg, int k, int d, float *s_red) {
-  for (int e = threadIdx.x; e < cs.kp * D; e += blockDim.x) {
-    const int j = e / D, t = e - j * D;
+  constexpr int CS = hpc_cstride(D);
+  for (int e = threadIdx.x; e < cs.kp * CS; e += blockDim.x) {
+    const int j = e / CS, t = e - j * CS;
     cs.cm[e] = (j < k && t < d) ? -2.0f * C[(int64_t)j * d + t] : 0.0f;
   }
   __syncthreads();
@@ -94,8 +99,8 @@ __device__ __forceinline__ bool hpc_is_dead(const hpc_cent_smem &cs, int j) {
 template <int D, int R>
 __device__ __forceinline__ void hpc_pair_values(const float (&x)[R][D], const hpc_cent_smem &cs, int j,
                                                 float (&va)[R], float (&vb)[R]) {
-  const float *ca = cs.cm + j * D;
-  const float *cb = ca + D;
+  const float *ca = cs.cm + j * hpc_cstride(D);
+  const float *cb = ca + hpc_cstride(D);
   const float4 nz = *reinterpret_cast<const float4 *>(cs.cnz + j);  // (n_a, 0, n_b, 0)
   float2 aa[R], ab[R];
 #pragma unroll
@@ -208,14 +213,14 @@ __device__ __forceinline__ float hpc_dist32_cm(const float (&x)[D], const float 
 // partial sums; relative error <= (D/2 + 4) u.  Used for the objective.
 template <int D>
 __device__ __forceinline__ float hpc_dist_direct_cm(const float (&x)[D], const float *cm) {
-  float a0 = 0.0f, a1 = 0.0f;
+  float2 acc = make_float2(0.0f, 0.0f);
+  const float2 half = make_float2(0.5f, 0.5f);
 #pragma unroll
   for (int t = 0; t + 1 < D; t += 2) {
-    const float e0 = fmaf(0.5f, cm[t], x[t]), e1 = fmaf(0.5f, cm[t + 1], x[t + 1]);
-    a0 = fmaf(e0, e0, a0);
-    a1 = fmaf(e1, e1, a1);
+    const float2 e = hpc_fma2(half, make_float2(cm[t], cm[t + 1]), make_float2(x[t], x[t + 1]));
+    acc = hpc_fma2(e, e, acc);
   }
-  return a0 + a1;
+  return acc.x + acc.y;
 }
 
 // Warp-cooperative exact assignment of one row (every lane calls it with
@@ -231,7 +236,7 @@ __device__ __noinline__ int hpc_rescore_row(const float *__restrict__ xrow, int 
   int ja = 0x7fffffff;
   for (int j = lane; j < cs.kp; j += 32) {
     if (hpc_is_dead(cs, j)) continue;
-    const float v = hpc_dist32_cm<D>(x, cs.cm + j * D);
+    const float v = hpc_dist32_cm<D>(x, cs.cm + j * hpc_cstride(D));
     if (v < a1) {
       a2 = a1;
       a1 = v;
@@ -256,7 +261,7 @@ __device__ __noinline__ int hpc_rescore_row(const float *__restrict__ xrow, int 
     if (hpc_is_dead(cs, j)) continue;
     double acc = 0.0;
     for (int t = 0; t < d; ++t) {
-      const double c = -0.5 * (double)cs.cm[j * D + t];
+      const double c = -0.5 * (double)cs.cm[j * hpc_cstride(D) + t];
       const double diff = __dsub_rn((double)x[t], c);
       acc = __dadd_rn(acc, __dmul_rn(diff, diff));
     }
@@ -307,7 +312,7 @@ __device__ __forceinline__ float hpc_assign_group(const float *__restrict__ X, i
     // a NaN/inf row never updates d1: its label is meaningless, use slot 0
     const bool found = d1[r] < HPC_DEAD * 0.5f;
     if (!found) lab[r] = 0;
-    dd[r] = hpc_dist_direct_cm<D>(x[r], cs.cm + lab[r] * D);
+    dd[r] = hpc_dist_direct_cm<D>(x[r], cs.cm + lab[r] * hpc_cstride(D));
     // ||x|| <= sqrt(dd) + ||c_j1|| <= sqrt(dd) + cmax
     const float rad = sqrtf(dd[r]) * 1.0001f + 2.0f * cs.cmax * 1.00001f;
     float bound = 2.001f * (float)(D + 4) * HPC_U32 * rad * rad;
@@ -330,7 +335,7 @@ __device__ __forceinline__ float hpc_assign_group(const float *__restrict__ X, i
       const int j = hpc_rescore_row<D>(X + i * d, d, cs);
       if ((tid & 31) == src && j != lab[r]) {
         lab[r] = j;
-        dd[r] = hpc_dist_direct_cm<D>(x[r], cs.cm + j * D);
+        dd[r] = hpc_dist_direct_cm<D>(x[r], cs.cm + j * hpc_cstride(D));
       }
     }
   }

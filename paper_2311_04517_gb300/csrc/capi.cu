@@ -22,6 +22,7 @@ struct hpc_ctx {
   void *ws;
   size_t ws_bytes;
   int64_t launches;
+  int use_tc;  // 0 never, 1 wherever built, 2 (default) for d >= 64
   char err[256];
 };
 
@@ -193,7 +194,11 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
   h.part = part;
   h.done_count = reinterpret_cast<unsigned *>(c->dwords + 1);
   h.max_blocks = c->grid_bound;
-  int rc = hpc_objective_launch(c->L, h);
+  const bool want_tc = c->use_tc == 1 || (c->use_tc == 2 && d >= 64);
+  int rc = (want_tc && X && aligned16(X) && hpc_tc_objective_supported(d, k, n))
+               ? hpc_tc_objective_launch(c->L, h)
+               : HPC_ERR_UNSUPPORTED;
+  if (rc == HPC_ERR_UNSUPPORTED) rc = hpc_objective_launch(c->L, h);
   if (rc == HPC_ERR_CUDA) return cuda_fail(c, cudaGetLastError(), "objective launch");
   if (rc) return fail(c, rc, "objective: unsupported shape");
   c->launches += 1;
@@ -272,6 +277,7 @@ int hpc_create(hpc_ctx **ctx, int device, void *stream) {
   cudaDeviceGetAttribute(&c->L.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   c->L.smem_optin -= 2048;  // keep room for the kernels' static shared memory
   c->grid_bound = hpc_grid_bound(c->L);
+  c->use_tc = 2;
   if (cudaMalloc(&c->dwords, 256) != cudaSuccess) {
     delete c;
     return HPC_ERR_NOMEM;
@@ -318,6 +324,12 @@ int hpc_sync_status(hpc_ctx *c) {
 }
 
 const char *hpc_last_error(hpc_ctx *c) { return c ? c->err : "null context"; }
+
+int hpc_set_tensor_cores(hpc_ctx *c, int mode) {
+  if (!c || mode < 0 || mode > 2) return HPC_ERR_ARG;
+  c->use_tc = mode;
+  return HPC_OK;
+}
 
 int64_t hpc_launch_count(hpc_ctx *c) { return c ? c->launches : 0; }
 

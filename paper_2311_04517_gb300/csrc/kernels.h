@@ -68,6 +68,8 @@ struct KppArgsHost {
 
 int hpc_lloyd_launch(const hpc_launch &L, const LloydArgsHost &h);
 int hpc_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
+bool hpc_tc_objective_supported(int d, int k, int64_t n);
+int hpc_tc_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
 int hpc_kmeanspp_launch(const hpc_launch &L, const KppArgsHost &h);
 int hpc_sample_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
                       uint32_t worker, uint32_t round, int64_t s, float *S, int64_t *idx);

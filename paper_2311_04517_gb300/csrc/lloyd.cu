@@ -64,7 +64,7 @@ struct LloydSmem {
   __host__ __device__ LloydSmem(int D, int R, int THREADS, int k, int d, bool smem_sums) {
     const int kp = (k + 1) & ~1;
     cent = 0;
-    dead = align16((size_t)kp * D * 4 + (size_t)kp * 8);
+    dead = align16(hpc_cent_smem_bytes(D, k));
     lab = dead + align16((size_t)kp);
     sums = lab + align16((size_t)R * THREADS * 4);
     cnt = sums + (smem_sums ? align16((size_t)k * d * 8) : 0);
@@ -114,8 +114,9 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(a.gmaxabs, s_umax);
   }
-  for (int e = threadIdx.x; e < cs.kp * D; e += THREADS) {
-    const int j = e / D, t = e - j * D;
+  constexpr int CS = hpc_cstride(D);
+  for (int e = threadIdx.x; e < cs.kp * CS; e += THREADS) {
+    const int j = e / CS, t = e - j * CS;
     cs.cm[e] = (j < k && t < d) ? -2.0f * a.C[(int64_t)j * d + t] : 0.0f;
   }
   __syncthreads();
@@ -227,8 +228,8 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
       }
       return;
     }
-    for (int e = threadIdx.x; e < k * D; e += THREADS) {
-      const int j = e / D, t = e - j * D;
+    for (int e = threadIdx.x; e < k * CS; e += THREADS) {
+      const int j = e / CS, t = e - j * CS;
       if (dead[j] || t >= d) continue;
       const unsigned cnt = __ldcg(gc + j);
       if (cnt == 0u) continue;
@@ -366,8 +367,7 @@ template <int D, bool PACKED>
 int objective_launch_t(const hpc_launch &L, const ObjArgsHost &h) {
   using T = Tile<D>;
   auto kern = objective_kernel<D, T::R, T::THREADS, PACKED>;
-  const int kp = (h.k + 1) & ~1;
-  const size_t smem = (size_t)kp * D * 4 + (size_t)kp * 8;
+  const size_t smem = hpc_cent_smem_bytes(D, h.k);
   if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HPC_ERR_CUDA;

@@ -84,6 +84,7 @@ def load() -> ctypes.CDLL:
         "hpc_lloyd": ([P, P, i64, i32, i32, P, P, i32, f64, i32, P, P, P], ctypes.c_int),
         "hpc_objective": ([P, P, i64, i32, P, i32, P, i32, P, P], ctypes.c_int),
         "hpc_selftest_wait_timeout": ([P, i64], ctypes.c_int),
+        "hpc_set_tensor_cores": ([P, ctypes.c_int], ctypes.c_int),
         "hpc_round": ([P, P, i64, i32, ctypes.POINTER(hpc_batch), i32, u64, u32, i32, f64,
                        i32, i32], ctypes.c_int),
     }
@@ -156,6 +157,11 @@ class Context:
 
     def reserve(self, nbytes: int):
         self._check(self.lib.hpc_reserve(self.h, int(nbytes)))
+
+    def set_tensor_cores(self, mode):
+        """Tensor-core search: False/0 never, True/1 wherever built, 2 auto
+        (the default; see include/hpclust.h)."""
+        self._check(self.lib.hpc_set_tensor_cores(self.h, int(mode)))
 
     def selftest_wait_timeout(self, limit_ns: int):
         """Launches the bounded-wait self-test (see include/hpclust.h)."""
