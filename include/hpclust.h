@@ -209,6 +209,29 @@ int hpc_round(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
               uint32_t round, int32_t max_iter, double rel_tol,
               int32_t n_candidates, int32_t prec);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* The full-data objective of hpc_objective (CUDA-core search; same labels,
+ * same objective) for callers that cannot allocate device memory when they
+ * need it: code running while a stream is captured into a CUDA graph, loops
+ * with a fixed memory budget, hosts that hand out device memory only through
+ * their own pool.  The paper has no counterpart: this is a calling
+ * convention, not a step of the method.  No context and no allocation: the
+ * kernel's per-block partial sums live in a fixed array inside the library
+ * (about 16 KB per device, kept until the process exits); the caller passes
+ * inputs and outputs as for hpc_objective, plus status_out, a device int
+ * that receives HPC_OK or the device-side error (HPC_ERR_NONFINITE,
+ * HPC_ERR_DEGENERATE_ALL) once `stream` (a cudaStream_t) has run the call.
+ * Every call on a device shares that array, so calls that may overlap on
+ * the GPU race: serialise them.  The first call on each device looks up the
+ * array's address with that device current; make it before any stream
+ * capture.  Errors: HPC_ERR_ARG for bad sizes or unaligned pointers,
+ * HPC_ERR_UNSUPPORTED if the centroid block does not fit in shared memory,
+ * HPC_ERR_CUDA if a launch fails. */
+int hpc_objective_noalloc(const float *X, int64_t n, int32_t d, const float *C, int32_t k,
+                          const uint8_t *degenerate, double *f_out, int32_t *labels_out,
+                          int32_t *status_out, void *stream);
+
 /* ---- diagnostics -------------------------------------------------------- */
 
 /* Failure-detection self-test (the paper has no counterpart).  Launches a
