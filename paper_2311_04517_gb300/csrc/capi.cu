@@ -12,6 +12,11 @@
 #include "common.cuh"
 #include "kernels.h"
 
+// Workers of one round launch per persistent kernel (every launch has at
+// least one block per SM, so at least this many tasks fit).
+#define HPC_ROUND_CHUNK 128
+#define HPC_MAX_WORKERS 65535
+
 struct hpc_ctx {
   int device;
   cudaStream_t stream;
@@ -23,6 +28,13 @@ struct hpc_ctx {
   size_t ws_bytes;
   int64_t launches;
   int use_tc;  // 0 never, 1 wherever built, 2 (default) for d >= 64
+  // pinned staging ring for the per-round descriptor tables: slot i is
+  // rewritten only after the copy issued from it last time has run
+  void *stage_host[4];
+  size_t stage_bytes[4];
+  cudaEvent_t stage_ev[4];
+  bool stage_used[4];
+  int stage_next;
   char err[256];
 };
 
@@ -81,99 +93,121 @@ int check_dims(hpc_ctx *c, int32_t d) {
 // ---- scratch layouts (one per operation) ----
 size_t pad256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-size_t lloyd_ws(const hpc_ctx *c, int64_t s, int d, int k) {
-  (void)s;
-  return pad256(64) + pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
+// Per-task words that must be zero when the persistent kernels start: the
+// Lloyd barrier and max |x| word, the K-means++ barrier, max-weight words
+// and candidate potentials.  One 256-byte header per task.
+struct TaskHeader {
+  hpc_gridbar lbar;
+  unsigned gmaxabs;
+  unsigned pad0;
+  hpc_gridbar kbar;
+  unsigned mx[2];
+  unsigned long long phi[2 * 8];
+  unsigned char pad1[256 - 32 - 128];
+};
+static_assert(sizeof(TaskHeader) == 256, "task header is one 256-byte line");
+
+size_t lloyd_ws(const hpc_ctx *c, int d, int k) {
+  return sizeof(TaskHeader) + pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
          pad256((size_t)2 * c->grid_bound * 8) + pad256((size_t)k) + 256;
 }
 
 size_t kpp_ws(const hpc_ctx *c, int64_t s, int L) {
-  return pad256(64) + pad256((size_t)s * 4) + pad256((size_t)L * s * 4) +
-         pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8) + pad256((size_t)2 * L * 8) +
-         256;
+  return sizeof(TaskHeader) + pad256((size_t)s * 4) + pad256((size_t)L * s * 4) +
+         pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8) + 256;
 }
 
 size_t obj_ws(const hpc_ctx *c) { return pad256((size_t)c->grid_bound * 8) + 256; }
 
-// Launches Lloyd with scratch carved from `cv` (layout of lloyd_ws).
+// Lloyd scratch of one task (header zeroed by the caller).
+void lloyd_task_scratch(const hpc_ctx *c, Carver &cv, TaskHeader *hd, int d, int k,
+                        hpc_lloyd_task &t) {
+  t.bar = &hd->lbar;
+  t.gmaxabs = &hd->gmaxabs;
+  t.gsum = cv.take<unsigned long long>((size_t)3 * k * d);
+  t.gcount = cv.take<unsigned>((size_t)3 * k);
+  t.gpart = cv.take<double>((size_t)2 * c->grid_bound);
+}
+
+void kpp_task_scratch(const hpc_ctx *c, Carver &cv, TaskHeader *hd, int64_t s, int L,
+                      hpc_kpp_task &t) {
+  t.bar = &hd->kbar;
+  t.mx = hd->mx;
+  t.phi = hd->phi;
+  t.w = cv.take<float>((size_t)s);
+  t.dc = cv.take<float>((size_t)L * s);
+  t.chunkQ = cv.take<unsigned long long>((size_t)c->grid_bound);
+  t.cand = cv.take<long long>((size_t)L);
+}
+
+int plan_fail(hpc_ctx *c, int rc, const char *what) {
+  if (rc == HPC_ERR_CUDA) return cuda_fail(c, cudaGetLastError(), what);
+  return fail(c, rc, what);
+}
+
+// Launches Lloyd on one sample with scratch carved from `cv`.
 int run_lloyd(hpc_ctx *c, Carver &cv, const float *S, int64_t s, int d, int k, float *C,
               uint8_t *deg, int max_iter, double tol, int32_t *labels, double *f_out,
               int32_t *iters_out) {
-  char *zero_begin = cv.base + ((cv.off + 255) & ~(size_t)255);
-  hpc_gridbar *bar = cv.take<hpc_gridbar>(1);
-  unsigned *gmax = reinterpret_cast<unsigned *>(bar + 1);
-  unsigned long long *gsum = cv.take<unsigned long long>((size_t)3 * k * d);
-  unsigned *gcount = cv.take<unsigned>((size_t)3 * k);
-  char *zero_end = cv.base + cv.off;
-  double *gpart = cv.take<double>((size_t)2 * c->grid_bound);
-  uint8_t *degbuf = deg;
-  if (!degbuf) degbuf = cv.take<uint8_t>((size_t)k);
-  cudaError_t e = cudaMemsetAsync(zero_begin, 0, (size_t)(zero_end - zero_begin), c->stream);
+  TaskHeader *hd = cv.take<TaskHeader>(1);
+  hpc_lloyd_task t{};
+  t.S = S;
+  t.s = s;
+  t.k = k;
+  t.C = C;
+  t.labels = labels;
+  t.f_out = f_out;
+  t.iters_out = iters_out;
+  lloyd_task_scratch(c, cv, hd, d, k, t);
+  t.deg = deg ? deg : cv.take<uint8_t>((size_t)k);
+  cudaError_t e = cudaMemsetAsync(hd, 0, sizeof(TaskHeader), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
-  if (!deg && (e = cudaMemsetAsync(degbuf, 0, (size_t)k, c->stream)) != cudaSuccess)
+  if (!deg && (e = cudaMemsetAsync(t.deg, 0, (size_t)k, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "memset");
-  LloydArgsHost h{};
-  h.S = S;
-  h.s = s;
+  LloydLaunch h{};
+  h.W = 1;
+  h.tasks = &t;
   h.d = d;
-  h.k = k;
-  h.C = C;
-  h.deg = degbuf;
+  h.kmax = k;
   h.max_iter = max_iter;
   h.tol = tol;
-  h.labels = labels;
-  h.f_out = f_out;
-  h.iters_out = iters_out;
-  h.bar = bar;
   h.status = c->dwords;
-  h.gmaxabs = gmax;
-  h.gsum = gsum;
-  h.gcount = gcount;
-  h.gpart = gpart;
-  h.grid_cap = c->grid_bound;
-  int rc = hpc_lloyd_launch(c->L, h);
-  if (rc == HPC_ERR_CUDA) return cuda_fail(c, cudaGetLastError(), "lloyd launch");
-  if (rc) return fail(c, rc, "lloyd: unsupported shape");
+  h.max_blocks = c->grid_bound;
+  h.gpart_cap = 2 * c->grid_bound;
+  int rc = hpc_lloyd_plan(c->L, h);
+  if (rc) return plan_fail(c, rc, "lloyd: unsupported shape");
+  if ((rc = hpc_lloyd_run(c->L, h))) return plan_fail(c, rc, "lloyd launch");
   c->launches += 1;
   return HPC_OK;
 }
 
 int run_kmeanspp(hpc_ctx *c, Carver &cv, const float *S, int64_t s, int d, int k, float *C,
                  uint8_t *deg, int L, uint64_t seed, uint32_t worker, uint32_t round) {
-  char *zero_begin = cv.base + ((cv.off + 255) & ~(size_t)255);
-  hpc_gridbar *bar = cv.take<hpc_gridbar>(1);
-  unsigned *mx = reinterpret_cast<unsigned *>(bar + 1);  // 2 words
-  unsigned long long *phi = cv.take<unsigned long long>((size_t)2 * L);
-  char *zero_end = cv.base + cv.off;
-  float *w = cv.take<float>((size_t)s);
-  float *dc = cv.take<float>((size_t)L * s);
-  unsigned long long *chunkQ = cv.take<unsigned long long>((size_t)c->grid_bound);
-  long long *cand = cv.take<long long>((size_t)L);
-  cudaError_t e = cudaMemsetAsync(zero_begin, 0, (size_t)(zero_end - zero_begin), c->stream);
+  TaskHeader *hd = cv.take<TaskHeader>(1);
+  hpc_kpp_task t{};
+  t.S = S;
+  t.s = s;
+  t.k = k;
+  t.worker = worker;
+  t.C = C;
+  t.deg = deg;
+  kpp_task_scratch(c, cv, hd, s, L, t);
+  cudaError_t e = cudaMemsetAsync(hd, 0, sizeof(TaskHeader), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
-  KppArgsHost h{};
-  h.S = S;
-  h.s = s;
+  KppLaunch h{};
+  h.W = 1;
+  h.tasks = &t;
   h.d = d;
-  h.k = k;
-  h.C = C;
-  h.deg = deg;
+  h.kmax = k;
   h.L = L;
   h.seed = seed;
-  h.worker = worker;
   h.round = round;
-  h.bar = bar;
   h.status = c->dwords;
-  h.w = w;
-  h.dc = dc;
-  h.chunkQ = chunkQ;
-  h.cand = cand;
-  h.phi = phi;
-  h.mx = mx;
-  h.grid_cap = c->grid_bound;
-  int rc = hpc_kmeanspp_launch(c->L, h);
-  if (rc == HPC_ERR_CUDA) return cuda_fail(c, cudaGetLastError(), "kmeanspp launch");
-  if (rc) return fail(c, rc, "kmeanspp: unsupported shape");
+  h.max_blocks = c->grid_bound;
+  h.chunk_cap = c->grid_bound;
+  int rc = hpc_kmeanspp_plan(c->L, h);
+  if (rc) return plan_fail(c, rc, "kmeanspp: unsupported shape");
+  if ((rc = hpc_kmeanspp_run(c->L, h))) return plan_fail(c, rc, "kmeanspp launch");
   c->launches += 1;
   return HPC_OK;
 }
@@ -205,44 +239,88 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
   return HPC_OK;
 }
 
-// Cooperative base selection and incumbent rule (Algorithms 3 and 4).
-__global__ void base_select_kernel(const double *__restrict__ fhat_snap, const int32_t *__restrict__ peers,
-                                   int npeers, int self, const float *__restrict__ C_snap,
-                                   const uint8_t *__restrict__ deg_snap, const int64_t *__restrict__ coff,
-                                   const int64_t *__restrict__ koff, int kd, int k, float *__restrict__ C_base,
-                                   uint8_t *__restrict__ deg_base) {
-  __shared__ int s_b;
-  if (threadIdx.x == 0) {
-    int b = self;
-    for (int p = 0; p < npeers; ++p) {
-      const int v = peers[p];
-      if (fhat_snap[v] < fhat_snap[b] || (fhat_snap[v] == fhat_snap[b] && v < b)) b = v;
+// One worker of a batched round, as the base-selection and incumbent
+// kernels see it.
+struct RoundWorker {
+  int64_t s;
+  int64_t C_off, K_off;
+  int k, group;
+  float *Cn;    // base, then Lloyd's result
+  uint8_t *dn;
+  double *fw;   // Lloyd objective (NaN until written)
+  int32_t *itw;
+};
+
+// Base of every worker (Algorithm 3: its own incumbent; Algorithm 4: the
+// incumbent with the smallest objective per sample point among the workers
+// of its group with its k, lowest index on ties).  All bases are read before
+// any incumbent of this round changes, which is the round-start snapshot.
+__global__ void __launch_bounds__(256) base_select_kernel(const RoundWorker *__restrict__ wk, int W,
+                                                          int cooperative, const double *__restrict__ fhat,
+                                                          const float *__restrict__ Cpool,
+                                                          const uint8_t *__restrict__ Kpool, int d) {
+  __shared__ double s_f[256];
+  __shared__ int s_v[256];
+  const int w = blockIdx.x;
+  const RoundWorker me = wk[w];
+  double bf = fhat[w];
+  int bv = w;
+  if (cooperative) {
+    for (int v = threadIdx.x; v < W; v += blockDim.x) {
+      const RoundWorker o = wk[v];
+      if (o.group != me.group || o.k != me.k) continue;
+      const double f = fhat[v];
+      if (f < bf || (f == bf && v < bv)) {
+        bf = f;
+        bv = v;
+      }
     }
-    s_b = b;
   }
+  s_f[threadIdx.x] = bf;
+  s_v[threadIdx.x] = bv;
   __syncthreads();
-  const int b = s_b;
-  for (int e = threadIdx.x; e < kd; e += blockDim.x) C_base[e] = C_snap[coff[b] + e];
-  for (int j = threadIdx.x; j < k; j += blockDim.x) deg_base[j] = deg_snap[koff[b] + j];
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      const double f = s_f[threadIdx.x + h];
+      const int v = s_v[threadIdx.x + h];
+      if (f < s_f[threadIdx.x] || (f == s_f[threadIdx.x] && v < s_v[threadIdx.x])) {
+        s_f[threadIdx.x] = f;
+        s_v[threadIdx.x] = v;
+      }
+    }
+    __syncthreads();
+  }
+  const int b = s_v[0];
+  const int64_t coff = wk[b].C_off, koff = wk[b].K_off;
+  const int kd = me.k * d;
+  for (int e = threadIdx.x; e < kd; e += blockDim.x) me.Cn[e] = Cpool[coff + e];
+  for (int j = threadIdx.x; j < me.k; j += blockDim.x) me.dn[j] = Kpool[koff + j];
+  if (threadIdx.x == 0) {
+    *me.fw = __longlong_as_double(0x7ff8000000000000ll);  // a failed run is never accepted
+    *me.itw = 0;
+  }
 }
 
-__global__ void incumbent_kernel(const double *__restrict__ f, int64_t s, double *__restrict__ fhat,
-                                 const float *__restrict__ C_new, const uint8_t *__restrict__ deg_new,
-                                 float *__restrict__ C_w, uint8_t *__restrict__ deg_w, int kd, int k,
-                                 double *f_new_out, int32_t *iters_out, const int32_t *iters,
-                                 uint8_t *acc_out) {
-  const double per = *f / (double)s;
-  const bool acc = per < *fhat;
-  for (int e = threadIdx.x; e < kd; e += blockDim.x)
-    if (acc) C_w[e] = C_new[e];
-  for (int j = threadIdx.x; j < k; j += blockDim.x)
-    if (acc) deg_w[j] = deg_new[j];
-  __syncthreads();
+// Incumbent rule of Algorithms 3-4: replace C_w when f / s_w < fhat_w.
+__global__ void __launch_bounds__(256) incumbent_kernel(const RoundWorker *__restrict__ wk, int d,
+                                                        double *__restrict__ fhat, float *__restrict__ Cpool,
+                                                        uint8_t *__restrict__ Kpool, double *f_new,
+                                                        int32_t *iters, uint8_t *accepted) {
+  const int w = blockIdx.x;
+  const RoundWorker me = wk[w];
+  const double f = *me.fw;
+  const double per = f / (double)me.s;
+  const bool acc = per < fhat[w];
+  if (acc) {
+    const int kd = me.k * d;
+    for (int e = threadIdx.x; e < kd; e += blockDim.x) Cpool[me.C_off + e] = me.Cn[e];
+    for (int j = threadIdx.x; j < me.k; j += blockDim.x) Kpool[me.K_off + j] = me.dn[j];
+  }
   if (threadIdx.x == 0) {
-    if (acc) *fhat = per;
-    if (f_new_out) *f_new_out = *f;
-    if (iters_out) *iters_out = *iters;
-    if (acc_out) *acc_out = acc ? 1 : 0;
+    if (acc) fhat[w] = per;
+    if (f_new) f_new[w] = f;
+    if (iters) iters[w] = *me.itw;
+    if (accepted) accepted[w] = acc ? 1 : 0;
   }
 }
 
@@ -250,7 +328,44 @@ __global__ void incumbent_kernel(const double *__restrict__ f, int64_t s, double
 // wait gives up after limit_ns and records HPC_ERR_TIMEOUT.
 __global__ void selftest_timeout_kernel(hpc_gridbar *bar, int *status, uint64_t limit_ns) {
   if (blockIdx.x == 1) return;
-  hpc_grid_sync(bar, status, limit_ns);
+  hpc_grid_sync(bar, status, 2u, limit_ns);
+}
+
+// Pinned host slot `slot` of the staging ring, at least `bytes` long; waits
+// for the copy issued from it last time.
+int stage_acquire(hpc_ctx *c, int slot, size_t bytes, char **out) {
+  cudaError_t e;
+  if (c->stage_used[slot]) {
+    if ((e = cudaEventSynchronize(c->stage_ev[slot])) != cudaSuccess)
+      return cuda_fail(c, e, "staging wait");
+    c->stage_used[slot] = false;
+  }
+  if (c->stage_bytes[slot] < bytes) {
+    if (c->stage_host[slot]) cudaFreeHost(c->stage_host[slot]);
+    c->stage_host[slot] = nullptr;
+    c->stage_bytes[slot] = 0;
+    const size_t want = std::max(bytes, (size_t)1 << 16);
+    if ((e = cudaHostAlloc(&c->stage_host[slot], want, cudaHostAllocDefault)) != cudaSuccess) {
+      cudaGetLastError();
+      c->stage_host[slot] = nullptr;
+      return fail(c, HPC_ERR_NOMEM, "pinned staging allocation failed");
+    }
+    c->stage_bytes[slot] = want;
+  }
+  if (!c->stage_ev[slot] &&
+      (e = cudaEventCreateWithFlags(&c->stage_ev[slot], cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(c, e, "event");
+  *out = static_cast<char *>(c->stage_host[slot]);
+  return HPC_OK;
+}
+
+// Marks the copies just issued from `slot`; the next call uses the next slot.
+int stage_release(hpc_ctx *c, int slot) {
+  const cudaError_t e = cudaEventRecord(c->stage_ev[slot], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "event record");
+  c->stage_used[slot] = true;
+  c->stage_next = (slot + 1) % 4;
+  return HPC_OK;
 }
 
 }  // namespace
@@ -294,6 +409,10 @@ int hpc_destroy(hpc_ctx *c) {
   cudaStreamSynchronize(c->stream);
   if (c->ws) cudaFree(c->ws);
   if (c->dwords) cudaFree(c->dwords);
+  for (int i = 0; i < 4; ++i) {
+    if (c->stage_host[i]) cudaFreeHost(c->stage_host[i]);
+    if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
+  }
   delete c;
   return HPC_OK;
 }
@@ -388,7 +507,7 @@ int hpc_lloyd(hpc_ctx *c, const float *S, int64_t s, int32_t d, int32_t k, float
   if (prec != HPC_FP32) return fail(c, HPC_ERR_UNSUPPORTED, "only HPC_FP32 is built");
   if (!aligned16(S) || !aligned16(C_inout)) return fail(c, HPC_ERR_ARG, "unaligned");
   cudaSetDevice(c->device);
-  if (int rc = ensure_ws(c, lloyd_ws(c, s, d, k))) return rc;
+  if (int rc = ensure_ws(c, lloyd_ws(c, d, k))) return rc;
   Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
   return run_lloyd(c, cv, S, s, d, k, C_inout, degenerate_inout, max_iter, rel_tol, labels_out,
                    f_out, iters_out);
@@ -430,8 +549,8 @@ int hpc_round(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch 
               int32_t n_candidates, int32_t prec) {
   if (!c || !b) return HPC_ERR_ARG;
   if (int rc = check_dims(c, d)) return rc;
-  if (n < 1 || !X || b->W < 1 || !b->s || !b->k || !b->C_off || !b->K_off || !b->C ||
-      !b->degenerate || !b->fhat)
+  if (n < 1 || !X || b->W < 1 || b->W > HPC_MAX_WORKERS || !b->s || !b->k || !b->C_off ||
+      !b->K_off || !b->C || !b->degenerate || !b->fhat)
     return fail(c, HPC_ERR_ARG, "malformed batch");
   if (strategy != HPC_COMPETITIVE && strategy != HPC_COOPERATIVE)
     return fail(c, HPC_ERR_ARG, "unknown strategy");
@@ -440,96 +559,145 @@ int hpc_round(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch 
   if (max_iter < 0 || max_iter > HPC_MAX_ITER) return fail(c, HPC_ERR_ARG, "max_iter out of range");
   if (!aligned16(X) || !aligned16(b->C)) return fail(c, HPC_ERR_ARG, "unaligned");
   const int W = b->W;
-  int64_t smax = 0, kmax = 0, poolf = 0, poolk = 0;
+  const int L = n_candidates;
+  int64_t smax = 0;
+  int kmax = 0;
   for (int w = 0; w < W; ++w) {
     if (b->s[w] < 1 || b->k[w] < 1 || b->C_off[w] < 0 || b->K_off[w] < 0 || (b->C_off[w] & 3))
       return fail(c, HPC_ERR_ARG, "malformed batch entry");
     smax = std::max<int64_t>(smax, b->s[w]);
-    kmax = std::max<int64_t>(kmax, b->k[w]);
-    poolf = std::max<int64_t>(poolf, b->C_off[w] + (int64_t)b->k[w] * d);
-    poolk = std::max<int64_t>(poolk, b->K_off[w] + b->k[w]);
+    kmax = std::max<int>(kmax, b->k[w]);
   }
   cudaSetDevice(c->device);
-  // persistent part of the round's scratch, then room for the inner calls
-  const size_t fixed = pad256((size_t)smax * d * 4) + pad256((size_t)smax * 8) +
-                       pad256((size_t)kmax * d * 4) + pad256((size_t)kmax) + pad256(8) +
-                       pad256(4) + pad256((size_t)poolf * 4) + pad256((size_t)poolk) +
-                       pad256((size_t)W * 8) + pad256(((size_t)W * W + W) * 4) +
-                       pad256((size_t)W * 2 * 8) + 4096;
-  const size_t inner =
-      std::max(lloyd_ws(c, smax, d, (int)kmax), kpp_ws(c, smax, n_candidates));
-  if (int rc = ensure_ws(c, fixed + inner)) return rc;
-  Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
-  float *Sw = cv.take<float>((size_t)smax * d);
-  int64_t *idx = cv.take<int64_t>((size_t)smax);
-  float *Cn = cv.take<float>((size_t)kmax * d);
-  uint8_t *dn = cv.take<uint8_t>((size_t)kmax);
-  double *fw = cv.take<double>(1);
-  int32_t *itw = cv.take<int32_t>(1);
-  float *C_snap = cv.take<float>((size_t)poolf);
-  uint8_t *deg_snap = cv.take<uint8_t>((size_t)poolk);
-  double *fhat_snap = cv.take<double>((size_t)W);
-  int32_t *peers_dev = cv.take<int32_t>((size_t)W * W + W);
-  int64_t *offs_dev = cv.take<int64_t>((size_t)W * 2);
-  const size_t inner_off = cv.off;
-  cudaError_t e;
-  std::vector<int32_t> npeers(W, 0);
-  if (strategy == HPC_COOPERATIVE) {
-    if ((e = cudaMemcpyAsync(C_snap, b->C, (size_t)poolf * 4, cudaMemcpyDeviceToDevice, c->stream)) ||
-        (e = cudaMemcpyAsync(deg_snap, b->degenerate, (size_t)poolk, cudaMemcpyDeviceToDevice,
-                             c->stream)) ||
-        (e = cudaMemcpyAsync(fhat_snap, b->fhat, (size_t)W * 8, cudaMemcpyDeviceToDevice, c->stream)))
-      return cuda_fail(c, e, "snapshot");
-    // peers of worker w: the workers of its group with its k (flat W x W)
-    std::vector<int64_t> offs(2 * W);
-    std::vector<int32_t> peers((size_t)W * W, 0);
-    for (int w = 0; w < W; ++w) {
-      offs[w] = b->C_off[w];
-      offs[W + w] = b->K_off[w];
-      const int gw = b->group ? b->group[w] : 0;
-      for (int v = 0; v < W; ++v)
-        if ((b->group ? b->group[v] : 0) == gw && b->k[v] == b->k[w])
-          peers[(size_t)w * W + npeers[w]++] = v;
-    }
-    if ((e = cudaMemcpyAsync(offs_dev, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice,
-                             c->stream)) ||
-        (e = cudaMemcpyAsync(peers_dev, peers.data(), peers.size() * 4, cudaMemcpyHostToDevice,
-                             c->stream)) ||
-        (e = cudaStreamSynchronize(c->stream)))  // host vectors must outlive the copies
-      return cuda_fail(c, e, "peer tables");
-  }
+
+  // ---- scratch: task headers (zeroed), per-worker buffers, tables ----
+  const int nchunks = (W + HPC_ROUND_CHUNK - 1) / HPC_ROUND_CHUNK;
+  size_t need = pad256((size_t)W * sizeof(TaskHeader)) + 4096;
   for (int w = 0; w < W; ++w) {
     const int64_t s = b->s[w];
     const int k = b->k[w];
-    const int kd = k * d;
-    float *Cw = b->C + b->C_off[w];
-    uint8_t *dw = b->degenerate + b->K_off[w];
-    if (int rc = hpc_draw_sample(c, X, n, d, seed, (uint32_t)w, round, s, Sw, idx)) return rc;
-    if (strategy == HPC_COOPERATIVE) {
-      base_select_kernel<<<1, 256, 0, c->stream>>>(fhat_snap, peers_dev + (size_t)w * W, npeers[w], w,
-                                                   C_snap, deg_snap, offs_dev, offs_dev + W, kd, k, Cn,
-                                                   dn);
-    } else {
-      if ((e = cudaMemcpyAsync(Cn, Cw, (size_t)kd * 4, cudaMemcpyDeviceToDevice, c->stream)) ||
-          (e = cudaMemcpyAsync(dn, dw, (size_t)k, cudaMemcpyDeviceToDevice, c->stream)))
-        return cuda_fail(c, e, "base copy");
-    }
-    // NaN until Lloyd writes it: a failed run is never accepted
-    if ((e = cudaMemsetAsync(fw, 0xff, 8, c->stream))) return cuda_fail(c, e, "memset");
-    if (strategy == HPC_COOPERATIVE) c->launches += 1;
-    cv.off = inner_off;
-    if (int rc = run_kmeanspp(c, cv, Sw, s, d, k, Cn, dn, n_candidates, seed, (uint32_t)w, round))
-      return rc;
-    cv.off = inner_off;
-    if (int rc = run_lloyd(c, cv, Sw, s, d, k, Cn, dn, max_iter, rel_tol, nullptr, fw, itw))
-      return rc;
-    incumbent_kernel<<<1, 256, 0, c->stream>>>(fw, s, b->fhat + w, Cn, dn, Cw, dw, kd, k,
-                                               b->f_new ? b->f_new + w : nullptr,
-                                               b->iters ? b->iters + w : nullptr, itw,
-                                               b->accepted ? b->accepted + w : nullptr);
-    if ((e = cudaGetLastError())) return cuda_fail(c, e, "incumbent launch");
-    c->launches += 1;
+    need += pad256((size_t)s * d * 4) + pad256((size_t)k * d * 4) + pad256((size_t)k) +
+            pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
+            pad256((size_t)2 * c->grid_bound * 8) + pad256((size_t)s * 4) +
+            pad256((size_t)L * s * 4) + pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8);
   }
+  const size_t tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) +
+                           pad256((size_t)W * sizeof(RoundWorker)) +
+                           pad256((size_t)W * sizeof(hpc_kpp_task)) +
+                           pad256((size_t)W * sizeof(hpc_lloyd_task)) +
+                           2 * (size_t)nchunks * pad256((size_t)c->grid_bound * 4);
+  need += pad256(W * 16) + tab_bytes + 256;
+  if (int rc = ensure_ws(c, need)) return rc;
+  Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
+  TaskHeader *hdr = cv.take<TaskHeader>((size_t)W);
+  double *fw = cv.take<double>((size_t)W);
+  int32_t *itw = cv.take<int32_t>((size_t)W);
+  // device tables, mirrored byte for byte in a pinned staging slot
+  char *tab_dev = cv.take<char>(tab_bytes);
+  char *tab_host = nullptr;
+  const int slot = c->stage_next;
+  if (int rc = stage_acquire(c, slot, tab_bytes, &tab_host)) return rc;
+  Carver th{tab_host, 0, tab_bytes}, td{tab_dev, 0, tab_bytes};
+  hpc_sample_task *st_h = th.take<hpc_sample_task>((size_t)W);
+  hpc_sample_task *st_d = td.take<hpc_sample_task>((size_t)W);
+  RoundWorker *rw_h = th.take<RoundWorker>((size_t)W);
+  RoundWorker *rw_d = td.take<RoundWorker>((size_t)W);
+  hpc_kpp_task *kt_h = th.take<hpc_kpp_task>((size_t)W);
+  hpc_kpp_task *kt_d = td.take<hpc_kpp_task>((size_t)W);
+  hpc_lloyd_task *lt_h = th.take<hpc_lloyd_task>((size_t)W);
+  hpc_lloyd_task *lt_d = td.take<hpc_lloyd_task>((size_t)W);
+  for (int w = 0; w < W; ++w) {
+    const int64_t s = b->s[w];
+    const int k = b->k[w];
+    float *S = cv.take<float>((size_t)s * d);
+    float *Cn = cv.take<float>((size_t)k * d);
+    uint8_t *dn = cv.take<uint8_t>((size_t)k);
+    st_h[w] = hpc_sample_task{S, nullptr, s, (uint32_t)w};
+    rw_h[w] = RoundWorker{s, b->C_off[w], b->K_off[w], k, b->group ? b->group[w] : 0, Cn, dn,
+                          fw + w, itw + w};
+    hpc_kpp_task &kt = kt_h[w];
+    kt = hpc_kpp_task{};
+    kt.S = S;
+    kt.s = s;
+    kt.k = k;
+    kt.worker = (uint32_t)w;
+    kt.C = Cn;
+    kt.deg = dn;
+    kpp_task_scratch(c, cv, hdr + w, s, L, kt);
+    hpc_lloyd_task &lt = lt_h[w];
+    lt = hpc_lloyd_task{};
+    lt.S = S;
+    lt.s = s;
+    lt.k = k;
+    lt.C = Cn;
+    lt.deg = dn;
+    lt.f_out = fw + w;
+    lt.iters_out = itw + w;
+    lloyd_task_scratch(c, cv, hdr + w, d, k, lt);
+  }
+  // plans of the persistent launches, HPC_ROUND_CHUNK workers each
+  std::vector<KppLaunch> kl(nchunks);
+  std::vector<LloydLaunch> ll(nchunks);
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int w0 = ch * HPC_ROUND_CHUNK, cw = std::min(W - w0, HPC_ROUND_CHUNK);
+    int kk = 0;
+    for (int w = w0; w < w0 + cw; ++w) kk = std::max(kk, b->k[w]);
+    KppLaunch &kh = kl[ch];
+    kh = KppLaunch{};
+    kh.W = cw;
+    kh.tasks = kt_h + w0;
+    kh.block_task_host = th.take<int>((size_t)c->grid_bound);
+    kh.tasks_dev = kt_d + w0;
+    kh.block_task_dev = td.take<int>((size_t)c->grid_bound);
+    kh.d = d;
+    kh.kmax = kk;
+    kh.L = L;
+    kh.seed = seed;
+    kh.round = round;
+    kh.status = c->dwords;
+    kh.max_blocks = c->grid_bound;
+    kh.chunk_cap = c->grid_bound;
+    if (int rc = hpc_kmeanspp_plan(c->L, kh)) return plan_fail(c, rc, "kmeanspp: unsupported shape");
+    LloydLaunch &lh = ll[ch];
+    lh = LloydLaunch{};
+    lh.W = cw;
+    lh.tasks = lt_h + w0;
+    lh.block_task_host = th.take<int>((size_t)c->grid_bound);
+    lh.tasks_dev = lt_d + w0;
+    lh.block_task_dev = td.take<int>((size_t)c->grid_bound);
+    lh.d = d;
+    lh.kmax = kk;
+    lh.max_iter = max_iter;
+    lh.tol = rel_tol;
+    lh.status = c->dwords;
+    lh.max_blocks = c->grid_bound;
+    lh.gpart_cap = 2 * c->grid_bound;
+    if (int rc = hpc_lloyd_plan(c->L, lh)) return plan_fail(c, rc, "lloyd: unsupported shape");
+  }
+
+  if (cv.off > cv.cap || th.off > th.cap) return fail(c, HPC_ERR_NOMEM, "round scratch layout overflow");
+
+  // ---- the round: one memset, one table copy, 3 + 2 * chunks launches ----
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(hdr, 0, (size_t)W * sizeof(TaskHeader), c->stream)) ||
+      (e = cudaMemcpyAsync(tab_dev, tab_host, tab_bytes, cudaMemcpyHostToDevice, c->stream)))
+    return cuda_fail(c, e, "round set-up");
+  if (int rc = stage_release(c, slot)) return rc;
+  if (int rc = hpc_sample_batch_launch(c->L, X, n, d, seed, round, W, st_d, smax))
+    return plan_fail(c, rc, "sample launch");
+  base_select_kernel<<<W, 256, 0, c->stream>>>(rw_d, W, strategy == HPC_COOPERATIVE ? 1 : 0, b->fhat,
+                                               b->C, b->degenerate, d);
+  if ((e = cudaGetLastError())) return cuda_fail(c, e, "base launch");
+  c->launches += 2;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    if (int rc = hpc_kmeanspp_run(c->L, kl[ch])) return plan_fail(c, rc, "kmeanspp launch");
+    if (int rc = hpc_lloyd_run(c->L, ll[ch])) return plan_fail(c, rc, "lloyd launch");
+    c->launches += 2;
+  }
+  incumbent_kernel<<<W, 256, 0, c->stream>>>(rw_d, d, b->fhat, b->C, b->degenerate, b->f_new,
+                                             b->iters, b->accepted);
+  if ((e = cudaGetLastError())) return cuda_fail(c, e, "incumbent launch");
+  c->launches += 1;
   return HPC_OK;
 }
 

@@ -66,10 +66,11 @@ __device__ __forceinline__ uint64_t hpc_scale_word(uint64_t r, uint64_t m) {
 }
 
 // ---------------------------------------------------------------------------
-// Grid-wide barrier for cooperative launches, with a bounded wait.  Returns
-// false (in every thread of the block) when the device status word carries
-// an error, including a wait that ran past HPC_WAIT_LIMIT_NS; the caller
-// then returns.  The barrier words are zeroed before each launch.
+// Barrier over the `nblocks` blocks of a group (the whole grid, or one
+// task's blocks) of a cooperative launch, with a bounded wait.  Returns false
+// (in every thread of the block) when the device status word carries an
+// error, including a wait that ran past the limit; the caller then returns.
+// The barrier words are zeroed before each launch.
 // ---------------------------------------------------------------------------
 struct hpc_gridbar {
   unsigned int arrive;
@@ -100,7 +101,7 @@ __device__ __forceinline__ void hpc_status_set(int *status, int code) {
   atomicCAS(status, 0, code);
 }
 
-static __device__ __noinline__ bool hpc_grid_sync(hpc_gridbar *bar, int *status,
+static __device__ __noinline__ bool hpc_grid_sync(hpc_gridbar *bar, int *status, unsigned nblocks,
                                                   uint64_t limit_ns = HPC_WAIT_LIMIT_NS) {
   __shared__ int s_ok;
   __syncthreads();
@@ -109,7 +110,7 @@ static __device__ __noinline__ bool hpc_grid_sync(hpc_gridbar *bar, int *status,
     const unsigned g = hpc_ld_acquire(&bar->gen);
     __threadfence();
     const unsigned prev = atomicAdd(&bar->arrive, 1u);
-    if (prev == gridDim.x - 1) {
+    if (prev == nblocks - 1) {
       atomicExch(&bar->arrive, 0u);
       __threadfence();
       hpc_st_release(&bar->gen, g + 1);

@@ -1,4 +1,11 @@
 // Host-side launch descriptors of the HPClust kernels (internal).
+//
+// The persistent kernels (Lloyd, K-means++) take a batch of independent
+// problems ("tasks", one per worker): every task gets its own contiguous
+// group of blocks and its own bounded group barrier, so workers with
+// different sample sizes and cluster counts iterate independently inside
+// one cooperative launch.  A batch of one task is passed by value; larger
+// batches live in device memory together with a block -> task map.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -6,30 +13,85 @@
 
 struct hpc_gridbar;
 
+// Largest batch of independent problems one launch takes.
+#define HPC_MAX_TASKS 4096
+
 struct hpc_launch {
   cudaStream_t stream;
   int num_sms;
   int smem_optin;  // max dynamic shared memory per block
 };
 
-struct LloydArgsHost {
+// ---- Lloyd (one task = one sample) ----
+struct hpc_lloyd_task {
   const float *S;
   int64_t s;
-  int d, k;
+  int k;
+  int block0, nblocks;  // filled by the launcher
   float *C;
-  uint8_t *deg;
+  uint8_t *deg;         // never null
+  int32_t *labels;      // nullable
+  double *f_out;
+  int32_t *iters_out;   // nullable
+  hpc_gridbar *bar;     // zero at launch
+  unsigned *gmaxabs;    // zero at launch
+  unsigned long long *gsum;  // 3 * k * d
+  unsigned *gcount;          // 3 * k
+  double *gpart;             // 2 * blocks of the task
+};
+// Lloyd zeroes gsum / gcount itself; bar and gmaxabs must be zero at launch.
+
+struct LloydLaunch {
+  int W;
+  hpc_lloyd_task *tasks;       // host array [W]; block0 / nblocks written by the plan
+  int *block_task_host;        // host [grid] (W > 1), written by the plan
+  const hpc_lloyd_task *tasks_dev;  // device copy of tasks (W > 1), uploaded by the caller
+  const int *block_task_dev;        // device copy of block_task_host (W > 1)
+  int d, kmax;
   int max_iter;
   double tol;
-  int32_t *labels;
-  double *f_out;
-  int32_t *iters_out;
-  hpc_gridbar *bar;
   int *status;
-  unsigned *gmaxabs;
-  unsigned long long *gsum;
-  unsigned *gcount;
-  double *gpart;
-  int64_t grid_cap;  // upper bound on blocks (size of gpart / 2)
+  int64_t max_blocks;          // blocks the caller's scratch allows in total
+  int64_t gpart_cap;           // doubles of gpart reserved per task (2 per block)
+  // written by the plan
+  int64_t grid;
+  size_t smem;
+  int smem_sums;
+};
+
+// ---- K-means++ (one task = one sample) ----
+struct hpc_kpp_task {
+  const float *S;
+  int64_t s;
+  int k;
+  int block0, nblocks;
+  uint32_t worker;
+  float *C;
+  uint8_t *deg;  // never null
+  hpc_gridbar *bar;           // zero at launch
+  unsigned *mx;               // 2 words, zero at launch
+  unsigned long long *phi;    // 2 * L, zero at launch
+  float *w;                   // s
+  float *dc;                  // L * s
+  unsigned long long *chunkQ; // blocks of the task
+  long long *cand;            // L
+};
+
+struct KppLaunch {
+  int W;
+  hpc_kpp_task *tasks;         // host [W]; block0 / nblocks written by the plan
+  int *block_task_host;        // host [grid] (W > 1)
+  const hpc_kpp_task *tasks_dev;
+  const int *block_task_dev;
+  int d, kmax, L;
+  uint64_t seed;
+  uint32_t round;
+  int *status;
+  int64_t max_blocks;
+  int64_t chunk_cap;  // chunkQ entries reserved per task (1 per block)
+  // written by the plan
+  int64_t grid;
+  size_t smem;
 };
 
 struct ObjArgsHost {
@@ -46,34 +108,36 @@ struct ObjArgsHost {
   int64_t max_blocks;
 };
 
-struct KppArgsHost {
-  const float *S;
+// ---- sampling (one task = one worker's sample) ----
+struct hpc_sample_task {
+  float *S;
+  int64_t *idx;
   int64_t s;
-  int d, k;
-  float *C;
-  uint8_t *deg;
-  int L;
-  uint64_t seed;
-  uint32_t worker, round;
-  hpc_gridbar *bar;
-  int *status;
-  float *w;
-  float *dc;
-  unsigned long long *chunkQ;
-  long long *cand;
-  unsigned long long *phi;
-  unsigned *mx;
-  int64_t grid_cap;
+  uint32_t worker;
 };
 
-int hpc_lloyd_launch(const hpc_launch &L, const LloydArgsHost &h);
+// Plan: chooses the kernel variant and the grid, splits the blocks over the
+// tasks (tasks[w].block0 / nblocks, block_task_host).  Run: one cooperative
+// launch; for W > 1 the caller has copied tasks and block_task_host to
+// tasks_dev / block_task_dev on the same stream before it.
+int hpc_lloyd_plan(const hpc_launch &L, LloydLaunch &h);
+int hpc_lloyd_run(const hpc_launch &L, const LloydLaunch &h);
+int hpc_kmeanspp_plan(const hpc_launch &L, KppLaunch &h);
+int hpc_kmeanspp_run(const hpc_launch &L, const KppLaunch &h);
 int hpc_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
 bool hpc_tc_objective_supported(int d, int k, int64_t n);
 int hpc_tc_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
-int hpc_kmeanspp_launch(const hpc_launch &L, const KppArgsHost &h);
 int hpc_sample_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
                       uint32_t worker, uint32_t round, int64_t s, float *S, int64_t *idx);
+// W samples at once; tasks_dev is a device array [W], smax the largest s.
+int hpc_sample_batch_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
+                            uint32_t round, int W, const hpc_sample_task *tasks_dev, int64_t smax);
 
 // Blocks the cooperative kernels may use at most (upper bound for scratch
 // sizing): resident blocks per SM times SMs.
 int64_t hpc_grid_bound(const hpc_launch &L);
+
+// Splits `total` co-resident blocks over W tasks in proportion to their row
+// counts (each task gets at least one block and at most `cap_rows(task)`).
+void hpc_split_blocks(int W, const int64_t *rows, int64_t rows_per_block, int64_t total,
+                      int *block0, int *nblocks);

@@ -10,30 +10,25 @@
 // F = 62 - bitlen(s) - e (2^(e-1) <= max weight < 2^e), so every block, and
 // any reference that follows the same definition, takes the same decisions.
 // Four bounded grid barriers per seeded centroid.
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
 
 #define HPC_MAX_CAND 8
+#define KPP_THREADS 256
 
 namespace {
 
 struct KppArgs {
-  const float *S;
-  int64_t s;
-  int d, k;
-  float *C;
-  uint8_t *deg;
-  int L;
+  int W;
+  hpc_kpp_task single;        // W == 1
+  const hpc_kpp_task *tasks;  // W > 1 (device)
+  const int *block_task;      // W > 1 (device)
+  int d, L;
   uint64_t seed;
-  uint32_t worker, round;
-  hpc_gridbar *bar;
+  uint32_t round;
   int *status;
-  float *w;
-  float *dc;
-  unsigned long long *chunkQ;
-  long long *cand;
-  unsigned long long *phi;
-  unsigned *mx;
 };
 
 template <int THREADS>
@@ -88,15 +83,17 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
   __shared__ unsigned long long s_tgt[HPC_MAX_CAND];
   __shared__ int s_lstar;
 
-  const int k = a.k, d = a.d, L = a.L;
-  const int64_t s = a.s;
-  const int G = gridDim.x;
-  const int64_t lo = s * blockIdx.x / G, hi = s * (blockIdx.x + 1) / G;
+  // this block's task (one worker's sample) and its place in the task's group
+  const hpc_kpp_task tk = a.W == 1 ? a.single : a.tasks[a.block_task[blockIdx.x]];
+  const int k = tk.k, d = a.d, L = a.L;
+  const int64_t s = tk.s;
+  const int G = tk.nblocks, lb = (int)blockIdx.x - tk.block0;
+  const int64_t lo = s * lb / G, hi = s * (lb + 1) / G;
   float *cl = smem;          // k x D live centroids
   float *cr = cl + k * D;    // L x D candidate rows
   uint8_t *flags = reinterpret_cast<uint8_t *>(cr + L * D);  // k: 1 = to be seeded
 
-  for (int j = threadIdx.x; j < k; j += THREADS) flags[j] = a.deg ? a.deg[j] : 1;
+  for (int j = threadIdx.x; j < k; j += THREADS) flags[j] = tk.deg[j];
   __syncthreads();
   int any_deg = 0, any_live = 0;
   for (int j = threadIdx.x; j < k; j += THREADS) {
@@ -108,20 +105,20 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
   if (!any_deg) return;  // nothing to seed (same answer in every block)
   for (int e = threadIdx.x; e < k * D; e += THREADS) {
     const int j = e / D, t = e - j * D;
-    cl[e] = (t < d && !flags[j]) ? a.C[(int64_t)j * d + t] : 0.0f;
+    cl[e] = (t < d && !flags[j]) ? tk.C[(int64_t)j * d + t] : 0.0f;
   }
   __syncthreads();
   if (!any_live) {  // uniform first pick into the lowest slot
-    const uint64_t r = hpc_draw(a.seed, a.worker, a.round, HPC_TAG_SEED, 0);
+    const uint64_t r = hpc_draw(a.seed, tk.worker, a.round, HPC_TAG_SEED, 0);
     const int64_t i0 = (int64_t)hpc_scale_word(r, (uint64_t)s);
     for (int t = threadIdx.x; t < D; t += THREADS) {
-      const float v = t < d ? a.S[i0 * d + t] : 0.0f;
+      const float v = t < d ? tk.S[i0 * d + t] : 0.0f;
       cl[t] = v;
-      if (blockIdx.x == 0 && t < d) a.C[t] = v;
+      if (lb == 0 && t < d) tk.C[t] = v;
     }
     if (threadIdx.x == 0) {
       flags[0] = 0;
-      if (blockIdx.x == 0) a.deg[0] = 0;
+      if (lb == 0) tk.deg[0] = 0;
     }
     __syncthreads();
   }
@@ -132,23 +129,23 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
     unsigned m = 0u;
     for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) {
       float x[D];
-      hpc_load_row<D>(x, a.S + i * d, d);
+      hpc_load_row<D>(x, tk.S + i * d, d);
       float best = __int_as_float(0x7f800000);
       for (int j = 0; j < k; ++j) {
         if (flags[j]) continue;
         best = fminf(best, hpc_dist32_seq<D>(x, cl + j * D));
       }
       if (!(best <= 3.4028234663852886e38f)) best = __int_as_float(0x7fc00000);  // flag non-finite
-      a.w[i] = best;
+      tk.w[i] = best;
       const unsigned b = __float_as_uint(best) & 0x7fffffffu;
       m = b > m ? b : m;
     }
     atomicMax(&s_umax, m);
     __syncthreads();
-    if (threadIdx.x == 0) atomicMax(&a.mx[0], s_umax);
+    if (threadIdx.x == 0) atomicMax(&tk.mx[0], s_umax);
   }
-  if (!hpc_grid_sync(a.bar, a.status)) return;
-  if (__ldcg(&a.mx[0]) >= 0x7f800000u) {
+  if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
+  if (__ldcg(&tk.mx[0]) >= 0x7f800000u) {
     hpc_status_set(a.status, HPC_ERR_NONFINITE);
     return;
   }
@@ -156,21 +153,21 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
   int t = 0;
   for (int j = 0; j < k; ++j) {
     if (!flags[j]) continue;
-    const float M = __uint_as_float(__ldcg(&a.mx[t & 1]));
+    const float M = __uint_as_float(__ldcg(&tk.mx[t & 1]));
     if (!(M > 0.0f)) break;  // every row sits on a live centroid
     const int F = 62 - B - hpc_frexp_exp(M);
     // block sums of the fixed-point weights
     unsigned long long qs = 0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) qs += (unsigned long long)hpc_quant(a.w[i], F);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) qs += (unsigned long long)hpc_quant(tk.w[i], F);
     qs = block_sum_u64<THREADS>(qs, s_u64);
     if (threadIdx.x == 0) {
-      a.chunkQ[blockIdx.x] = qs;
-      if (blockIdx.x == 0) {
-        a.mx[(t + 1) & 1] = 0u;
-        for (int l = 0; l < L; ++l) a.phi[(size_t)((t + 1) & 1) * L + l] = 0ull;
+      tk.chunkQ[lb] = qs;
+      if (lb == 0) {
+        tk.mx[(t + 1) & 1] = 0u;
+        for (int l = 0; l < L; ++l) tk.phi[(size_t)((t + 1) & 1) * L + l] = 0ull;
       }
     }
-    if (!hpc_grid_sync(a.bar, a.status)) return;
+    if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
     // targets and the block owning each: every block scans the per-block
     // sums in parallel (segments of ceil(G / THREADS) blocks per thread)
     if (threadIdx.x < L) s_owner[threadIdx.x] = -1;
@@ -178,18 +175,18 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
       const int seg = (G + THREADS - 1) / THREADS;
       const int g0 = threadIdx.x * seg, g1 = min(G, g0 + seg);
       unsigned long long loc = 0;
-      for (int g = g0; g < g1; ++g) loc += __ldcg(&a.chunkQ[g]);
+      for (int g = g0; g < g1; ++g) loc += __ldcg(&tk.chunkQ[g]);
       unsigned long long Q;
       const unsigned long long incl = block_scan_u64<THREADS>(loc, s_u64, &Q);
       const unsigned long long excl = incl - loc;
       for (int l = 0; l < L; ++l) {
-        const uint64_t r = hpc_draw(a.seed, a.worker, a.round, HPC_TAG_SEED,
+        const uint64_t r = hpc_draw(a.seed, tk.worker, a.round, HPC_TAG_SEED,
                                     1ull + (uint64_t)t * (uint64_t)L + (uint64_t)l);
         const unsigned long long target = hpc_scale_word(r, Q);
         if (excl <= target && target < incl) {  // exactly one thread: its segment holds it
           unsigned long long run = excl;
           for (int g = g0; g < g1; ++g) {
-            const unsigned long long q = __ldcg(&a.chunkQ[g]);
+            const unsigned long long q = __ldcg(&tk.chunkQ[g]);
             if (run + q > target) {
               s_owner[l] = g;
               s_tgt[l] = target - run;
@@ -202,12 +199,12 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
     }
     __syncthreads();
     for (int l = 0; l < L; ++l) {
-      if (s_owner[l] != (int)blockIdx.x) continue;
+      if (s_owner[l] != lb) continue;
       unsigned long long tgt = s_tgt[l];
       long long found = -1;
       for (int64_t base = lo; base < hi; base += THREADS) {
         const int64_t i = base + threadIdx.x;
-        const unsigned long long q = i < hi ? (unsigned long long)hpc_quant(a.w[i], F) : 0ull;
+        const unsigned long long q = i < hi ? (unsigned long long)hpc_quant(tk.w[i], F) : 0ull;
         unsigned long long tot;
         const unsigned long long incl = block_scan_u64<THREADS>(q, s_u64, &tot);
         const int cnt = __syncthreads_count(i < hi && incl <= tgt);
@@ -218,15 +215,15 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
         }
         tgt -= tot;
       }
-      if (threadIdx.x == 0) a.cand[l] = found;
+      if (threadIdx.x == 0) tk.cand[l] = found;
       __syncthreads();
     }
-    if (!hpc_grid_sync(a.bar, a.status)) return;
+    if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
     // candidate potentials phi_l = sum_i q(min(w_i, D(x_i, cand_l)^2))
     for (int e = threadIdx.x; e < L * D; e += THREADS) {
       const int l = e / D, tt = e - l * D;
-      const long long ci = __ldcg(&a.cand[l]);
-      cr[e] = (tt < d && ci >= 0) ? a.S[ci * d + tt] : 0.0f;
+      const long long ci = __ldcg(&tk.cand[l]);
+      cr[e] = (tt < d && ci >= 0) ? tk.S[ci * d + tt] : 0.0f;
     }
     __syncthreads();
     unsigned long long ph[HPC_MAX_CAND];
@@ -234,13 +231,13 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
     for (int l = 0; l < HPC_MAX_CAND; ++l) ph[l] = 0ull;
     for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) {
       float x[D];
-      hpc_load_row<D>(x, a.S + i * d, d);
-      const float wi = a.w[i];
+      hpc_load_row<D>(x, tk.S + i * d, d);
+      const float wi = tk.w[i];
 #pragma unroll
       for (int l = 0; l < HPC_MAX_CAND; ++l) {
         if (l >= L) break;
         const float v = hpc_dist32_seq<D>(x, cr + l * D);
-        a.dc[(int64_t)l * s + i] = v;
+        tk.dc[(int64_t)l * s + i] = v;
         ph[l] += (unsigned long long)hpc_quant(fminf(wi, v), F);
       }
     }
@@ -248,15 +245,15 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
     for (int l = 0; l < HPC_MAX_CAND; ++l) {
       if (l >= L) break;
       const unsigned long long bs = block_sum_u64<THREADS>(ph[l], s_u64);
-      if (threadIdx.x == 0 && bs != 0ull) atomicAdd(&a.phi[(size_t)(t & 1) * L + l], bs);
+      if (threadIdx.x == 0 && bs != 0ull) atomicAdd(&tk.phi[(size_t)(t & 1) * L + l], bs);
     }
-    if (!hpc_grid_sync(a.bar, a.status)) return;
+    if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
     // keep the candidate with the smallest potential (first drawn on ties)
     if (threadIdx.x == 0) {
       int best = 0;
-      unsigned long long bp = __ldcg(&a.phi[(size_t)(t & 1) * L]);
+      unsigned long long bp = __ldcg(&tk.phi[(size_t)(t & 1) * L]);
       for (int l = 1; l < L; ++l) {
-        const unsigned long long p = __ldcg(&a.phi[(size_t)(t & 1) * L + l]);
+        const unsigned long long p = __ldcg(&tk.phi[(size_t)(t & 1) * L + l]);
         if (p < bp) {
           bp = p;
           best = l;
@@ -267,21 +264,21 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
     }
     __syncthreads();
     const int ls = s_lstar;
-    if (blockIdx.x == 0) {
-      for (int tt = threadIdx.x; tt < d; tt += THREADS) a.C[(int64_t)j * d + tt] = cr[ls * D + tt];
-      if (threadIdx.x == 0) a.deg[j] = 0;
+    if (lb == 0) {
+      for (int tt = threadIdx.x; tt < d; tt += THREADS) tk.C[(int64_t)j * d + tt] = cr[ls * D + tt];
+      if (threadIdx.x == 0) tk.deg[j] = 0;
     }
     unsigned m = 0u;
     for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) {
-      const float v = fminf(a.w[i], a.dc[(int64_t)ls * s + i]);
-      a.w[i] = v;
+      const float v = fminf(tk.w[i], tk.dc[(int64_t)ls * s + i]);
+      tk.w[i] = v;
       const unsigned b = __float_as_uint(v);
       m = b > m ? b : m;
     }
     atomicMax(&s_umax, m);
     __syncthreads();
-    if (threadIdx.x == 0) atomicMax(&a.mx[(t + 1) & 1], s_umax);
-    if (!hpc_grid_sync(a.bar, a.status)) return;
+    if (threadIdx.x == 0) atomicMax(&tk.mx[(t + 1) & 1], s_umax);
+    if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
     ++t;
   }
 }
@@ -291,58 +288,80 @@ size_t kpp_smem_bytes(int D, int k, int L) {
 }
 
 template <int D>
-int kpp_launch_t(const hpc_launch &Lc, const KppArgsHost &h) {
-  constexpr int THREADS = 256;
-  auto kern = kmeanspp_kernel<D, THREADS>;
-  const size_t smem = kpp_smem_bytes(D, h.k, h.L);
+int kpp_plan_t(const hpc_launch &Lc, KppLaunch &h) {
+  auto kern = kmeanspp_kernel<D, KPP_THREADS>;
+  const size_t smem = kpp_smem_bytes(D, h.kmax, h.L);
   if (smem > (size_t)Lc.smem_optin) return HPC_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HPC_ERR_CUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, KPP_THREADS, smem) != cudaSuccess ||
       per_sm < 1)
     return HPC_ERR_UNSUPPORTED;
-  int64_t G = (int64_t)per_sm * Lc.num_sms;
-  const int64_t want = (h.s + THREADS - 1) / THREADS;
-  if (G > want) G = want;
-  if (G < 1) G = 1;
-  if (G > h.grid_cap) G = h.grid_cap;
+  int64_t total = (int64_t)per_sm * Lc.num_sms;
+  if (total > h.max_blocks) total = h.max_blocks;
+  if (total > h.chunk_cap * h.W) total = h.chunk_cap * h.W;
+  if (h.W > total || h.W > HPC_MAX_TASKS) return HPC_ERR_UNSUPPORTED;
+  std::vector<int64_t> rows(h.W);
+  std::vector<int> b0(h.W), nb(h.W);
+  for (int w = 0; w < h.W; ++w) rows[w] = h.tasks[w].s;
+  hpc_split_blocks(h.W, rows.data(), KPP_THREADS, total, b0.data(), nb.data());
+  int64_t grid = 0;
+  for (int w = 0; w < h.W; ++w) {
+    if (nb[w] > h.chunk_cap) nb[w] = (int)h.chunk_cap;
+    h.tasks[w].block0 = (int)grid;
+    h.tasks[w].nblocks = nb[w];
+    if (h.W > 1)
+      for (int b = 0; b < nb[w]; ++b) h.block_task_host[grid + b] = w;
+    grid += nb[w];
+  }
+  h.grid = grid;
+  h.smem = smem;
+  return HPC_OK;
+}
+
+template <int D>
+int kpp_run_t(const hpc_launch &Lc, const KppLaunch &h) {
+  auto kern = kmeanspp_kernel<D, KPP_THREADS>;
   KppArgs a;
-  a.S = h.S;
-  a.s = h.s;
+  a.W = h.W;
+  a.single = h.tasks[0];
+  a.tasks = h.tasks_dev;
+  a.block_task = h.block_task_dev;
   a.d = h.d;
-  a.k = h.k;
-  a.C = h.C;
-  a.deg = h.deg;
   a.L = h.L;
   a.seed = h.seed;
-  a.worker = h.worker;
   a.round = h.round;
-  a.bar = h.bar;
   a.status = h.status;
-  a.w = h.w;
-  a.dc = h.dc;
-  a.chunkQ = h.chunkQ;
-  a.cand = h.cand;
-  a.phi = h.phi;
-  a.mx = h.mx;
   void *args[] = {&a};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)G),
-                                                    dim3(THREADS), args, smem, Lc.stream);
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)h.grid),
+                                                    dim3(KPP_THREADS), args, h.smem, Lc.stream);
   return e == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 
 }  // namespace
 
-int hpc_kmeanspp_launch(const hpc_launch &L, const KppArgsHost &h) {
+int hpc_kmeanspp_plan(const hpc_launch &L, KppLaunch &h) {
   if (h.L < 1 || h.L > HPC_MAX_CAND) return HPC_ERR_ARG;
   switch (hpc_pad_dim(h.d)) {
-    case 2: return kpp_launch_t<2>(L, h);
-    case 4: return kpp_launch_t<4>(L, h);
-    case 8: return kpp_launch_t<8>(L, h);
-    case 16: return kpp_launch_t<16>(L, h);
-    case 32: return kpp_launch_t<32>(L, h);
-    case 64: return kpp_launch_t<64>(L, h);
-    default: return kpp_launch_t<128>(L, h);
+    case 2: return kpp_plan_t<2>(L, h);
+    case 4: return kpp_plan_t<4>(L, h);
+    case 8: return kpp_plan_t<8>(L, h);
+    case 16: return kpp_plan_t<16>(L, h);
+    case 32: return kpp_plan_t<32>(L, h);
+    case 64: return kpp_plan_t<64>(L, h);
+    default: return kpp_plan_t<128>(L, h);
+  }
+}
+
+int hpc_kmeanspp_run(const hpc_launch &L, const KppLaunch &h) {
+  switch (hpc_pad_dim(h.d)) {
+    case 2: return kpp_run_t<2>(L, h);
+    case 4: return kpp_run_t<4>(L, h);
+    case 8: return kpp_run_t<8>(L, h);
+    case 16: return kpp_run_t<16>(L, h);
+    case 32: return kpp_run_t<32>(L, h);
+    case 64: return kpp_run_t<64>(L, h);
+    default: return kpp_run_t<128>(L, h);
   }
 }

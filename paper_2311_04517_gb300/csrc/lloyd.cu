@@ -11,29 +11,23 @@
 // reads the same sums and objective partials, takes the same stop decision
 // and computes the same new centroids (no second barrier).  The global sum
 // buffers rotate over three slots so that zeroing never races a reader.
+#include <vector>
+
 #include "assign.cuh"
 #include "kernels.h"
 
 namespace {
 
 struct LloydArgs {
-  const float *S;
-  int64_t s;
-  int d, k;
-  float *C;
-  uint8_t *deg;
+  int W;
+  hpc_lloyd_task single;        // W == 1
+  const hpc_lloyd_task *tasks;  // W > 1 (device)
+  const int *block_task;        // W > 1: task of every block (device)
+  int d;
   int max_iter;
   double tol;
-  int32_t *labels;
-  double *f_out;
-  int32_t *iters_out;
-  hpc_gridbar *bar;
   int *status;
-  unsigned *gmaxabs;
-  unsigned long long *gsum;  // 3 * k * d
-  unsigned *gcount;          // 3 * k
-  double *gpart;             // 2 * gridDim.x
-  int smem_sums;             // 1: per-block sums in shared memory
+  int smem_sums;  // 1: per-block sums in shared memory
 };
 
 // Objective: several rows per thread amortise the centroid reads.
@@ -81,9 +75,11 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   __shared__ unsigned s_umax;
   constexpr int LPR = LTile<D>::LPR, RPP = LTile<D>::RPP, TPL = LTile<D>::TPL, NB = LTile<D>::NB;
 
-  const int k = a.k, d = a.d;
-  const int64_t s = a.s;
-  const int G = gridDim.x;
+  // this block's task (one worker's sample) and its place in the task's group
+  const hpc_lloyd_task tk = a.W == 1 ? a.single : a.tasks[a.block_task[blockIdx.x]];
+  const int k = tk.k, d = a.d;
+  const int64_t s = tk.s;
+  const int G = tk.nblocks, lb = (int)blockIdx.x - tk.block0;
   const LloydSmem L(D, R, THREADS, k, d, a.smem_sums != 0);
   hpc_cent_smem cs;
   hpc_cent_bind(cs, smem_raw, D, k);
@@ -99,30 +95,34 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   // Phase 0: largest |x| of the sample (sets the fixed-point grid and
   // detects non-finite rows: NaN/inf bit patterns compare above finite).
   if (threadIdx.x == 0) s_umax = 0u;
-  for (int j = threadIdx.x; j < cs.kp; j += THREADS) dead[j] = (j >= k) || (a.deg && a.deg[j]);
+  for (int j = threadIdx.x; j < cs.kp; j += THREADS) dead[j] = (j >= k) || tk.deg[j] != 0;
+  // sum slots 0 and 1 start at zero (slot 2 is cleared in iteration 0)
+  for (int64_t e = (int64_t)lb * THREADS + threadIdx.x; e < 2ll * k * d; e += (int64_t)G * THREADS)
+    tk.gsum[e] = 0ull;
+  for (int e = lb * THREADS + threadIdx.x; e < 2 * k; e += G * THREADS) tk.gcount[e] = 0u;
   __syncthreads();
   {
     unsigned m = 0u;
-    for (int64_t g = blockIdx.x; g < ngroups; g += G) {
+    for (int64_t g = lb; g < ngroups; g += G) {
       const int64_t e1 = min((g + 1) * TR, s) * d;
       for (int64_t e = g * TR * d + threadIdx.x; e < e1; e += THREADS) {
-        const unsigned b = __float_as_uint(a.S[e]) & 0x7fffffffu;
+        const unsigned b = __float_as_uint(tk.S[e]) & 0x7fffffffu;
         m = b > m ? b : m;
       }
     }
     atomicMax(&s_umax, m);
     __syncthreads();
-    if (threadIdx.x == 0) atomicMax(a.gmaxabs, s_umax);
+    if (threadIdx.x == 0) atomicMax(tk.gmaxabs, s_umax);
   }
   constexpr int CS = hpc_cstride(D);
   for (int e = threadIdx.x; e < cs.kp * CS; e += THREADS) {
     const int j = e / CS, t = e - j * CS;
-    cs.cm[e] = (j < k && t < d) ? -2.0f * a.C[(int64_t)j * d + t] : 0.0f;
+    cs.cm[e] = (j < k && t < d) ? -2.0f * tk.C[(int64_t)j * d + t] : 0.0f;
   }
   __syncthreads();
   hpc_cent_finish<D>(cs, k, s_red, [&](int j) { return dead[j] != 0; });
-  if (!hpc_grid_sync(a.bar, a.status)) return;
-  const unsigned mabs = __ldcg(a.gmaxabs);
+  if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
+  const unsigned mabs = __ldcg(tk.gmaxabs);
   if (mabs >= 0x7f800000u) {
     hpc_status_set(a.status, HPC_ERR_NONFINITE);
     return;
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   double f_prev = 0.0;
   for (int it = 0;; ++it) {
     const int buf = it % 3;
-    unsigned long long *gs = a.gsum + (size_t)buf * k * d;
-    unsigned *gc = a.gcount + (size_t)buf * k;
+    unsigned long long *gs = tk.gsum + (size_t)buf * k * d;
+    unsigned *gc = tk.gcount + (size_t)buf * k;
     unsigned long long *acc_sum = a.smem_sums ? ssum : gs;
     unsigned *acc_cnt = a.smem_sums ? scnt : gc;
     if (a.smem_sums) {
@@ -151,16 +151,16 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
     __syncthreads();
     // Phase A: assignment, then accumulation with lanes over dimensions
     double fpart = 0.0;
-    for (int64_t g = blockIdx.x; g < ngroups; g += G) {
+    for (int64_t g = lb; g < ngroups; g += G) {
       const int64_t base = g * TR;
       int lab[R];
       bool valid[R];
-      fpart += (double)hpc_assign_group<D, R, THREADS, PACKED>(a.S, s, d, base, cs, lab, valid,
+      fpart += (double)hpc_assign_group<D, R, THREADS, PACKED>(tk.S, s, d, base, cs, lab, valid,
                                                                a.status);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         wlab[r * THREADS + threadIdx.x] = valid[r] ? lab[r] : -1;
-        if (valid[r] && a.labels) a.labels[base + (int64_t)r * THREADS + threadIdx.x] = lab[r];
+        if (valid[r] && tk.labels) tk.labels[base + (int64_t)r * THREADS + threadIdx.x] = lab[r];
       }
       __syncwarp();
       // lane (rsub, t0) takes dimensions t0, t0 + LPR, ... of rows
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
           for (int i = 0; i < NB; ++i) {
             const int rr = rsub + RPP * (b0 + i);
             jj[i] = (b0 + i < 32 / RPP) ? wl[rr] : -1;
-            const float *xr = a.S + (row0 + rr) * d;
+            const float *xr = tk.S + (row0 + rr) * d;
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {
               const int t = t0 + u * LPR;
@@ -210,21 +210,21 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
         if (scnt[j] != 0u) atomicAdd(&gc[j], scnt[j]);
     }
     const double bsum = hpc_block_sum(fpart, s_dsum);
-    if (threadIdx.x == 0) a.gpart[(size_t)(it & 1) * G + blockIdx.x] = bsum;
-    if (!hpc_grid_sync(a.bar, a.status)) return;
+    if (threadIdx.x == 0) tk.gpart[(size_t)(it & 1) * G + lb] = bsum;
+    if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
 
     // Phase B (every block): objective, stop test, new centroids
     {
-      const double f = hpc_block_sum_array(a.gpart + (size_t)(it & 1) * G, G, s_dsum);
+      const double f = hpc_block_sum_array(tk.gpart + (size_t)(it & 1) * G, G, s_dsum);
       if (threadIdx.x == 0) s_f = f;
     }
     __syncthreads();
     const double f = s_f;
     const bool done = (it > 0 && (f_prev == 0.0 || (f_prev - f) < a.tol * f_prev)) || it == a.max_iter;
     if (done) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *a.f_out = f;
-        if (a.iters_out) *a.iters_out = it;
+      if (lb == 0 && threadIdx.x == 0) {
+        *tk.f_out = f;
+        if (tk.iters_out) *tk.iters_out = it;
       }
       return;
     }
@@ -236,18 +236,18 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
       const long long q = (long long)__ldcg(gs + (size_t)j * d + t);
       const float v = (float)(((double)q * qinv) / (double)cnt);
       cs.cm[e] = -2.0f * v;
-      if (blockIdx.x == 0) a.C[(int64_t)j * d + t] = v;
+      if (lb == 0) tk.C[(int64_t)j * d + t] = v;
     }
-    if (blockIdx.x == 0) {  // recycle the slot read two iterations ago
+    if (lb == 0) {  // recycle the slot read two iterations ago
       const int zb = (it + 2) % 3;
-      for (int e = threadIdx.x; e < k * d; e += THREADS) a.gsum[(size_t)zb * k * d + e] = 0ull;
-      for (int j = threadIdx.x; j < k; j += THREADS) a.gcount[(size_t)zb * k + j] = 0u;
+      for (int e = threadIdx.x; e < k * d; e += THREADS) tk.gsum[(size_t)zb * k * d + e] = 0ull;
+      for (int j = threadIdx.x; j < k; j += THREADS) tk.gcount[(size_t)zb * k + j] = 0u;
     }
     __syncthreads();
     for (int j = threadIdx.x; j < k; j += THREADS) {
       if (!dead[j] && __ldcg(gc + j) == 0u) {  // emptied: degenerate for the rest of the run
         dead[j] = 1;
-        if (blockIdx.x == 0) a.deg[j] = 1;
+        if (lb == 0) tk.deg[j] = 1;
       }
     }
     __syncthreads();
@@ -318,11 +318,11 @@ __global__ void __launch_bounds__(THREADS, D <= 16 ? 2 : 1) objective_kernel(Obj
 }
 
 template <int D, bool PACKED>
-int lloyd_launch_t(const hpc_launch &L, const LloydArgsHost &h) {
+int lloyd_plan_t(const hpc_launch &L, LloydLaunch &h) {
   using T = LTile<D>;
   auto kern = lloyd_kernel<D, T::R, T::THREADS, PACKED>;
-  const LloydSmem with(D, T::R, T::THREADS, h.k, h.d, true);
-  const LloydSmem without(D, T::R, T::THREADS, h.k, h.d, false);
+  const LloydSmem with(D, T::R, T::THREADS, h.kmax, h.d, true);
+  const LloydSmem without(D, T::R, T::THREADS, h.kmax, h.d, false);
   const bool smem_sums = with.total <= (size_t)L.smem_optin;
   const size_t smem = smem_sums ? with.total : without.total;
   if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
@@ -332,34 +332,47 @@ int lloyd_launch_t(const hpc_launch &L, const LloydArgsHost &h) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T::THREADS, smem) != cudaSuccess ||
       per_sm < 1)
     return HPC_ERR_UNSUPPORTED;
-  const int64_t TR = (int64_t)T::THREADS * T::R;
-  const int64_t groups = (h.s + TR - 1) / TR;
-  int64_t G = (int64_t)per_sm * L.num_sms;
-  if (G > groups) G = groups;
-  if (G < 1) G = 1;
-  if (h.grid_cap > 0 && G > h.grid_cap) G = h.grid_cap;
+  const int64_t per_task = h.gpart_cap / 2;
+  int64_t total = (int64_t)per_sm * L.num_sms;
+  if (total > h.max_blocks) total = h.max_blocks;
+  if (total > per_task * h.W) total = per_task * h.W;
+  if (h.W > total || h.W > HPC_MAX_TASKS) return HPC_ERR_UNSUPPORTED;
+  std::vector<int64_t> rows(h.W);
+  std::vector<int> b0(h.W), nb(h.W);
+  for (int w = 0; w < h.W; ++w) rows[w] = h.tasks[w].s;
+  hpc_split_blocks(h.W, rows.data(), (int64_t)T::THREADS * T::R, total, b0.data(), nb.data());
+  int64_t grid = 0;
+  for (int w = 0; w < h.W; ++w) {
+    if (nb[w] > per_task) nb[w] = (int)per_task;
+    h.tasks[w].block0 = (int)grid;
+    h.tasks[w].nblocks = nb[w];
+    if (h.W > 1)
+      for (int b = 0; b < nb[w]; ++b) h.block_task_host[grid + b] = w;
+    grid += nb[w];
+  }
+  h.grid = grid;
+  h.smem = smem;
+  h.smem_sums = smem_sums ? 1 : 0;
+  return HPC_OK;
+}
+
+template <int D, bool PACKED>
+int lloyd_run_t(const hpc_launch &L, const LloydLaunch &h) {
+  using T = LTile<D>;
+  auto kern = lloyd_kernel<D, T::R, T::THREADS, PACKED>;
   LloydArgs a;
-  a.S = h.S;
-  a.s = h.s;
+  a.W = h.W;
+  a.single = h.tasks[0];
+  a.tasks = h.tasks_dev;
+  a.block_task = h.block_task_dev;
   a.d = h.d;
-  a.k = h.k;
-  a.C = h.C;
-  a.deg = h.deg;
   a.max_iter = h.max_iter;
   a.tol = h.tol;
-  a.labels = h.labels;
-  a.f_out = h.f_out;
-  a.iters_out = h.iters_out;
-  a.bar = h.bar;
   a.status = h.status;
-  a.gmaxabs = h.gmaxabs;
-  a.gsum = h.gsum;
-  a.gcount = h.gcount;
-  a.gpart = h.gpart;
-  a.smem_sums = smem_sums ? 1 : 0;
+  a.smem_sums = h.smem_sums;
   void *args[] = {&a};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)G),
-                                                    dim3(T::THREADS), args, smem, L.stream);
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)h.grid),
+                                                    dim3(T::THREADS), args, h.smem, L.stream);
   return e == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 
@@ -398,8 +411,13 @@ int objective_launch_t(const hpc_launch &L, const ObjArgsHost &h) {
 }
 
 template <int D>
-int lloyd_dispatch(const hpc_launch &L, const LloydArgsHost &h) {
-  return h.k <= 32 ? lloyd_launch_t<D, true>(L, h) : lloyd_launch_t<D, false>(L, h);
+int lloyd_plan_d(const hpc_launch &L, LloydLaunch &h) {
+  return h.kmax <= 32 ? lloyd_plan_t<D, true>(L, h) : lloyd_plan_t<D, false>(L, h);
+}
+
+template <int D>
+int lloyd_run_d(const hpc_launch &L, const LloydLaunch &h) {
+  return h.kmax <= 32 ? lloyd_run_t<D, true>(L, h) : lloyd_run_t<D, false>(L, h);
 }
 
 template <int D>
@@ -409,15 +427,56 @@ int objective_dispatch(const hpc_launch &L, const ObjArgsHost &h) {
 
 }  // namespace
 
-int hpc_lloyd_launch(const hpc_launch &L, const LloydArgsHost &h) {
+void hpc_split_blocks(int W, const int64_t *rows, int64_t rows_per_block, int64_t total,
+                      int *block0, int *nblocks) {
+  // one block each, then the next block always to the task with the most
+  // rows per block that can still use one (largest first, lowest index on ties)
+  int64_t left = total - W;
+  for (int w = 0; w < W; ++w) nblocks[w] = 1;
+  while (left > 0) {
+    int best = -1;
+    double best_load = 0.0;
+    for (int w = 0; w < W; ++w) {
+      const int64_t need = (rows[w] + rows_per_block - 1) / rows_per_block;
+      if (nblocks[w] >= need) continue;
+      const double load = (double)rows[w] / nblocks[w];
+      if (best < 0 || load > best_load) {
+        best = w;
+        best_load = load;
+      }
+    }
+    if (best < 0) break;
+    ++nblocks[best];
+    --left;
+  }
+  int64_t acc = 0;
+  for (int w = 0; w < W; ++w) {
+    block0[w] = (int)acc;
+    acc += nblocks[w];
+  }
+}
+
+int hpc_lloyd_plan(const hpc_launch &L, LloydLaunch &h) {
   switch (hpc_pad_dim(h.d)) {
-    case 2: return lloyd_dispatch<2>(L, h);
-    case 4: return lloyd_dispatch<4>(L, h);
-    case 8: return lloyd_dispatch<8>(L, h);
-    case 16: return lloyd_dispatch<16>(L, h);
-    case 32: return lloyd_dispatch<32>(L, h);
-    case 64: return lloyd_dispatch<64>(L, h);
-    default: return lloyd_dispatch<128>(L, h);
+    case 2: return lloyd_plan_d<2>(L, h);
+    case 4: return lloyd_plan_d<4>(L, h);
+    case 8: return lloyd_plan_d<8>(L, h);
+    case 16: return lloyd_plan_d<16>(L, h);
+    case 32: return lloyd_plan_d<32>(L, h);
+    case 64: return lloyd_plan_d<64>(L, h);
+    default: return lloyd_plan_d<128>(L, h);
+  }
+}
+
+int hpc_lloyd_run(const hpc_launch &L, const LloydLaunch &h) {
+  switch (hpc_pad_dim(h.d)) {
+    case 2: return lloyd_run_d<2>(L, h);
+    case 4: return lloyd_run_d<4>(L, h);
+    case 8: return lloyd_run_d<8>(L, h);
+    case 16: return lloyd_run_d<16>(L, h);
+    case 32: return lloyd_run_d<32>(L, h);
+    case 64: return lloyd_run_d<64>(L, h);
+    default: return lloyd_run_d<128>(L, h);
   }
 }
 

@@ -40,7 +40,64 @@ __global__ void gather1_kernel(const float *__restrict__ X, int d, int64_t s,
   S[e] = __ldg(X + idx[i] * d + t);
 }
 
+// Batched form for one round: blockIdx.y is the worker.  A block draws the
+// indices of 1024 consecutive sample rows (256 Philox blocks, one per
+// thread) into shared memory, then copies those rows with coalesced loads.
+constexpr int SB_THREADS = 256, SB_ROWS = 4 * SB_THREADS;
+
+template <bool VEC4>
+__global__ void __launch_bounds__(SB_THREADS) sample_batch_kernel(
+    const float *__restrict__ X, int64_t n, int d, uint64_t seed, uint32_t round,
+    const hpc_sample_task *__restrict__ tasks) {
+  __shared__ int64_t s_idx[SB_ROWS];
+  const hpc_sample_task t = tasks[blockIdx.y];
+  const int64_t r0 = (int64_t)blockIdx.x * SB_ROWS;
+  if (r0 >= t.s) return;
+  const int rows = (int)min((int64_t)SB_ROWS, t.s - r0);
+  {
+    uint64_t v[4];
+    hpc_draw_block(seed, t.worker, round, HPC_TAG_SAMPLE, (uint64_t)(r0 / 4) + threadIdx.x, v);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = threadIdx.x * 4 + w;
+      if (i < rows) {
+        const int64_t x = (int64_t)hpc_scale_word(v[w], (uint64_t)n);
+        s_idx[i] = x;
+        if (t.idx) t.idx[r0 + i] = x;
+      }
+    }
+  }
+  __syncthreads();
+  if (VEC4) {
+    const int d4 = d >> 2;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    float4 *S4 = reinterpret_cast<float4 *>(t.S) + r0 * d4;
+    for (int e = threadIdx.x; e < rows * d4; e += SB_THREADS) {
+      const int i = e / d4, c = e - i * d4;
+      S4[e] = __ldg(X4 + s_idx[i] * d4 + c);
+    }
+  } else {
+    float *S = t.S + r0 * d;
+    for (int e = threadIdx.x; e < rows * d; e += SB_THREADS) {
+      const int i = e / d, c = e - i * d;
+      S[e] = __ldg(X + s_idx[i] * d + c);
+    }
+  }
+}
+
 }  // namespace
+
+int hpc_sample_batch_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
+                            uint32_t round, int W, const hpc_sample_task *tasks_dev, int64_t smax) {
+  if (W < 1 || smax < 1) return HPC_OK;
+  if (W > 65535) return HPC_ERR_ARG;
+  const dim3 grid((unsigned)((smax + SB_ROWS - 1) / SB_ROWS), (unsigned)W);
+  if (d % 4 == 0)
+    sample_batch_kernel<true><<<grid, SB_THREADS, 0, L.stream>>>(X, n, d, seed, round, tasks_dev);
+  else
+    sample_batch_kernel<false><<<grid, SB_THREADS, 0, L.stream>>>(X, n, d, seed, round, tasks_dev);
+  return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
+}
 
 int hpc_sample_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
                       uint32_t worker, uint32_t round, int64_t s, float *S, int64_t *idx) {

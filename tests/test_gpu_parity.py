@@ -371,6 +371,33 @@ def test_round_several_workers(ctx, strategy):
         check_round(ctx, X, Xd, batch, strategy, 3, rnd)
 
 
+@pytest.mark.parametrize("strategy", [0, 1])
+def test_round_mixed_k_batch(ctx, strategy):
+    # batching-workload shape at test size: 16 workers, k_w = (10, 25, 50, 100)[w mod 4],
+    # uneven samples, cooperative sharing only among equal k; one launch per phase
+    X = mixture(60000, 32, 50, 5, sd=2.0)
+    Xd = dev(X)
+    rng = np.random.default_rng(9)
+    W = 16
+    s = rng.integers(1500, 6000, W).tolist()
+    k = [(10, 25, 50, 100)[w % 4] for w in range(W)]
+    batch = H.Batch(32, s, k, [0] * W)
+    for rnd in range(3):
+        check_round(ctx, X, Xd, batch, strategy, 17, rnd)
+
+
+def test_round_more_workers_than_one_launch_takes(ctx):
+    # 300 workers: the persistent kernels run in chunks of workers
+    X = mixture(5000, 4, 6, 8)
+    Xd = dev(X)
+    W = 300
+    s = [200 + 7 * (w % 13) for w in range(W)]
+    k = [3 + (w % 3) for w in range(W)]
+    batch = H.Batch(4, s, k, [w % 2 for w in range(W)])
+    for rnd in range(2):
+        check_round(ctx, X, Xd, batch, 1, 23, rnd)
+
+
 # ---------------------------------------------------------------------------
 # Failure detection: a bounded device wait that runs out reports an error
 # ---------------------------------------------------------------------------
