@@ -95,11 +95,12 @@ int64_t hpc_launch_count(hpc_ctx *ctx);
 int hpc_reserve(hpc_ctx *ctx, int64_t bytes);
 
 /* Chooses where hpc_objective runs its nearest-centroid search on the
- * tensor cores (TF32 products with exact rescoring of rows inside the
- * products' error bound) instead of the FP32 CUDA-core form: mode 0 never,
- * 1 wherever built (d in {16, 32, 64, 128}, k <= 128), 2 (default) wherever
- * built with d >= 64.  Both forms return the same labels (each proves its
- * winner or rescores the row exactly) and objectives within rounding. */
+ * tensor cores instead of the FP32 CUDA-core form: mode 0 never; 1 wherever
+ * built (d in {16, 32}: split-TF32 products, three MMAs per K step, row
+ * operand written to tensor memory; d in {64, 128}: TF32 products; k <= 128
+ * for both); 2 (default) for d in {64, 128} only.  Every form proves its
+ * winner against its products' error bound or settles the row exactly, so
+ * all return the same labels and objectives within rounding. */
 int hpc_set_tensor_cores(hpc_ctx *ctx, int mode);
 
 /* ---- the hot path ------------------------------------------------------ */

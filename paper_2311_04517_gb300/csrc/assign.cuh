@@ -139,6 +139,23 @@ __device__ __forceinline__ void hpc_pair_values(const float (&x)[R][D], const hp
   }
 }
 
+__device__ __forceinline__ float hpc_min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Folds four (value, index) keys into the running top-2 (d1 <= d2): the
+// smallest of the four and the second smallest, then the merge.
+__device__ __forceinline__ void hpc_top2_fold4(float &d1, float &d2, float k0, float k1, float k2,
+                                               float k3) {
+  const float a = fminf(k0, k1), b = fmaxf(k0, k1);
+  const float c = fminf(k2, k3), e = fmaxf(k2, k3);
+  const float m = fminf(a, c), s = hpc_min3(b, e, fmaxf(a, c));
+  d2 = hpc_min3(d2, s, fmaxf(d1, m));
+  d1 = fminf(d1, m);
+}
+
 __device__ __forceinline__ float hpc_key(float v, int j) {
   return __int_as_float((__float_as_int(v) & ~31) | j);
 }
@@ -280,6 +297,31 @@ __device__ __noinline__ int hpc_rescore_row(const float *__restrict__ xrow, int 
     }
   }
   return jb < cs.kp ? jb : 0;
+}
+
+// FP32 stage of the exact assignment of one row by one thread (the
+// per-thread form of hpc_rescore_row's first phase): direct form against
+// every live centroid with its relative bound (D + 3) u.  Returns the label,
+// or -1 when the two best are not separated (the caller then settles the
+// row in FP64, warp-cooperatively: FP64 runs at a small fraction of the
+// FP32 rate, so one thread must not walk every centroid in it).
+template <int D>
+__device__ __noinline__ int hpc_exact_row32(const float (&x)[D], const hpc_cent_smem &cs) {
+  float a1 = __int_as_float(0x7f800000), a2 = a1;
+  int ja = 0;
+  for (int j = 0; j < cs.kp; ++j) {
+    if (hpc_is_dead(cs, j)) continue;
+    const float v = hpc_dist32_cm<D>(x, cs.cm + j * hpc_cstride(D));
+    if (v < a1) {
+      a2 = a1;
+      a1 = v;
+      ja = j;
+    } else {
+      a2 = fminf(a2, v);
+    }
+  }
+  const float bound = (float)(D + 3) * HPC_U32 * 1.001f * (a1 + a2);
+  return a2 - a1 > bound ? ja : -1;
 }
 
 // Assigns the R rows of this thread in row group `base` (rows

@@ -27,7 +27,7 @@ struct hpc_ctx {
   void *ws;
   size_t ws_bytes;
   int64_t launches;
-  int use_tc;  // 0 never, 1 wherever built, 2 (default) for d >= 64
+  int use_tc;  // 0 never, 1 wherever built, 2 (default): tensor cores for d >= 64
   // pinned staging ring for the per-round descriptor tables: slot i is
   // rewritten only after the copy issued from it last time has run
   void *stage_host[4];
@@ -117,7 +117,13 @@ size_t kpp_ws(const hpc_ctx *c, int64_t s, int L) {
          pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8) + 256;
 }
 
-size_t obj_ws(const hpc_ctx *c) { return pad256((size_t)c->grid_bound * 8) + 256; }
+// near-tie rows the tensor-core search settles after its main loop, per block
+#define HPC_OBJ_QUEUE_CAP 4096
+
+size_t obj_ws(const hpc_ctx *c) {
+  return pad256((size_t)c->grid_bound * 8) + pad256((size_t)c->L.num_sms * HPC_OBJ_QUEUE_CAP * 8) +
+         512;
+}
 
 // Lloyd scratch of one task (header zeroed by the caller).
 void lloyd_task_scratch(const hpc_ctx *c, Carver &cv, TaskHeader *hd, int d, int k,
@@ -215,7 +221,11 @@ int run_kmeanspp(hpc_ctx *c, Carver &cv, const float *S, int64_t s, int d, int k
 int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, const float *C, int k,
                   const uint8_t *deg, double *f_out, int32_t *labels) {
   double *part = cv.take<double>((size_t)c->grid_bound);
+  int64_t *queue = cv.take<int64_t>((size_t)c->L.num_sms * HPC_OBJ_QUEUE_CAP);
   ObjArgsHost h{};
+  h.queue = queue;
+  h.queue_cap = HPC_OBJ_QUEUE_CAP;
+  h.queue_ctas = c->L.num_sms;
   h.X = X;
   h.n = n;
   h.d = d;
@@ -228,10 +238,17 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
   h.part = part;
   h.done_count = reinterpret_cast<unsigned *>(c->dwords + 1);
   h.max_blocks = c->grid_bound;
-  const bool want_tc = c->use_tc == 1 || (c->use_tc == 2 && d >= 64);
-  int rc = (want_tc && X && aligned16(X) && hpc_tc_objective_supported(d, k, n))
-               ? hpc_tc_objective_launch(c->L, h)
-               : HPC_ERR_UNSUPPORTED;
+  // Tensor-core searches: TF32 with exact resolution for d = 64 / 128 (the
+  // default there); split TF32 for d = 16 / 32 on request (mode 1) -- at
+  // these widths the CUDA-core search is as fast, both bound by their
+  // per-row instruction streams rather than by HBM.
+  int rc = HPC_ERR_UNSUPPORTED;
+  if (c->use_tc != 0 && X && aligned16(X)) {
+    if (c->use_tc == 1 && hpc_tcs_objective_supported(d, k, n))
+      rc = hpc_tcs_objective_launch(c->L, h);
+    else if (hpc_tc_objective_supported(d, k, n) && d >= 64)
+      rc = hpc_tc_objective_launch(c->L, h);
+  }
   if (rc == HPC_ERR_UNSUPPORTED) rc = hpc_objective_launch(c->L, h);
   if (rc == HPC_ERR_CUDA) return cuda_fail(c, cudaGetLastError(), "objective launch");
   if (rc) return fail(c, rc, "objective: unsupported shape");

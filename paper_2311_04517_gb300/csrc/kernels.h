@@ -106,6 +106,11 @@ struct ObjArgsHost {
   double *part;
   unsigned *done_count;
   int64_t max_blocks;
+  // optional: near-tie rows deferred by the split-TF32 search (queue_cap
+  // rows for each of queue_ctas blocks)
+  int64_t *queue;
+  int64_t queue_cap;
+  int64_t queue_ctas;
 };
 
 // ---- sampling (one task = one worker's sample) ----
@@ -127,6 +132,9 @@ int hpc_kmeanspp_run(const hpc_launch &L, const KppLaunch &h);
 int hpc_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
 bool hpc_tc_objective_supported(int d, int k, int64_t n);
 int hpc_tc_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
+// split-TF32 tensor-core search for rows of 16 or 32 floats
+bool hpc_tcs_objective_supported(int d, int k, int64_t n);
+int hpc_tcs_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
 int hpc_sample_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
                       uint32_t worker, uint32_t round, int64_t s, float *S, int64_t *idx);
 // W samples at once; tasks_dev is a device array [W], smax the largest s.

@@ -40,6 +40,22 @@ __device__ __forceinline__ bool hpc_mbar_try_wait(uint64_t *bar, uint32_t parity
   return ok != 0;
 }
 
+// As hpc_mbar_try_wait, but a thread whose phase is not complete yet is
+// suspended (up to hint_ns) until it is, instead of returning at once: the
+// waiting warp takes no issue slots from the others.
+__device__ __forceinline__ bool hpc_mbar_try_wait_sleep(uint64_t *bar, uint32_t parity,
+                                                        uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(hpc_smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for the completion of the phase with the given parity.  Gives up
 // (returns false) when *abort is set by another role, or after limit_ns, in
 // which case it records HPC_ERR_TIMEOUT and sets *abort.
@@ -48,9 +64,9 @@ __device__ __forceinline__ bool hpc_mbar_wait(uint64_t *bar, uint32_t parity, vo
   if (hpc_mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = hpc_globaltimer();
   for (uint32_t n = 1;; ++n) {
-    if (hpc_mbar_try_wait(bar, parity)) return true;
+    if (hpc_mbar_try_wait_sleep(bar, parity, 20000u)) return true;
     if (*abort) return false;
-    if ((n & 63u) == 0u && hpc_globaltimer() - t0 > limit_ns) {
+    if ((n & 7u) == 0u && hpc_globaltimer() - t0 > limit_ns) {
       hpc_status_set(status, HPC_ERR_TIMEOUT);
       *abort = 1;
       return false;

@@ -1,5 +1,6 @@
-"""Tensor-core nearest-centroid search (TF32 split-precision tcgen05 MMAs)
-against the CPU oracle and against the SIMT search.
+"""Tensor-core nearest-centroid searches against the CPU oracle and against
+the SIMT search: split TF32 (three tcgen05 MMAs per K step, row operand in
+tensor memory) for d = 16 / 32, TF32 with exact resolution for d = 64 / 128.
 
 Bars: labels equal the oracle's except near ties (two nearest FP64 distances
 within 1e-6 relative); objectives within 1e-6 relative; the two GPU forms
@@ -77,6 +78,27 @@ def test_tc_near_ties_are_resolved_exactly(ctx):
     lab_o, d1, d2, _ = orc.assign(X, C)
     strict = (d2 - d1) > 1e-12 * d1
     np.testing.assert_array_equal(lab[strict], lab_o[strict])
+
+
+@pytest.mark.parametrize("d", [16, 32])
+def test_tc_margins_across_the_error_window(ctx, d):
+    # rows on a line through the bisector of two centroids, at distances
+    # from it spread over 1e-5 .. 10: their top-2 margins span the split-TF32
+    # error window on both sides
+    rng = np.random.default_rng(d)
+    c0 = rng.uniform(50, 60, d)
+    c1 = c0 + rng.uniform(-1, 1, d) * 0.5
+    far = c0 + 40.0
+    mid = (c0 + c1) / 2
+    u = (c1 - c0) / np.linalg.norm(c1 - c0)
+    t = np.logspace(-5, 1, 4000)
+    t = np.concatenate([t, -t])
+    X = (mid + np.outer(t, u) + rng.standard_normal((t.size, d)) * 1e-6).astype(np.float32)
+    C = np.stack([c0, far, c1]).astype(np.float32)
+    _, lab = run(ctx, X, C, None, True)
+    lab_o, d1, d2, f_o = orc.assign(X, C)
+    away = (d2 - d1) > 1e-6 * d1
+    np.testing.assert_array_equal(lab[away], lab_o[away])
 
 
 def test_tc_tight_clusters_need_rescoring(ctx):
