@@ -50,7 +50,12 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
     p.add_argument("--workload", default="fp32")
-    p.add_argument("--strategy", choices=["competitive", "cooperative"], default="competitive")
+    p.add_argument("--strategy", choices=["competitive", "cooperative", "hybrid"],
+                   default="competitive")
+    p.add_argument("--n-competitive", type=int, default=None,
+                   help="hybrid: rounds of the competitive phase (default: half the run)")
+    p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=2,
+                   help="objective search: 0 CUDA cores, 1 tensor cores wherever built, 2 auto")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
     return p.parse_args()
@@ -157,15 +162,31 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 def dist_count(iters, s, k, n, k_best):
-    return float(sum((int(i) + 1) * int(sw) * int(kw) for i, sw, kw in zip(iters, s, k))) + n * k_best
+    """Distances of one step: every Lloyd assignment pass (iters + 1 per
+    worker) over its sample, plus the full-data objective of each group's
+    best incumbent (k_best: list of their k)."""
+    kb = sum(int(v) for v in k_best) if hasattr(k_best, "__len__") else int(k_best)
+    return float(sum((int(i) + 1) * int(sw) * int(kw) for i, sw, kw in zip(iters, s, k))) + n * kb
+
+
+def group_members(ws):
+    return [np.flatnonzero(ws.group == g) for g in sorted(set(int(v) for v in ws.group))]
 
 
 def workload_config(wl, strategy, args):
+    st = strategy if strategy != "hybrid" else f"hybrid (competitive for {n_comp(args)} rounds)"
     return {"workload": f"{wl.name}: {wl.notes}", "n": wl.n, "d": wl.d, "k": list(wl.k),
-            "workers": wl.W, "s": list(wl.s), "strategy": strategy,
-            "step": "one HPClust round + full-data objective of the incumbent",
+            "workers": wl.W, "s": list(wl.s), "strategy": st,
+            "step": "one HPClust round for every worker + full-data objective of the best "
+                    "incumbent of each sharing group (workers with equal k)",
             "l2": "inputs larger than L2 (X is %.0f MB)" % (wl.n * wl.d * 4 / 1e6),
             "lloyd_max_iter": 300, "lloyd_rel_tol": 1e-4, "kmeanspp_candidates": 3}
+
+
+def n_comp(args):
+    if args.n_competitive is not None:
+        return args.n_competitive
+    return (args.warmup + args.steps) // 2
 
 
 def load_data(wl, device, seed):
@@ -177,24 +198,55 @@ def load_data(wl, device, seed):
 
 
 def cpu_oracle_rate(X_np, wl, ws, strategy, seed, budget_s=12.0, max_rounds=5):
+    """Oracle distances/s on the host cores.  Small workloads: whole steps
+    (round + objectives) from the all-degenerate start.  Workloads whose one
+    oracle step would take minutes: a bounded sample of the same work -- one
+    worker's round (K-means++ and Lloyd on its sample) and the objective over
+    a row subset -- with the distances it evaluated counted."""
     import oracle as orc
     orc.build()
-    st = orc.RoundState(wl.d, ws.s, ws.k, ws.group)
-    strat = orc.COOPERATIVE if strategy == "cooperative" else orc.COMPETITIVE
-    dist = 0.0
+    strat = {"cooperative": orc.COOPERATIVE, "hybrid": orc.HYBRID}.get(strategy, orc.COMPETITIVE)
+    groups = group_members(ws)
+    step_work = sum((10 + 1) * int(s) * int(k) for s, k in zip(ws.s, ws.k)) + wl.n * sum(
+        int(ws.k[g[0]]) for g in groups)
+    if step_work * wl.d < 2e10:
+        st = orc.RoundState(wl.d, ws.s, ws.k, ws.group)
+        dist = 0.0
+        t0 = time.perf_counter()
+        rounds = 0
+        while rounds < max_rounds:
+            res = orc.round_(X_np, st, strat, seed, rounds, n_competitive=max_rounds // 2)
+            kb = []
+            for g in groups:
+                b = int(g[np.argmin(st.fhat[g])])
+                C, deg = st.centroids(b)
+                orc.objective(X_np, C, deg)
+                kb.append(int(ws.k[b]))
+            dist += dist_count(res["iters"], ws.s, ws.k, X_np.shape[0], kb)
+            rounds += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        el = time.perf_counter() - t0
+        return dist / el, el, (f"{rounds} oracle rounds from all-degenerate start "
+                               f"(each: round + full-data objectives), {el:.1f} s"), orc.num_threads()
+    # bounded sample: worker 0's first round, then objective rows until the budget
+    w0 = 0
+    st = orc.RoundState(wl.d, ws.s[:1], ws.k[:1], ws.group[:1])
     t0 = time.perf_counter()
-    rounds = 0
-    while rounds < max_rounds:
-        res = orc.round_(X_np, st, strat, seed, rounds)
-        b = int(np.argmin(st.fhat))
-        C, deg = st.centroids(b)
-        orc.objective(X_np, C, deg)
-        dist += dist_count(res["iters"], ws.s, ws.k, wl.n, int(ws.k[b]))
-        rounds += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
+    res = orc.round_(X_np, st, orc.COMPETITIVE, seed, 0)
+    dist = float((int(res["iters"][0]) + 1) * int(ws.s[w0]) * int(ws.k[w0]))
+    C, deg = st.centroids(0)
+    rows = 0
+    chunk = max(1000, int(2e9 / (wl.d * int(ws.k[w0]))))
+    while time.perf_counter() - t0 < budget_s and rows < X_np.shape[0]:
+        b = min(X_np.shape[0], rows + chunk)
+        orc.objective(X_np[rows:b], C, deg)
+        dist += float(b - rows) * int(ws.k[w0])
+        rows = b
     el = time.perf_counter() - t0
-    return dist / el, el, rounds, orc.num_threads()
+    return dist / el, el, (f"bounded sample: worker 0's first round (s={int(ws.s[w0])}, "
+                           f"k={int(ws.k[w0])}) + objective over {rows} rows, {el:.1f} s"), \
+        orc.num_threads()
 
 
 def run_reference(args):
@@ -206,15 +258,20 @@ def run_reference(args):
     wl = synth.WORKLOADS[args.workload]
     ws = synth.worker_setup(wl)
     X = load_data(wl, "cpu", wl.seed).numpy()
-    strat = orc.COOPERATIVE if args.strategy == "cooperative" else orc.COMPETITIVE
+    strat = {"cooperative": orc.COOPERATIVE, "hybrid": orc.HYBRID}.get(args.strategy,
+                                                                       orc.COMPETITIVE)
     st = orc.RoundState(wl.d, ws.s, ws.k, ws.group)
+    groups = group_members(ws)
 
     def step(r):
-        res = orc.round_(X, st, strat, wl.seed, r)
-        b = int(np.argmin(st.fhat))
-        C, deg = st.centroids(b)
-        orc.objective(X, C, deg)
-        return dist_count(res["iters"], ws.s, ws.k, wl.n, int(ws.k[b]))
+        res = orc.round_(X, st, strat, wl.seed, r, n_competitive=n_comp(args))
+        kb = []
+        for g in groups:
+            b = int(g[np.argmin(st.fhat[g])])
+            C, deg = st.centroids(b)
+            orc.objective(X, C, deg)
+            kb.append(int(ws.k[b]))
+        return dist_count(res["iters"], ws.s, ws.k, wl.n, kb)
 
     for r in range(args.warmup):
         step(r)
@@ -251,22 +308,39 @@ def run_mine(args):
     ws = synth.worker_setup(wl)
     seed = wl.seed + rank            # independent replica per rank
     X = load_data(wl, dev, seed)
-    strategy = H.HPC_COOPERATIVE if args.strategy == "cooperative" else H.HPC_COMPETITIVE
+    strategy = {"cooperative": H.HPC_COOPERATIVE, "hybrid": H.HPC_HYBRID}.get(
+        args.strategy, H.HPC_COMPETITIVE)
     ctx = H.Context(local)
-    batch = H.Batch(wl.d, ws.s, ws.k, ws.group, device=dev)
-    f_sse = torch.zeros(1, dtype=torch.float64, device=dev)
+    ctx.set_tensor_cores(args.tensor_cores)
+    batch = H.Batch(wl.d, ws.s, ws.k, ws.group, device=dev, n_competitive=n_comp(args))
+    groups = group_members(ws)
+    f_sse = torch.zeros(len(groups), dtype=torch.float64, device=dev)
     K, Wm = args.steps, args.warmup
     iters_log = torch.zeros((K, wl.W), dtype=torch.int32, device=dev)
-    best = 0  # single-worker workloads: the incumbent of worker 0
+    best_log = []
+    fhat_host = torch.empty(wl.W, dtype=torch.float64).pin_memory()
+
+    def bests():
+        # the incumbent with the smallest objective per sample point in each
+        # group (one worker: no read-back needed)
+        if wl.W == 1:
+            return [0]
+        fhat_host.copy_(batch.fhat)
+        fh = fhat_host.numpy()
+        return [int(g[np.argmin(fh[g])]) for g in groups]
 
     def step(r, log_row=None, ev=None):
         H.hpc_round(ctx, X, batch, strategy, seed, r)
         if log_row is not None:
             iters_log[log_row].copy_(batch.iters, non_blocking=True)
-        C, deg = batch.centroids(best)
+        bs = bests()
+        if log_row is not None:
+            best_log.append(bs)
         if ev is not None:
             ev[0].record()
-        H.hpc_objective(ctx, X, C, deg, f_out=f_sse)
+        for gi, b in enumerate(bs):
+            C, deg = batch.centroids(b)
+            H.hpc_objective(ctx, X, C, deg, f_out=f_sse[gi:gi + 1])
         if ev is not None:
             ev[1].record()
 
@@ -299,7 +373,8 @@ def run_mine(args):
     ms = start.elapsed_time(end)
     obj_ms = [a.elapsed_time(b) for a, b in evs]
     iters = iters_log.cpu().numpy()
-    dist_total = sum(dist_count(iters[i], ws.s, ws.k, wl.n, int(ws.k[best])) for i in range(K))
+    dist_total = sum(dist_count(iters[i], ws.s, ws.k, wl.n, [int(ws.k[b]) for b in best_log[i]])
+                     for i in range(K))
     if dist_ok:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -312,9 +387,10 @@ def run_mine(args):
     # end to end: host-resident (pinned) data copied in every step, results read back
     E = args.e2e_steps if args.e2e_steps is not None else max(3, min(K, 20))
     X_host = X.cpu().pin_memory()
-    res_host = torch.empty(1 + wl.W, dtype=torch.float64).pin_memory()
+    res_host = torch.empty(len(groups) + wl.W, dtype=torch.float64).pin_memory()
     C_host = torch.empty_like(batch.C, device="cpu").pin_memory()
     e_iters = torch.zeros((E, wl.W), dtype=torch.int32, device=dev)
+    e_best = []
     r0 = Wm + K
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -323,16 +399,20 @@ def run_mine(args):
         X.copy_(X_host, non_blocking=True)
         H.hpc_round(ctx, X, batch, strategy, seed, r0 + i)
         e_iters[i].copy_(batch.iters, non_blocking=True)
-        C, deg = batch.centroids(best)
-        H.hpc_objective(ctx, X, C, deg, f_out=f_sse)
-        res_host[0:1].copy_(f_sse, non_blocking=True)
-        res_host[1:].copy_(batch.fhat, non_blocking=True)
+        bs = bests()
+        e_best.append(bs)
+        for gi, b in enumerate(bs):
+            C, deg = batch.centroids(b)
+            H.hpc_objective(ctx, X, C, deg, f_out=f_sse[gi:gi + 1])
+        res_host[:len(groups)].copy_(f_sse, non_blocking=True)
+        res_host[len(groups):].copy_(batch.fhat, non_blocking=True)
         C_host.copy_(batch.C, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
     e_ms = e0.elapsed_time(e1)
     ei = e_iters.cpu().numpy()
-    e_dist = sum(dist_count(ei[i], ws.s, ws.k, wl.n, int(ws.k[best])) for i in range(E))
+    e_dist = sum(dist_count(ei[i], ws.s, ws.k, wl.n, [int(ws.k[b]) for b in e_best[i]])
+                 for i in range(E))
     if dist_ok:
         t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -343,14 +423,20 @@ def run_mine(args):
     e_value = e_dist / (e_ms / 1e3)
 
     hbm, src = peaks()
-    obj_avg_ms = float(np.mean(obj_ms))
+    obj_avg_ms = float(np.mean(obj_ms)) / len(groups)  # one launch per group per step
     bytes_obj = float(wl.n) * wl.d * 4
     achieved = bytes_obj / (obj_avg_ms / 1e3) / 1e9
+    kb0 = int(ws.k[best_log[0][0]]) if best_log else int(ws.k[0])
+    split = wl.d in (16, 32) and (args.tensor_cores == 1 or
+                                  (args.tensor_cores == 2 and wl.d == 32 and kb0 <= 64))
+    tf32 = args.tensor_cores != 0 and wl.d in (64, 128)
+    obj_kernel = "tcs_objective_kernel" if split else "tc_objective_kernel" if tf32 \
+        else "objective_kernel"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(wl, args.strategy, args),
-            "roofline": {"kernel": "objective_kernel (full-data objective, Eq. 1)",
+            "roofline": {"kernel": f"{obj_kernel} (full-data objective, Eq. 1)",
                          "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "peak_source": f"{src} hbm_gbs", "unit": "GB/s",
                          "frac": achieved / hbm,
@@ -359,15 +445,18 @@ def run_mine(args):
                          "avg_launch_ms": obj_avg_ms},
             "e2e": {"value": e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(X_host.numel() * 4),
-                    "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4)},
+                    "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4 +
+                                              (wl.W * 8 if wl.W > 1 else 0))},
             "gpu_launches": int(launches),
             "clocks": clocks.summary(t0, t1),
             "lloyd_iters_mean": float(iters.mean())}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, el, rounds, cores = cpu_oracle_rate(X.cpu().numpy(), wl, ws, args.strategy, seed)
+        # the host copy for the oracle: whole X up to 2e8 floats, else a row prefix
+        n_host = wl.n if wl.n * wl.d <= 200_000_000 else max(1, 200_000_000 // wl.d)
+        rate, el, sample, cores = cpu_oracle_rate(X[:n_host].cpu().numpy(), wl, ws, args.strategy,
+                                                  seed)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{rounds} oracle rounds from all-degenerate start "
-                                          f"(each: round + full-data objective), {el:.1f} s"}
+                                "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -62,7 +62,9 @@ typedef enum hpc_precision {
 
 typedef enum hpc_strategy {
   HPC_COMPETITIVE = 0, /* Algorithm 3: each worker starts from its own incumbent */
-  HPC_COOPERATIVE = 1  /* Algorithm 4: from the best incumbent of its group */
+  HPC_COOPERATIVE = 1, /* Algorithm 4: from the best incumbent of its group */
+  HPC_HYBRID = 2       /* Algorithm 5: competitive while round < batch->n_competitive,
+                          cooperative afterwards */
 } hpc_strategy;
 
 /* ---- context ----------------------------------------------------------- */
@@ -98,7 +100,8 @@ int hpc_reserve(hpc_ctx *ctx, int64_t bytes);
  * tensor cores instead of the FP32 CUDA-core form: mode 0 never; 1 wherever
  * built (d in {16, 32}: split-TF32 products, three MMAs per K step, row
  * operand written to tensor memory; d in {64, 128}: TF32 products; k <= 128
- * for both); 2 (default) for d in {64, 128} only.  Every form proves its
+ * for both); 2 (default) where it was measured faster on GB300: d = 32 with
+ * k <= 64 (split TF32) and d in {64, 128} (TF32).  Every form proves its
  * winner against its products' error bound or settles the row exactly, so
  * all return the same labels and objectives within rounding. */
 int hpc_set_tensor_cores(hpc_ctx *ctx, int mode);
@@ -194,6 +197,8 @@ typedef struct hpc_batch {
   double *f_new;        /* device [W] (nullable): this round's Lloyd objective */
   int32_t *iters;       /* device [W] (nullable): this round's Lloyd updates */
   uint8_t *accepted;    /* device [W] (nullable): 1 if the incumbent was replaced */
+  int32_t n_competitive; /* HPC_HYBRID: rounds 0 .. n_competitive - 1 form the
+                            competitive phase (Algorithm 5's N1); ignored otherwise */
 } hpc_batch;
 
 /* One HPClust round for every worker of `batch` (one pass of the loop body

@@ -49,6 +49,7 @@
 
 #define ORC_STRAT_COMPETITIVE 0 /* Algorithm 3 */
 #define ORC_STRAT_COOPERATIVE 1 /* Algorithm 4 */
+#define ORC_STRAT_HYBRID 2      /* Algorithm 5: competitive phase, then cooperative */
 
 typedef unsigned __int128 orc_u128;
 
@@ -459,8 +460,13 @@ int orc_round(const float *X, int64_t n, int32_t d, int32_t W, const int64_t *s,
               const int64_t *C_off, uint8_t *deg_pool, const int64_t *K_off,
               double *fhat, int32_t strategy, uint64_t seed, uint32_t round,
               int32_t max_iter, double rel_tol, int32_t L, double *f_new_out,
-              int32_t *iters_out, uint8_t *accepted_out) {
+              int32_t *iters_out, uint8_t *accepted_out, int32_t n_competitive) {
   if (W < 1 || d < 1 || n < 1) return ORC_ERR_ARG;
+  /* Algorithm 5 runs its phases in order over the round counter t_w (the
+   * same for every worker here): the competitive phase while
+   * t_w < n_competitive, the cooperative phase after it. */
+  if (strategy == ORC_STRAT_HYBRID)
+    strategy = (int64_t)round < (int64_t)n_competitive ? ORC_STRAT_COMPETITIVE : ORC_STRAT_COOPERATIVE;
   int64_t pool_f = 0, pool_k = 0;
   for (int32_t w = 0; w < W; ++w) {
     if (s[w] < 1 || k[w] < 1) return ORC_ERR_ARG;

@@ -27,7 +27,7 @@ struct hpc_ctx {
   void *ws;
   size_t ws_bytes;
   int64_t launches;
-  int use_tc;  // 0 never, 1 wherever built, 2 (default): tensor cores for d >= 64
+  int use_tc;  // 0 never, 1 wherever built, 2 (default): where measured faster
   // pinned staging ring for the per-round descriptor tables: slot i is
   // rewritten only after the copy issued from it last time has run
   void *stage_host[4];
@@ -238,13 +238,15 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
   h.part = part;
   h.done_count = reinterpret_cast<unsigned *>(c->dwords + 1);
   h.max_blocks = c->grid_bound;
-  // Tensor-core searches: TF32 with exact resolution for d = 64 / 128 (the
-  // default there); split TF32 for d = 16 / 32 on request (mode 1) -- at
-  // these widths the CUDA-core search is as fast, both bound by their
-  // per-row instruction streams rather than by HBM.
+  // Tensor-core searches (measured on GB300): TF32 with exact resolution
+  // for d = 64 / 128; split TF32 for d = 32 with k <= 64, where it beats the
+  // CUDA-core search (1.5x at k = 25).  At d = 16, or k > 64 with d = 32,
+  // the CUDA-core search is as fast or faster; mode 1 forces the split form.
   int rc = HPC_ERR_UNSUPPORTED;
   if (c->use_tc != 0 && X && aligned16(X)) {
-    if (c->use_tc == 1 && hpc_tcs_objective_supported(d, k, n))
+    const bool split = hpc_tcs_objective_supported(d, k, n) &&
+                       (c->use_tc == 1 || (d == 32 && k <= 64));
+    if (split)
       rc = hpc_tcs_objective_launch(c->L, h);
     else if (hpc_tc_objective_supported(d, k, n) && d >= 64)
       rc = hpc_tc_objective_launch(c->L, h);
@@ -569,12 +571,15 @@ int hpc_round(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch 
   if (n < 1 || !X || b->W < 1 || b->W > HPC_MAX_WORKERS || !b->s || !b->k || !b->C_off ||
       !b->K_off || !b->C || !b->degenerate || !b->fhat)
     return fail(c, HPC_ERR_ARG, "malformed batch");
-  if (strategy != HPC_COMPETITIVE && strategy != HPC_COOPERATIVE)
+  if (strategy != HPC_COMPETITIVE && strategy != HPC_COOPERATIVE && strategy != HPC_HYBRID)
     return fail(c, HPC_ERR_ARG, "unknown strategy");
   if (prec != HPC_FP32) return fail(c, HPC_ERR_UNSUPPORTED, "only HPC_FP32 is built");
   if (n_candidates < 1 || n_candidates > 8) return fail(c, HPC_ERR_ARG, "n_candidates in [1, 8]");
   if (max_iter < 0 || max_iter > HPC_MAX_ITER) return fail(c, HPC_ERR_ARG, "max_iter out of range");
   if (!aligned16(X) || !aligned16(b->C)) return fail(c, HPC_ERR_ARG, "unaligned");
+  // Algorithm 5: the competitive phase, then the cooperative one
+  if (strategy == HPC_HYBRID)
+    strategy = (int64_t)round < (int64_t)b->n_competitive ? HPC_COMPETITIVE : HPC_COOPERATIVE;
   const int W = b->W;
   const int L = n_candidates;
   int64_t smax = 0;

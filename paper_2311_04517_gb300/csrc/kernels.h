@@ -145,7 +145,8 @@ int hpc_sample_batch_launch(const hpc_launch &L, const float *X, int64_t n, int 
 // sizing): resident blocks per SM times SMs.
 int64_t hpc_grid_bound(const hpc_launch &L);
 
-// Splits `total` co-resident blocks over W tasks in proportion to their row
-// counts (each task gets at least one block and at most `cap_rows(task)`).
-void hpc_split_blocks(int W, const int64_t *rows, int64_t rows_per_block, int64_t total,
-                      int *block0, int *nblocks);
+// Splits `total` co-resident blocks over W tasks in proportion to their work
+// (rows when work is null): each task gets at least one block and at most
+// one per rows_per_block of its rows.
+void hpc_split_blocks(int W, const int64_t *rows, const int64_t *work, int64_t rows_per_block,
+                      int64_t total, int *block0, int *nblocks);

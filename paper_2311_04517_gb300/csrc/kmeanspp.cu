@@ -302,10 +302,15 @@ int kpp_plan_t(const hpc_launch &Lc, KppLaunch &h) {
   if (total > h.max_blocks) total = h.max_blocks;
   if (total > h.chunk_cap * h.W) total = h.chunk_cap * h.W;
   if (h.W > total || h.W > HPC_MAX_TASKS) return HPC_ERR_UNSUPPORTED;
-  std::vector<int64_t> rows(h.W);
+  // blocks in proportion to each task's sample rows times the live
+  // centroids its weights start from (at most k)
+  std::vector<int64_t> rows(h.W), work(h.W);
   std::vector<int> b0(h.W), nb(h.W);
-  for (int w = 0; w < h.W; ++w) rows[w] = h.tasks[w].s;
-  hpc_split_blocks(h.W, rows.data(), KPP_THREADS, total, b0.data(), nb.data());
+  for (int w = 0; w < h.W; ++w) {
+    rows[w] = h.tasks[w].s;
+    work[w] = h.tasks[w].s * (int64_t)h.tasks[w].k;
+  }
+  hpc_split_blocks(h.W, rows.data(), work.data(), KPP_THREADS, total, b0.data(), nb.data());
   int64_t grid = 0;
   for (int w = 0; w < h.W; ++w) {
     if (nb[w] > h.chunk_cap) nb[w] = (int)h.chunk_cap;

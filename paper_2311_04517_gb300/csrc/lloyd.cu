@@ -43,7 +43,7 @@ template <int D>
 struct LTile {
   static constexpr int R = 1;
   static constexpr int THREADS = 256;
-  static constexpr int MINB = D <= 16 ? 2 : 1;
+  static constexpr int MINB = D <= 32 ? 2 : 1;
   static constexpr int LPR = D < 32 ? D : 32;          // lanes per row
   static constexpr int RPP = 32 / LPR;                 // rows per pass
   static constexpr int TPL = (D + LPR - 1) / LPR;      // dimensions per lane
@@ -337,10 +337,15 @@ int lloyd_plan_t(const hpc_launch &L, LloydLaunch &h) {
   if (total > h.max_blocks) total = h.max_blocks;
   if (total > per_task * h.W) total = per_task * h.W;
   if (h.W > total || h.W > HPC_MAX_TASKS) return HPC_ERR_UNSUPPORTED;
-  std::vector<int64_t> rows(h.W);
+  // blocks in proportion to each task's distance work (rows x clusters)
+  std::vector<int64_t> rows(h.W), work(h.W);
   std::vector<int> b0(h.W), nb(h.W);
-  for (int w = 0; w < h.W; ++w) rows[w] = h.tasks[w].s;
-  hpc_split_blocks(h.W, rows.data(), (int64_t)T::THREADS * T::R, total, b0.data(), nb.data());
+  for (int w = 0; w < h.W; ++w) {
+    rows[w] = h.tasks[w].s;
+    work[w] = h.tasks[w].s * (int64_t)h.tasks[w].k;
+  }
+  hpc_split_blocks(h.W, rows.data(), work.data(), (int64_t)T::THREADS * T::R, total, b0.data(),
+                   nb.data());
   int64_t grid = 0;
   for (int w = 0; w < h.W; ++w) {
     if (nb[w] > per_task) nb[w] = (int)per_task;
@@ -427,10 +432,11 @@ int objective_dispatch(const hpc_launch &L, const ObjArgsHost &h) {
 
 }  // namespace
 
-void hpc_split_blocks(int W, const int64_t *rows, int64_t rows_per_block, int64_t total,
-                      int *block0, int *nblocks) {
+void hpc_split_blocks(int W, const int64_t *rows, const int64_t *work, int64_t rows_per_block,
+                      int64_t total, int *block0, int *nblocks) {
   // one block each, then the next block always to the task with the most
-  // rows per block that can still use one (largest first, lowest index on ties)
+  // work per block that can still use one (largest first, lowest index on
+  // ties); a task uses at most one block per rows_per_block rows
   int64_t left = total - W;
   for (int w = 0; w < W; ++w) nblocks[w] = 1;
   while (left > 0) {
@@ -439,7 +445,7 @@ void hpc_split_blocks(int W, const int64_t *rows, int64_t rows_per_block, int64_
     for (int w = 0; w < W; ++w) {
       const int64_t need = (rows[w] + rows_per_block - 1) / rows_per_block;
       if (nblocks[w] >= need) continue;
-      const double load = (double)rows[w] / nblocks[w];
+      const double load = (double)(work ? work[w] : rows[w]) / nblocks[w];
       if (best < 0 || load > best_load) {
         best = w;
         best_load = load;

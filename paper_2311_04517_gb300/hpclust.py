@@ -25,7 +25,7 @@ HPC_ERR_NONFINITE = -5
 HPC_ERR_DEGENERATE_ALL = -6
 HPC_ERR_UNSUPPORTED = -7
 HPC_FP32, HPC_BF16, HPC_FP8 = 0, 1, 2
-HPC_COMPETITIVE, HPC_COOPERATIVE = 0, 1
+HPC_COMPETITIVE, HPC_COOPERATIVE, HPC_HYBRID = 0, 1, 2
 
 # The paper's hyperparameters (Section 6.5).
 MAX_ITER = 300
@@ -51,7 +51,7 @@ class hpc_batch(ctypes.Structure):
                 ("K_off", ctypes.c_void_p), ("C", ctypes.c_void_p),
                 ("degenerate", ctypes.c_void_p), ("fhat", ctypes.c_void_p),
                 ("f_new", ctypes.c_void_p), ("iters", ctypes.c_void_p),
-                ("accepted", ctypes.c_void_p)]
+                ("accepted", ctypes.c_void_p), ("n_competitive", ctypes.c_int32)]
 
 
 _lib = None
@@ -231,9 +231,10 @@ def hpc_objective(ctx: Context, X, C, degenerate=None, prec: int = HPC_FP32, f_o
 class Batch:
     """Worker set for hpc_round: host descriptors plus device state."""
 
-    def __init__(self, d: int, s, k, group=None, device=None):
+    def __init__(self, d: int, s, k, group=None, device=None, n_competitive: int = 0):
         import numpy as np
         self.d = d
+        self.n_competitive = int(n_competitive)  # HPC_HYBRID: rounds of the competitive phase
         self.device = device or torch.device("cuda", 0)
         self.s = np.ascontiguousarray(s, dtype=np.int64)
         self.k = np.ascontiguousarray(k, dtype=np.int32)
@@ -260,7 +261,7 @@ class Batch:
         return hpc_batch(self.W, self.s.ctypes.data, self.k.ctypes.data, self.group.ctypes.data,
                          self.C_off.ctypes.data, self.K_off.ctypes.data, self.C.data_ptr(),
                          self.degenerate.data_ptr(), self.fhat.data_ptr(), self.f_new.data_ptr(),
-                         self.iters.data_ptr(), self.accepted.data_ptr())
+                         self.iters.data_ptr(), self.accepted.data_ptr(), self.n_competitive)
 
     def centroids(self, w: int):
         k = int(self.k[w])

@@ -334,7 +334,7 @@ def oracle_state_from(batch):
 
 def check_round(ctx, X, Xd, batch, strategy, seed, rnd):
     st = oracle_state_from(batch)
-    res = orc.round_(X, st, strategy, seed, rnd)
+    res = orc.round_(X, st, strategy, seed, rnd, n_competitive=batch.n_competitive)
     H.hpc_round(ctx, Xd, batch, strategy, seed, rnd)
     ctx.check_status()
     for w in range(batch.W):
@@ -384,6 +384,15 @@ def test_round_mixed_k_batch(ctx, strategy):
     batch = H.Batch(32, s, k, [0] * W)
     for rnd in range(3):
         check_round(ctx, X, Xd, batch, strategy, 17, rnd)
+
+
+def test_round_hybrid_switches_phase(ctx):
+    # Algorithm 5 with N1 = 2: two competitive rounds, then cooperative ones
+    X = mixture(20000, 6, 8, 31, sd=1.1)
+    Xd = dev(X)
+    batch = H.Batch(6, [2000, 3000, 2500, 2000], [5, 5, 5, 7], [0, 0, 0, 0], n_competitive=2)
+    for rnd in range(4):
+        check_round(ctx, X, Xd, batch, H.HPC_HYBRID, 41, rnd)
 
 
 def test_round_more_workers_than_one_launch_takes(ctx):

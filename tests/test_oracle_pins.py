@@ -471,6 +471,32 @@ def test_round_incumbents_never_worsen_and_coop_shares(orc):
     assert np.isfinite(st.fhat).all()
 
 
+@pytest.mark.parametrize("n1", [0, 2, 99])
+def test_hybrid_is_competitive_then_cooperative(orc, n1):
+    # Algorithm 5: rounds below N1 run the competitive phase, the rest the
+    # cooperative one; N1 = 0 is Algorithm 4 throughout, N1 >= rounds is
+    # Algorithm 3 throughout
+    rng = np.random.default_rng(23)
+    X = np.concatenate([rng.normal(c, 0.9, (120, 3)) for c in (-7, -2, 3, 8)]).astype(np.float32)
+    s, k, group = [40, 56, 40, 48], [3, 3, 3, 4], [0, 0, 0, 0]
+    hyb = orc.RoundState(3, s, k, group)
+    ref = orc.RoundState(3, s, k, group)
+    for rnd in range(4):
+        a = orc.round_(X, hyb, orc.HYBRID, seed=9, round_idx=rnd, n_competitive=n1)
+        b = orc.round_(X, ref, orc.COMPETITIVE if rnd < n1 else orc.COOPERATIVE, seed=9,
+                       round_idx=rnd)
+        np.testing.assert_array_equal(hyb.C_pool, ref.C_pool)
+        np.testing.assert_array_equal(hyb.fhat, ref.fhat)
+        assert list(a["iters"]) == list(b["iters"])
+    if n1 == 2:
+        # the cooperative phase really shares: a fresh competitive-only run
+        # from the same state differs in at least one worker's base
+        comp = orc.RoundState(3, s, k, group)
+        for rnd in range(4):
+            orc.round_(X, comp, orc.COMPETITIVE, seed=9, round_idx=rnd)
+        assert not np.array_equal(comp.C_pool, hyb.C_pool)
+
+
 def test_paper_hyperparameters_fixture(orc):
     hp = json.loads((GOLDEN / "paper_hyperparameters.json").read_text())
     assert hp["lloyd_max_iter"] == 300 and hp["lloyd_rel_tol"] == 1e-4
