@@ -255,7 +255,7 @@ def run_reference(args):
         return
     import oracle as orc
     orc.build()
-    wl = synth.WORKLOADS[args.workload]
+    wl = synth.workload(args.workload)
     ws = synth.worker_setup(wl)
     X = load_data(wl, "cpu", wl.seed).numpy()
     strat = {"cooperative": orc.COOPERATIVE, "hybrid": orc.HYBRID}.get(args.strategy,
@@ -304,7 +304,7 @@ def run_mine(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    wl = synth.WORKLOADS[args.workload]
+    wl = synth.workload(args.workload)
     ws = synth.worker_setup(wl)
     seed = wl.seed + rank            # independent replica per rank
     X = load_data(wl, dev, seed)

@@ -182,6 +182,59 @@ __device__ __forceinline__ float row_dist32(const RowRef<D> &r, const float *cm)
   }
 }
 
+// ||x||^2 and the FP32 direct-form distance to centroid j1 of every row of
+// a warp (rows row0 .. row0 + 31, lane l's row is row0 + l), each row read by
+// the whole warp with coalesced loads: lane l takes dimensions
+// [l D / 32, (l + 1) D / 32), then a butterfly sum.  Relative error of the
+// distance: (D / 32 + 6) u, within the (D + 3) u the callers assume.
+template <int D>
+__device__ __forceinline__ void warp_norm_direct(const float *__restrict__ X, int64_t row0,
+                                                 bool valid, int j1, const hpc_cent_smem &cs,
+                                                 float &nx, float &dd) {
+  constexpr int PER = D / 32;
+  constexpr int CS = hpc_cstride(D);
+  const int lane = threadIdx.x & 31;
+  nx = 0.0f;
+  dd = 0.0f;
+#pragma unroll 4
+  for (int src = 0; src < 32; ++src) {
+    const int js = __shfl_sync(0xffffffffu, j1, src);
+    const bool vs = __shfl_sync(0xffffffffu, (int)valid, src) != 0;
+    float px = 0.0f, pd = 0.0f;
+    if (vs) {
+      const float *xr = X + (row0 + src) * D + lane * PER;
+      const float *cm = cs.cm + js * CS + lane * PER;
+      float xv[PER];
+      if constexpr (PER == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(xr));
+        xv[0] = q.x;
+        xv[1] = q.y;
+        xv[2] = q.z;
+        xv[3] = q.w;
+      } else {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(xr));
+        xv[0] = q.x;
+        xv[1] = q.y;
+      }
+#pragma unroll
+      for (int t = 0; t < PER; ++t) {
+        const float diff = __fmaf_rn(0.5f, cm[t], xv[t]);
+        pd = __fmaf_rn(diff, diff, pd);
+        px = __fmaf_rn(xv[t], xv[t], px);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      px += __shfl_xor_sync(0xffffffffu, px, o);
+      pd += __shfl_xor_sync(0xffffffffu, pd, o);
+    }
+    if (lane == src) {
+      nx = px;
+      dd = pd;
+    }
+  }
+}
+
 template <int D, int NP, bool PACKED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_objective_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
@@ -421,7 +474,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!found) j1 = 0;
       // every value is within E of the exact ||c||^2 - 2 x.c; keys add at
       // most 2^-18 |v|
-      const float nx = valid ? row_norm2<D>(xr) : 0.0f;
+      float nx, dd;
+      if constexpr (Cfg::XREG) {
+        nx = valid ? row_norm2<D>(xr) : 0.0f;
+        dd = valid ? row_direct<D>(xr, cs.cm + j1 * CS) : 0.0f;
+      } else {
+        // rows of 256 / 512 bytes: the warp reads each of its 32 rows with
+        // coalesced loads and reduces ||x||^2 and the direct distance to the
+        // row's chosen centroid across its lanes
+        warp_norm_direct<D>(a.X, tg * TC_M + 32 * q, valid, j1, cs, nx, dd);
+      }
       const float rad = sqrtf(nx) * 1.0001f + cs.cmax * 1.0001f;
       float win = 2.0f * 9.765625e-04f * rad * rad;  // 2E, E = 2^-10 (||x|| + max||c||)^2
       if (PACKED) win += 7.7e-6f * (fabsf(d1) + fabsf(d2));
@@ -432,7 +494,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       const bool flag = valid && !(d2 - d1 > win);
       bool need64 = false, need_window = false;
-      float dd = valid ? row_direct<D>(xr, cs.cm + j1 * CS) : 0.0f;
       constexpr float rho = (float)(D + 3) * HPC_U32 * 1.001f;  // FP32 direct-form bound
       if (flag) {
         // the two nearest by the tensor-core values, exactly; every other

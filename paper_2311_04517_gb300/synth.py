@@ -59,6 +59,13 @@ WORKLOADS = {
 }
 
 
+def workload(name: str) -> Workload:
+    """A named workload: one of WORKLOADS, or "scaling<i>" (Section 6.8, i = 0..8)."""
+    if name.startswith("scaling"):
+        return scaling_workload(int(name[len("scaling"):] or 8))
+    return WORKLOADS[name]
+
+
 def mixture_params(wl: Workload, seed: int | None = None):
     """Means (comps x d), sds (comps) and weights (comps), float64 on the CPU."""
     g = torch.Generator().manual_seed(wl.seed if seed is None else seed)
@@ -90,8 +97,10 @@ def make_data(wl: Workload | str, device="cpu", seed: int | None = None, n: int 
               chunk: int = 4_000_000, out: torch.Tensor | None = None) -> torch.Tensor:
     """n x d float32 mixture sample (n defaults to the workload's)."""
     if isinstance(wl, str):
-        wl = WORKLOADS[wl]
+        wl = workload(wl)
     seed = wl.seed if seed is None else seed
+    if wl.means[0] == "scaling":
+        return scaling_data(wl.means[1], device, seed)
     n = wl.n if n is None else n
     device = torch.device(device)
     mu, sd, w = mixture_params(wl, seed)
@@ -112,15 +121,33 @@ def make_data(wl: Workload | str, device="cpu", seed: int | None = None, n: int 
 
 def scaling_data(i: int, device="cpu", seed: int = 0) -> torch.Tensor:
     """Section 6.8 scaling set: 10 blobs in (-40, 40)^10, sd ~ U(0, 10),
-    m = 3^(i+7) points, plus 500 uniform noise points in (-50, 50)^10."""
+    m = 3^(i+7) points, plus 500 uniform noise points in (-50, 50)^10
+    (the noise rows last)."""
     m = 3 ** (i + 7)
+    device = torch.device(device)
     g = torch.Generator().manual_seed(seed)
-    mu = -40 + 80 * torch.rand(10, 10, generator=g, dtype=torch.float64)
-    sd = 10 * torch.rand(10, generator=g, dtype=torch.float64)
-    comp = torch.randint(0, 10, (m,), generator=g)
-    X = (mu[comp] + sd[comp, None] * torch.randn(m, 10, generator=g, dtype=torch.float64))
-    noise = -50 + 100 * torch.rand(500, 10, generator=g, dtype=torch.float64)
-    return torch.cat([X, noise]).to(device=device, dtype=torch.float32)
+    mu = (-40 + 80 * torch.rand(10, 10, generator=g, dtype=torch.float64)).to(device)
+    sd = (10 * torch.rand(10, generator=g, dtype=torch.float64)).to(device)
+    gd = torch.Generator(device=device).manual_seed(int(seed) * 7919 + 3)
+    X = torch.empty((m + 500, 10), dtype=torch.float32, device=device)
+    chunk = 4_000_000
+    for a in range(0, m, chunk):
+        b = min(m, a + chunk)
+        comp = torch.randint(0, 10, (b - a,), generator=gd, device=device)
+        z = torch.randn((b - a, 10), generator=gd, device=device, dtype=torch.float64)
+        X[a:b] = (mu[comp] + sd[comp, None] * z).float()
+    X[m:] = (-50 + 100 * torch.rand((500, 10), generator=gd, device=device,
+                                    dtype=torch.float64)).float()
+    return X
+
+
+def scaling_workload(i: int) -> Workload:
+    """The Section 6.8 experiment as a workload: k = 10 (the blob count),
+    s = min(5000, m - 1000), eight workers (the paper's CPU count)."""
+    m = 3 ** (i + 7)
+    return Workload(f"scaling{i}", m + 500, 10, 10, ("scaling", i), ("uniform", 0.0, 10.0),
+                    "equal", (10,), 8, ("const", min(5000, m - 1000)), 10, 0,
+                    f"Section 6.8 scaling set, m = 3^{i + 7} = {m} points + 500 noise points")
 
 
 @dataclass
@@ -134,7 +161,7 @@ def worker_setup(wl: Workload | str, seed: int | None = None, W: int | None = No
     """Per-worker sample sizes, cluster counts and sharing groups (workers
     with the same k share one group)."""
     if isinstance(wl, str):
-        wl = WORKLOADS[wl]
+        wl = workload(wl)
     W = wl.W if W is None else W
     rng = np.random.default_rng((wl.seed if seed is None else seed) + 1234)
     if wl.s[0] == "const":

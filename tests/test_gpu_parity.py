@@ -407,6 +407,20 @@ def test_round_more_workers_than_one_launch_takes(ctx):
         check_round(ctx, X, Xd, batch, 1, 23, rnd)
 
 
+@pytest.mark.parametrize("i", [0, 1, 2])
+@pytest.mark.parametrize("strategy", [0, 1, 2])
+def test_round_scaling_workload(ctx, i, strategy):
+    # the Section 6.8 scaling set (10 blobs + uniform noise, k = 10,
+    # s = min(5000, m - 1000), eight workers), three rounds of each strategy
+    wl = synth.workload(f"scaling{i}")
+    X = host(synth.make_data(wl))
+    Xd = dev(X)
+    ws = synth.worker_setup(wl)
+    batch = H.Batch(wl.d, ws.s, ws.k, ws.group, n_competitive=1)
+    for rnd in range(3):
+        check_round(ctx, X, Xd, batch, strategy, 7 + i, rnd)
+
+
 # ---------------------------------------------------------------------------
 # Failure detection: a bounded device wait that runs out reports an error
 # ---------------------------------------------------------------------------
