@@ -54,6 +54,9 @@ def parse_args():
                    default="competitive")
     p.add_argument("--n-competitive", type=int, default=None,
                    help="hybrid: rounds of the competitive phase (default: half the run)")
+    p.add_argument("--graph", action="store_true",
+                   help="record one round in a CUDA graph (hpc_round_prepare / enqueue) and "
+                        "replay it every step")
     p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=2,
                    help="objective search: 0 CUDA cores, 1 tensor cores wherever built, 2 auto")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -175,6 +178,8 @@ def group_members(ws):
 
 def workload_config(wl, strategy, args):
     st = strategy if strategy != "hybrid" else f"hybrid (competitive for {n_comp(args)} rounds)"
+    if getattr(args, "graph", False):
+        st += "; each round replayed from one CUDA graph"
     return {"workload": f"{wl.name}: {wl.notes}", "n": wl.n, "d": wl.d, "k": list(wl.k),
             "workers": wl.W, "s": list(wl.s), "strategy": st,
             "step": "one HPClust round for every worker + full-data objective of the best "
@@ -329,8 +334,29 @@ def run_mine(args):
         fh = fhat_host.numpy()
         return [int(g[np.argmin(fh[g])]) for g in groups]
 
+    graph = None
+    graph_launches = 0
+    if args.graph:
+        # one round recorded once; its round index lives on the device and
+        # advances with every replay (rounds 0, 1, 2, ... as below)
+        H.hpc_round_prepare(ctx, X, batch, strategy, seed, 0)
+        side = torch.cuda.Stream(dev)
+        graph = torch.cuda.CUDAGraph()
+        l0 = ctx.launch_count()
+        with torch.cuda.graph(graph, stream=side):
+            ctx.set_stream(side)
+            H.hpc_round_enqueue(ctx)
+        ctx.set_stream(torch.cuda.current_stream(dev))
+        graph_launches = ctx.launch_count() - l0
+
+    def run_round(r):
+        if graph is not None:
+            graph.replay()
+        else:
+            H.hpc_round(ctx, X, batch, strategy, seed, r)
+
     def step(r, log_row=None, ev=None):
-        H.hpc_round(ctx, X, batch, strategy, seed, r)
+        run_round(r)
         if log_row is not None:
             iters_log[log_row].copy_(batch.iters, non_blocking=True)
         bs = bests()
@@ -366,7 +392,7 @@ def run_mine(args):
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     clocks.stop()
-    launches = ctx.launch_count() - launches0
+    launches = ctx.launch_count() - launches0 + graph_launches * K
     st = ctx.sync_status()
     if st != 0:
         raise RuntimeError(f"device status {st}")
@@ -397,7 +423,7 @@ def run_mine(args):
     e0.record()
     for i in range(E):
         X.copy_(X_host, non_blocking=True)
-        H.hpc_round(ctx, X, batch, strategy, seed, r0 + i)
+        run_round(r0 + i)
         e_iters[i].copy_(batch.iters, non_blocking=True)
         bs = bests()
         e_best.append(bs)

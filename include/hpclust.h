@@ -215,6 +215,27 @@ int hpc_round(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
               uint32_t round, int32_t max_iter, double rel_tol,
               int32_t n_candidates, int32_t prec);
 
+/* A round whose set-up is done once: hpc_round_prepare checks the batch,
+ * reserves the round's scratch in memory of its own (later calls on the
+ * context never overwrite it), writes the descriptor tables to the device and
+ * sets a device round counter to round0 (it synchronises the stream).
+ * hpc_round_enqueue then enqueues one round exactly as hpc_round would for
+ * the counter's current value, and the round's last kernel advances the
+ * counter: no host synchronisation, no allocation and no host-to-device copy,
+ * so a stream capture can record it once and a CUDA graph can replay it
+ * round after round (Algorithms 3-5 run the same round body every time).
+ * HPC_HYBRID is resolved on the device from the counter.  The prepared round
+ * reads X, the batch's device arrays and its host descriptors' sizes as they
+ * were at preparation: prepare again after changing any of them.  One
+ * prepared round per context; preparing again replaces it.
+ * Errors: as hpc_round; hpc_round_enqueue returns HPC_ERR_ARG when nothing is
+ * prepared. */
+int hpc_round_prepare(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
+                      const hpc_batch *batch, int32_t strategy, uint64_t seed,
+                      uint32_t round0, int32_t max_iter, double rel_tol,
+                      int32_t n_candidates, int32_t prec);
+int hpc_round_enqueue(hpc_ctx *ctx);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* The full-data objective of hpc_objective (CUDA-core search; same labels,

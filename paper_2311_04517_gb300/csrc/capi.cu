@@ -17,6 +17,8 @@
 #define HPC_ROUND_CHUNK 128
 #define HPC_MAX_WORKERS 65535
 
+struct hpc_round_plan;
+
 struct hpc_ctx {
   int device;
   cudaStream_t stream;
@@ -35,6 +37,12 @@ struct hpc_ctx {
   cudaEvent_t stage_ev[4];
   bool stage_used[4];
   int stage_next;
+  // a prepared round (hpc_round_prepare): its own device memory, so other
+  // calls on the context never overwrite it
+  hpc_round_plan *plan;
+  void *plan_mem;
+  size_t plan_bytes;
+  uint32_t *plan_round;  // device round counter, advanced by every enqueued round
   char err[256];
 };
 
@@ -275,11 +283,17 @@ struct RoundWorker {
 // of its group with its k, lowest index on ties).  All bases are read before
 // any incumbent of this round changes, which is the round-start snapshot.
 __global__ void __launch_bounds__(256) base_select_kernel(const RoundWorker *__restrict__ wk, int W,
-                                                          int cooperative, const double *__restrict__ fhat,
+                                                          int strategy, int32_t n_competitive,
+                                                          const uint32_t *round_dev, uint32_t round,
+                                                          const double *__restrict__ fhat,
                                                           const float *__restrict__ Cpool,
                                                           const uint8_t *__restrict__ Kpool, int d) {
   __shared__ double s_f[256];
   __shared__ int s_v[256];
+  // Algorithm 5: the competitive phase for rounds below n_competitive
+  const uint32_t rnd = round_dev ? *round_dev : round;
+  const bool cooperative = strategy == HPC_COOPERATIVE ||
+                           (strategy == HPC_HYBRID && (int64_t)rnd >= (int64_t)n_competitive);
   const int w = blockIdx.x;
   const RoundWorker me = wk[w];
   double bf = fhat[w];
@@ -324,8 +338,11 @@ __global__ void __launch_bounds__(256) base_select_kernel(const RoundWorker *__r
 __global__ void __launch_bounds__(256) incumbent_kernel(const RoundWorker *__restrict__ wk, int d,
                                                         double *__restrict__ fhat, float *__restrict__ Cpool,
                                                         uint8_t *__restrict__ Kpool, double *f_new,
-                                                        int32_t *iters, uint8_t *accepted) {
+                                                        int32_t *iters, uint8_t *accepted,
+                                                        uint32_t *round_advance) {
   const int w = blockIdx.x;
+  // the last kernel of a round moves a prepared round's counter on
+  if (round_advance && w == 0 && threadIdx.x == 0) *round_advance += 1u;
   const RoundWorker me = wk[w];
   const double f = *me.fw;
   const double per = f / (double)me.s;
@@ -391,6 +408,208 @@ int stage_release(hpc_ctx *c, int slot) {
 
 int64_t hpc_grid_bound(const hpc_launch &L) { return (int64_t)L.num_sms * 8; }
 
+// ---------------------------------------------------------------------------
+// Batched round (Algorithms 3-5): set-up shared by hpc_round and
+// hpc_round_prepare, and the launches of one round.
+
+// Everything one round needs once its descriptor tables are on the device.
+struct hpc_round_plan {
+  int W = 0, d = 0;
+  int64_t n = 0, smax = 0;
+  uint64_t seed = 0;
+  int strategy = 0;  // HPC_HYBRID is resolved on the device from the round
+  int32_t n_competitive = 0;
+  const float *X = nullptr;
+  float *C = nullptr;
+  uint8_t *deg = nullptr;
+  double *fhat = nullptr, *f_new = nullptr;
+  int32_t *iters = nullptr;
+  uint8_t *accepted = nullptr;
+  TaskHeader *hdr = nullptr;
+  const RoundWorker *rw_d = nullptr;
+  const hpc_sample_task *st_d = nullptr;
+  std::vector<char> host;  // host image of the tables of a prepared round
+  std::vector<KppLaunch> kl;
+  std::vector<LloydLaunch> ll;
+};
+
+static int round_check(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch *b,
+                       int32_t strategy, int32_t max_iter, int32_t n_candidates, int32_t prec) {
+  if (int rc = check_dims(c, d)) return rc;
+  if (n < 1 || !X || b->W < 1 || b->W > HPC_MAX_WORKERS || !b->s || !b->k || !b->C_off ||
+      !b->K_off || !b->C || !b->degenerate || !b->fhat)
+    return fail(c, HPC_ERR_ARG, "malformed batch");
+  if (strategy != HPC_COMPETITIVE && strategy != HPC_COOPERATIVE && strategy != HPC_HYBRID)
+    return fail(c, HPC_ERR_ARG, "unknown strategy");
+  if (prec != HPC_FP32) return fail(c, HPC_ERR_UNSUPPORTED, "only HPC_FP32 is built");
+  if (n_candidates < 1 || n_candidates > 8) return fail(c, HPC_ERR_ARG, "n_candidates in [1, 8]");
+  if (max_iter < 0 || max_iter > HPC_MAX_ITER) return fail(c, HPC_ERR_ARG, "max_iter out of range");
+  if (!aligned16(X) || !aligned16(b->C)) return fail(c, HPC_ERR_ARG, "unaligned");
+  for (int w = 0; w < b->W; ++w)
+    if (b->s[w] < 1 || b->k[w] < 1 || b->C_off[w] < 0 || b->K_off[w] < 0 || (b->C_off[w] & 3))
+      return fail(c, HPC_ERR_ARG, "malformed batch entry");
+  return HPC_OK;
+}
+
+// Device bytes of one round's scratch and tables (tables: *tab_bytes).
+static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, int L,
+                                  size_t *tab_bytes) {
+  const int W = b->W;
+  const int nchunks = (W + HPC_ROUND_CHUNK - 1) / HPC_ROUND_CHUNK;
+  size_t need = pad256((size_t)W * sizeof(TaskHeader)) + 4096;
+  for (int w = 0; w < W; ++w) {
+    const int64_t s = b->s[w];
+    const int k = b->k[w];
+    need += pad256((size_t)s * d * 4) + pad256((size_t)k * d * 4) + pad256((size_t)k) +
+            pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
+            pad256((size_t)2 * c->grid_bound * 8) + pad256((size_t)s * 4) +
+            pad256((size_t)L * s * 4) + pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8);
+  }
+  *tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) + pad256((size_t)W * sizeof(RoundWorker)) +
+               pad256((size_t)W * sizeof(hpc_kpp_task)) + pad256((size_t)W * sizeof(hpc_lloyd_task)) +
+               2 * (size_t)nchunks * pad256((size_t)c->grid_bound * 4);
+  return need + pad256((size_t)W * 8) + pad256((size_t)W * 4) + *tab_bytes + 1024;
+}
+
+// Carves the round's scratch from cv, writes the descriptor tables into
+// tab_host (their device home is tab_dev, same layout) and plans the
+// persistent launches.
+static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_batch *b,
+                       int strategy, uint64_t seed, uint32_t round, int max_iter, double rel_tol,
+                       int L, Carver &cv, char *tab_host, char *tab_dev, size_t tab_bytes,
+                       hpc_round_plan &p) {
+  const int W = b->W;
+  const int nchunks = (W + HPC_ROUND_CHUNK - 1) / HPC_ROUND_CHUNK;
+  int64_t smax = 0;
+  for (int w = 0; w < W; ++w) smax = std::max<int64_t>(smax, b->s[w]);
+  TaskHeader *hdr = cv.take<TaskHeader>((size_t)W);
+  double *fw = cv.take<double>((size_t)W);
+  int32_t *itw = cv.take<int32_t>((size_t)W);
+  Carver th{tab_host, 0, tab_bytes}, td{tab_dev, 0, tab_bytes};
+  hpc_sample_task *st_h = th.take<hpc_sample_task>((size_t)W);
+  hpc_sample_task *st_d = td.take<hpc_sample_task>((size_t)W);
+  RoundWorker *rw_h = th.take<RoundWorker>((size_t)W);
+  RoundWorker *rw_d = td.take<RoundWorker>((size_t)W);
+  hpc_kpp_task *kt_h = th.take<hpc_kpp_task>((size_t)W);
+  hpc_kpp_task *kt_d = td.take<hpc_kpp_task>((size_t)W);
+  hpc_lloyd_task *lt_h = th.take<hpc_lloyd_task>((size_t)W);
+  hpc_lloyd_task *lt_d = td.take<hpc_lloyd_task>((size_t)W);
+  for (int w = 0; w < W; ++w) {
+    const int64_t s = b->s[w];
+    const int k = b->k[w];
+    float *S = cv.take<float>((size_t)s * d);
+    float *Cn = cv.take<float>((size_t)k * d);
+    uint8_t *dn = cv.take<uint8_t>((size_t)k);
+    st_h[w] = hpc_sample_task{S, nullptr, s, (uint32_t)w};
+    rw_h[w] = RoundWorker{s, b->C_off[w], b->K_off[w], k, b->group ? b->group[w] : 0, Cn, dn,
+                          fw + w, itw + w};
+    hpc_kpp_task &kt = kt_h[w];
+    kt = hpc_kpp_task{};
+    kt.S = S;
+    kt.s = s;
+    kt.k = k;
+    kt.worker = (uint32_t)w;
+    kt.C = Cn;
+    kt.deg = dn;
+    kpp_task_scratch(c, cv, hdr + w, s, L, kt);
+    hpc_lloyd_task &lt = lt_h[w];
+    lt = hpc_lloyd_task{};
+    lt.S = S;
+    lt.s = s;
+    lt.k = k;
+    lt.C = Cn;
+    lt.deg = dn;
+    lt.f_out = fw + w;
+    lt.iters_out = itw + w;
+    lloyd_task_scratch(c, cv, hdr + w, d, k, lt);
+  }
+  // plans of the persistent launches, HPC_ROUND_CHUNK workers each
+  p.kl.assign(nchunks, KppLaunch{});
+  p.ll.assign(nchunks, LloydLaunch{});
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int w0 = ch * HPC_ROUND_CHUNK, cw = std::min(W - w0, HPC_ROUND_CHUNK);
+    int kk = 0;
+    for (int w = w0; w < w0 + cw; ++w) kk = std::max(kk, b->k[w]);
+    KppLaunch &kh = p.kl[ch];
+    kh.W = cw;
+    kh.tasks = kt_h + w0;
+    kh.block_task_host = th.take<int>((size_t)c->grid_bound);
+    kh.tasks_dev = kt_d + w0;
+    kh.block_task_dev = td.take<int>((size_t)c->grid_bound);
+    kh.d = d;
+    kh.kmax = kk;
+    kh.L = L;
+    kh.seed = seed;
+    kh.round = round;
+    kh.status = c->dwords;
+    kh.max_blocks = c->grid_bound;
+    kh.chunk_cap = c->grid_bound;
+    if (int rc = hpc_kmeanspp_plan(c->L, kh)) return plan_fail(c, rc, "kmeanspp: unsupported shape");
+    LloydLaunch &lh = p.ll[ch];
+    lh.W = cw;
+    lh.tasks = lt_h + w0;
+    lh.block_task_host = th.take<int>((size_t)c->grid_bound);
+    lh.tasks_dev = lt_d + w0;
+    lh.block_task_dev = td.take<int>((size_t)c->grid_bound);
+    lh.d = d;
+    lh.kmax = kk;
+    lh.max_iter = max_iter;
+    lh.tol = rel_tol;
+    lh.status = c->dwords;
+    lh.max_blocks = c->grid_bound;
+    lh.gpart_cap = 2 * c->grid_bound;
+    if (int rc = hpc_lloyd_plan(c->L, lh)) return plan_fail(c, rc, "lloyd: unsupported shape");
+  }
+  if (cv.off > cv.cap || th.off > th.cap) return fail(c, HPC_ERR_NOMEM, "round scratch layout overflow");
+  p.W = W;
+  p.d = d;
+  p.n = n;
+  p.smax = smax;
+  p.seed = seed;
+  p.strategy = strategy;
+  p.n_competitive = b->n_competitive;
+  p.X = X;
+  p.C = b->C;
+  p.deg = b->degenerate;
+  p.fhat = b->fhat;
+  p.f_new = b->f_new;
+  p.iters = b->iters;
+  p.accepted = b->accepted;
+  p.hdr = hdr;
+  p.rw_d = rw_d;
+  p.st_d = st_d;
+  return HPC_OK;
+}
+
+// One round: a memset of the task headers and 3 + 2 * chunks launches; no
+// host synchronisation, no allocation (a stream capture can record it).  The
+// round index is `round`, or *round_dev when that is given (a prepared round,
+// whose incumbent kernel then advances it).
+static int round_enqueue(hpc_ctx *c, const hpc_round_plan &p, uint32_t *round_dev, uint32_t round) {
+  cudaError_t e = cudaMemsetAsync(p.hdr, 0, (size_t)p.W * sizeof(TaskHeader), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "round set-up");
+  if (int rc = hpc_sample_batch_launch(c->L, p.X, p.n, p.d, p.seed, round, round_dev, p.W, p.st_d,
+                                       p.smax))
+    return plan_fail(c, rc, "sample launch");
+  base_select_kernel<<<p.W, 256, 0, c->stream>>>(p.rw_d, p.W, p.strategy, p.n_competitive, round_dev,
+                                                 round, p.fhat, p.C, p.deg, p.d);
+  if ((e = cudaGetLastError())) return cuda_fail(c, e, "base launch");
+  c->launches += 2;
+  for (size_t ch = 0; ch < p.kl.size(); ++ch) {
+    KppLaunch kh = p.kl[ch];
+    kh.round = round;
+    kh.round_dev = round_dev;
+    if (int rc = hpc_kmeanspp_run(c->L, kh)) return plan_fail(c, rc, "kmeanspp launch");
+    if (int rc = hpc_lloyd_run(c->L, p.ll[ch])) return plan_fail(c, rc, "lloyd launch");
+    c->launches += 2;
+  }
+  incumbent_kernel<<<p.W, 256, 0, c->stream>>>(p.rw_d, p.d, p.fhat, p.C, p.deg, p.f_new, p.iters,
+                                               p.accepted, round_dev);
+  if ((e = cudaGetLastError())) return cuda_fail(c, e, "incumbent launch");
+  c->launches += 1;
+  return HPC_OK;
+}
+
 extern "C" {
 
 int hpc_create(hpc_ctx **ctx, int device, void *stream) {
@@ -432,6 +651,8 @@ int hpc_destroy(hpc_ctx *c) {
     if (c->stage_host[i]) cudaFreeHost(c->stage_host[i]);
     if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
   }
+  if (c->plan_mem) cudaFree(c->plan_mem);
+  delete c->plan;
   delete c;
   return HPC_OK;
 }
@@ -567,160 +788,74 @@ int hpc_round(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch 
               int32_t strategy, uint64_t seed, uint32_t round, int32_t max_iter, double rel_tol,
               int32_t n_candidates, int32_t prec) {
   if (!c || !b) return HPC_ERR_ARG;
-  if (int rc = check_dims(c, d)) return rc;
-  if (n < 1 || !X || b->W < 1 || b->W > HPC_MAX_WORKERS || !b->s || !b->k || !b->C_off ||
-      !b->K_off || !b->C || !b->degenerate || !b->fhat)
-    return fail(c, HPC_ERR_ARG, "malformed batch");
-  if (strategy != HPC_COMPETITIVE && strategy != HPC_COOPERATIVE && strategy != HPC_HYBRID)
-    return fail(c, HPC_ERR_ARG, "unknown strategy");
-  if (prec != HPC_FP32) return fail(c, HPC_ERR_UNSUPPORTED, "only HPC_FP32 is built");
-  if (n_candidates < 1 || n_candidates > 8) return fail(c, HPC_ERR_ARG, "n_candidates in [1, 8]");
-  if (max_iter < 0 || max_iter > HPC_MAX_ITER) return fail(c, HPC_ERR_ARG, "max_iter out of range");
-  if (!aligned16(X) || !aligned16(b->C)) return fail(c, HPC_ERR_ARG, "unaligned");
-  // Algorithm 5: the competitive phase, then the cooperative one
-  if (strategy == HPC_HYBRID)
-    strategy = (int64_t)round < (int64_t)b->n_competitive ? HPC_COMPETITIVE : HPC_COOPERATIVE;
-  const int W = b->W;
-  const int L = n_candidates;
-  int64_t smax = 0;
-  int kmax = 0;
-  for (int w = 0; w < W; ++w) {
-    if (b->s[w] < 1 || b->k[w] < 1 || b->C_off[w] < 0 || b->K_off[w] < 0 || (b->C_off[w] & 3))
-      return fail(c, HPC_ERR_ARG, "malformed batch entry");
-    smax = std::max<int64_t>(smax, b->s[w]);
-    kmax = std::max<int>(kmax, b->k[w]);
-  }
+  if (int rc = round_check(c, X, n, d, b, strategy, max_iter, n_candidates, prec)) return rc;
   cudaSetDevice(c->device);
-
-  // ---- scratch: task headers (zeroed), per-worker buffers, tables ----
-  const int nchunks = (W + HPC_ROUND_CHUNK - 1) / HPC_ROUND_CHUNK;
-  size_t need = pad256((size_t)W * sizeof(TaskHeader)) + 4096;
-  for (int w = 0; w < W; ++w) {
-    const int64_t s = b->s[w];
-    const int k = b->k[w];
-    need += pad256((size_t)s * d * 4) + pad256((size_t)k * d * 4) + pad256((size_t)k) +
-            pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
-            pad256((size_t)2 * c->grid_bound * 8) + pad256((size_t)s * 4) +
-            pad256((size_t)L * s * 4) + pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8);
-  }
-  const size_t tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) +
-                           pad256((size_t)W * sizeof(RoundWorker)) +
-                           pad256((size_t)W * sizeof(hpc_kpp_task)) +
-                           pad256((size_t)W * sizeof(hpc_lloyd_task)) +
-                           2 * (size_t)nchunks * pad256((size_t)c->grid_bound * 4);
-  need += pad256(W * 16) + tab_bytes + 256;
+  size_t tab_bytes = 0;
+  const size_t need = round_scratch_bytes(c, b, d, n_candidates, &tab_bytes);
   if (int rc = ensure_ws(c, need)) return rc;
   Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
-  TaskHeader *hdr = cv.take<TaskHeader>((size_t)W);
-  double *fw = cv.take<double>((size_t)W);
-  int32_t *itw = cv.take<int32_t>((size_t)W);
-  // device tables, mirrored byte for byte in a pinned staging slot
   char *tab_dev = cv.take<char>(tab_bytes);
   char *tab_host = nullptr;
   const int slot = c->stage_next;
   if (int rc = stage_acquire(c, slot, tab_bytes, &tab_host)) return rc;
-  Carver th{tab_host, 0, tab_bytes}, td{tab_dev, 0, tab_bytes};
-  hpc_sample_task *st_h = th.take<hpc_sample_task>((size_t)W);
-  hpc_sample_task *st_d = td.take<hpc_sample_task>((size_t)W);
-  RoundWorker *rw_h = th.take<RoundWorker>((size_t)W);
-  RoundWorker *rw_d = td.take<RoundWorker>((size_t)W);
-  hpc_kpp_task *kt_h = th.take<hpc_kpp_task>((size_t)W);
-  hpc_kpp_task *kt_d = td.take<hpc_kpp_task>((size_t)W);
-  hpc_lloyd_task *lt_h = th.take<hpc_lloyd_task>((size_t)W);
-  hpc_lloyd_task *lt_d = td.take<hpc_lloyd_task>((size_t)W);
-  for (int w = 0; w < W; ++w) {
-    const int64_t s = b->s[w];
-    const int k = b->k[w];
-    float *S = cv.take<float>((size_t)s * d);
-    float *Cn = cv.take<float>((size_t)k * d);
-    uint8_t *dn = cv.take<uint8_t>((size_t)k);
-    st_h[w] = hpc_sample_task{S, nullptr, s, (uint32_t)w};
-    rw_h[w] = RoundWorker{s, b->C_off[w], b->K_off[w], k, b->group ? b->group[w] : 0, Cn, dn,
-                          fw + w, itw + w};
-    hpc_kpp_task &kt = kt_h[w];
-    kt = hpc_kpp_task{};
-    kt.S = S;
-    kt.s = s;
-    kt.k = k;
-    kt.worker = (uint32_t)w;
-    kt.C = Cn;
-    kt.deg = dn;
-    kpp_task_scratch(c, cv, hdr + w, s, L, kt);
-    hpc_lloyd_task &lt = lt_h[w];
-    lt = hpc_lloyd_task{};
-    lt.S = S;
-    lt.s = s;
-    lt.k = k;
-    lt.C = Cn;
-    lt.deg = dn;
-    lt.f_out = fw + w;
-    lt.iters_out = itw + w;
-    lloyd_task_scratch(c, cv, hdr + w, d, k, lt);
-  }
-  // plans of the persistent launches, HPC_ROUND_CHUNK workers each
-  std::vector<KppLaunch> kl(nchunks);
-  std::vector<LloydLaunch> ll(nchunks);
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int w0 = ch * HPC_ROUND_CHUNK, cw = std::min(W - w0, HPC_ROUND_CHUNK);
-    int kk = 0;
-    for (int w = w0; w < w0 + cw; ++w) kk = std::max(kk, b->k[w]);
-    KppLaunch &kh = kl[ch];
-    kh = KppLaunch{};
-    kh.W = cw;
-    kh.tasks = kt_h + w0;
-    kh.block_task_host = th.take<int>((size_t)c->grid_bound);
-    kh.tasks_dev = kt_d + w0;
-    kh.block_task_dev = td.take<int>((size_t)c->grid_bound);
-    kh.d = d;
-    kh.kmax = kk;
-    kh.L = L;
-    kh.seed = seed;
-    kh.round = round;
-    kh.status = c->dwords;
-    kh.max_blocks = c->grid_bound;
-    kh.chunk_cap = c->grid_bound;
-    if (int rc = hpc_kmeanspp_plan(c->L, kh)) return plan_fail(c, rc, "kmeanspp: unsupported shape");
-    LloydLaunch &lh = ll[ch];
-    lh = LloydLaunch{};
-    lh.W = cw;
-    lh.tasks = lt_h + w0;
-    lh.block_task_host = th.take<int>((size_t)c->grid_bound);
-    lh.tasks_dev = lt_d + w0;
-    lh.block_task_dev = td.take<int>((size_t)c->grid_bound);
-    lh.d = d;
-    lh.kmax = kk;
-    lh.max_iter = max_iter;
-    lh.tol = rel_tol;
-    lh.status = c->dwords;
-    lh.max_blocks = c->grid_bound;
-    lh.gpart_cap = 2 * c->grid_bound;
-    if (int rc = hpc_lloyd_plan(c->L, lh)) return plan_fail(c, rc, "lloyd: unsupported shape");
-  }
-
-  if (cv.off > cv.cap || th.off > th.cap) return fail(c, HPC_ERR_NOMEM, "round scratch layout overflow");
-
-  // ---- the round: one memset, one table copy, 3 + 2 * chunks launches ----
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(hdr, 0, (size_t)W * sizeof(TaskHeader), c->stream)) ||
-      (e = cudaMemcpyAsync(tab_dev, tab_host, tab_bytes, cudaMemcpyHostToDevice, c->stream)))
-    return cuda_fail(c, e, "round set-up");
+  hpc_round_plan p;
+  if (int rc = round_build(c, X, n, d, b, strategy, seed, round, max_iter, rel_tol, n_candidates,
+                           cv, tab_host, tab_dev, tab_bytes, p))
+    return rc;
+  // one table copy from the pinned staging slot, then the launches
+  cudaError_t e = cudaMemcpyAsync(tab_dev, tab_host, tab_bytes, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "round tables");
   if (int rc = stage_release(c, slot)) return rc;
-  if (int rc = hpc_sample_batch_launch(c->L, X, n, d, seed, round, W, st_d, smax))
-    return plan_fail(c, rc, "sample launch");
-  base_select_kernel<<<W, 256, 0, c->stream>>>(rw_d, W, strategy == HPC_COOPERATIVE ? 1 : 0, b->fhat,
-                                               b->C, b->degenerate, d);
-  if ((e = cudaGetLastError())) return cuda_fail(c, e, "base launch");
-  c->launches += 2;
-  for (int ch = 0; ch < nchunks; ++ch) {
-    if (int rc = hpc_kmeanspp_run(c->L, kl[ch])) return plan_fail(c, rc, "kmeanspp launch");
-    if (int rc = hpc_lloyd_run(c->L, ll[ch])) return plan_fail(c, rc, "lloyd launch");
-    c->launches += 2;
+  return round_enqueue(c, p, nullptr, round);
+}
+
+int hpc_round_prepare(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch *b,
+                      int32_t strategy, uint64_t seed, uint32_t round0, int32_t max_iter,
+                      double rel_tol, int32_t n_candidates, int32_t prec) {
+  if (!c || !b) return HPC_ERR_ARG;
+  if (int rc = round_check(c, X, n, d, b, strategy, max_iter, n_candidates, prec)) return rc;
+  cudaSetDevice(c->device);
+  cudaError_t e;
+  size_t tab_bytes = 0;
+  const size_t need = round_scratch_bytes(c, b, d, n_candidates, &tab_bytes) + 256;
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+  if (need > c->plan_bytes) {
+    if (c->plan_mem) cudaFree(c->plan_mem);
+    c->plan_mem = nullptr;
+    c->plan_bytes = 0;
+    if ((e = cudaMalloc(&c->plan_mem, need)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, HPC_ERR_NOMEM, "prepared-round allocation failed");
+    }
+    c->plan_bytes = need;
   }
-  incumbent_kernel<<<W, 256, 0, c->stream>>>(rw_d, d, b->fhat, b->C, b->degenerate, b->f_new,
-                                             b->iters, b->accepted);
-  if ((e = cudaGetLastError())) return cuda_fail(c, e, "incumbent launch");
-  c->launches += 1;
+  if (!c->plan) c->plan = new hpc_round_plan();
+  hpc_round_plan &p = *c->plan;
+  p = hpc_round_plan();
+  Carver cv{reinterpret_cast<char *>(c->plan_mem), 0, c->plan_bytes};
+  c->plan_round = cv.take<uint32_t>(1);
+  char *tab_dev = cv.take<char>(tab_bytes);
+  p.host.assign(tab_bytes, 0);
+  if (int rc = round_build(c, X, n, d, b, strategy, seed, round0, max_iter, rel_tol, n_candidates,
+                           cv, p.host.data(), tab_dev, tab_bytes, p)) {
+    p.W = 0;
+    return rc;
+  }
+  if ((e = cudaMemcpyAsync(tab_dev, p.host.data(), tab_bytes, cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaMemcpyAsync(c->plan_round, &round0, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                           c->stream)) ||
+      (e = cudaStreamSynchronize(c->stream))) {
+    p.W = 0;
+    return cuda_fail(c, e, "prepared-round tables");
+  }
   return HPC_OK;
+}
+
+int hpc_round_enqueue(hpc_ctx *c) {
+  if (!c) return HPC_ERR_ARG;
+  if (!c->plan || c->plan->W < 1) return fail(c, HPC_ERR_ARG, "no prepared round");
+  cudaSetDevice(c->device);
+  return round_enqueue(c, *c->plan, c->plan_round, 0);
 }
 
 }  // extern "C"

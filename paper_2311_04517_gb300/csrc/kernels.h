@@ -86,6 +86,7 @@ struct KppLaunch {
   int d, kmax, L;
   uint64_t seed;
   uint32_t round;
+  const uint32_t *round_dev;  // nullable: read the round from the device instead
   int *status;
   int64_t max_blocks;
   int64_t chunk_cap;  // chunkQ entries reserved per task (1 per block)
@@ -137,9 +138,11 @@ bool hpc_tcs_objective_supported(int d, int k, int64_t n);
 int hpc_tcs_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
 int hpc_sample_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
                       uint32_t worker, uint32_t round, int64_t s, float *S, int64_t *idx);
-// W samples at once; tasks_dev is a device array [W], smax the largest s.
+// W samples at once; tasks_dev is a device array [W], smax the largest s;
+// the round is *round_dev when that is not null.
 int hpc_sample_batch_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
-                            uint32_t round, int W, const hpc_sample_task *tasks_dev, int64_t smax);
+                            uint32_t round, const uint32_t *round_dev, int W,
+                            const hpc_sample_task *tasks_dev, int64_t smax);
 
 // Blocks the cooperative kernels may use at most (upper bound for scratch
 // sizing): resident blocks per SM times SMs.

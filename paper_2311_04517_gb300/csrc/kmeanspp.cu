@@ -28,6 +28,7 @@ struct KppArgs {
   int d, L;
   uint64_t seed;
   uint32_t round;
+  const uint32_t *round_dev;  // nullable
   int *status;
 };
 
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
 
   // this block's task (one worker's sample) and its place in the task's group
   const hpc_kpp_task tk = a.W == 1 ? a.single : a.tasks[a.block_task[blockIdx.x]];
+  const uint32_t round = a.round_dev ? *a.round_dev : a.round;
   const int k = tk.k, d = a.d, L = a.L;
   const int64_t s = tk.s;
   const int G = tk.nblocks, lb = (int)blockIdx.x - tk.block0;
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
   }
   __syncthreads();
   if (!any_live) {  // uniform first pick into the lowest slot
-    const uint64_t r = hpc_draw(a.seed, tk.worker, a.round, HPC_TAG_SEED, 0);
+    const uint64_t r = hpc_draw(a.seed, tk.worker, round, HPC_TAG_SEED, 0);
     const int64_t i0 = (int64_t)hpc_scale_word(r, (uint64_t)s);
     for (int t = threadIdx.x; t < D; t += THREADS) {
       const float v = t < d ? tk.S[i0 * d + t] : 0.0f;
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
       const unsigned long long incl = block_scan_u64<THREADS>(loc, s_u64, &Q);
       const unsigned long long excl = incl - loc;
       for (int l = 0; l < L; ++l) {
-        const uint64_t r = hpc_draw(a.seed, tk.worker, a.round, HPC_TAG_SEED,
+        const uint64_t r = hpc_draw(a.seed, tk.worker, round, HPC_TAG_SEED,
                                     1ull + (uint64_t)t * (uint64_t)L + (uint64_t)l);
         const unsigned long long target = hpc_scale_word(r, Q);
         if (excl <= target && target < incl) {  // exactly one thread: its segment holds it
@@ -337,6 +339,7 @@ int kpp_run_t(const hpc_launch &Lc, const KppLaunch &h) {
   a.L = h.L;
   a.seed = h.seed;
   a.round = h.round;
+  a.round_dev = h.round_dev;
   a.status = h.status;
   void *args[] = {&a};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)h.grid),

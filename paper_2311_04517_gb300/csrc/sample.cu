@@ -48,8 +48,9 @@ constexpr int SB_THREADS = 256, SB_ROWS = 4 * SB_THREADS;
 template <bool VEC4>
 __global__ void __launch_bounds__(SB_THREADS) sample_batch_kernel(
     const float *__restrict__ X, int64_t n, int d, uint64_t seed, uint32_t round,
-    const hpc_sample_task *__restrict__ tasks) {
+    const uint32_t *round_dev, const hpc_sample_task *__restrict__ tasks) {
   __shared__ int64_t s_idx[SB_ROWS];
+  if (round_dev) round = *round_dev;
   const hpc_sample_task t = tasks[blockIdx.y];
   const int64_t r0 = (int64_t)blockIdx.x * SB_ROWS;
   if (r0 >= t.s) return;
@@ -88,14 +89,17 @@ __global__ void __launch_bounds__(SB_THREADS) sample_batch_kernel(
 }  // namespace
 
 int hpc_sample_batch_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
-                            uint32_t round, int W, const hpc_sample_task *tasks_dev, int64_t smax) {
+                            uint32_t round, const uint32_t *round_dev, int W,
+                            const hpc_sample_task *tasks_dev, int64_t smax) {
   if (W < 1 || smax < 1) return HPC_OK;
   if (W > 65535) return HPC_ERR_ARG;
   const dim3 grid((unsigned)((smax + SB_ROWS - 1) / SB_ROWS), (unsigned)W);
   if (d % 4 == 0)
-    sample_batch_kernel<true><<<grid, SB_THREADS, 0, L.stream>>>(X, n, d, seed, round, tasks_dev);
+    sample_batch_kernel<true><<<grid, SB_THREADS, 0, L.stream>>>(X, n, d, seed, round, round_dev,
+                                                                 tasks_dev);
   else
-    sample_batch_kernel<false><<<grid, SB_THREADS, 0, L.stream>>>(X, n, d, seed, round, tasks_dev);
+    sample_batch_kernel<false><<<grid, SB_THREADS, 0, L.stream>>>(X, n, d, seed, round, round_dev,
+                                                                  tasks_dev);
   return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 

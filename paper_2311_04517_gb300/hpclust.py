@@ -87,6 +87,9 @@ def load() -> ctypes.CDLL:
         "hpc_set_tensor_cores": ([P, ctypes.c_int], ctypes.c_int),
         "hpc_round": ([P, P, i64, i32, ctypes.POINTER(hpc_batch), i32, u64, u32, i32, f64,
                        i32, i32], ctypes.c_int),
+        "hpc_round_prepare": ([P, P, i64, i32, ctypes.POINTER(hpc_batch), i32, u64, u32, i32,
+                               f64, i32, i32], ctypes.c_int),
+        "hpc_round_enqueue": ([P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -278,3 +281,19 @@ def hpc_round(ctx: Context, X, batch: Batch, strategy: int, seed: int, round_: i
     b = batch.struct()
     ctx._check(ctx.lib.hpc_round(ctx.h, _ptr(X), n, d, ctypes.byref(b), strategy, seed, round_,
                                  max_iter, rel_tol, n_candidates, prec))
+
+
+def hpc_round_prepare(ctx: Context, X, batch: Batch, strategy: int, seed: int, round0: int = 0,
+                      max_iter: int = MAX_ITER, rel_tol: float = REL_TOL,
+                      n_candidates: int = N_CANDIDATES, prec: int = HPC_FP32):
+    """Set-up of a round that hpc_round_enqueue then enqueues (and a stream
+    capture can record) round after round."""
+    n, d = X.shape
+    _need(X, torch.float32, "X", ctx.device)
+    b = batch.struct()
+    ctx._check(ctx.lib.hpc_round_prepare(ctx.h, _ptr(X), n, d, ctypes.byref(b), strategy, seed,
+                                         round0, max_iter, rel_tol, n_candidates, prec))
+
+
+def hpc_round_enqueue(ctx: Context):
+    ctx._check(ctx.lib.hpc_round_enqueue(ctx.h))
