@@ -3,8 +3,9 @@
 
 One step = one HPClust round on the benchmark workload (sample draw,
 K-means++ reseeding of degenerate centroids, Lloyd to the Section 6.5 stop
-rule, incumbent test) followed by the full-data objective of the incumbent
-(Eq. 1 over all n rows).  Distances counted per step: (Lloyd assignments) x
+rule, incumbent test), replayed from a CUDA graph that recorded one round
+(--no-graph: issued call by call), followed by the full-data objective of
+the best incumbent of each sharing group (Eq. 1 over all n rows).  Distances counted per step: (Lloyd assignments) x
 s x k + n x k.  Default workload: "fp32" (n = 10^7 points in 16 dims, 25
 Gaussians, k = 25, one worker, s = 10^5).
 
@@ -54,9 +55,9 @@ def parse_args():
                    default="competitive")
     p.add_argument("--n-competitive", type=int, default=None,
                    help="hybrid: rounds of the competitive phase (default: half the run)")
-    p.add_argument("--graph", action="store_true",
-                   help="record one round in a CUDA graph (hpc_round_prepare / enqueue) and "
-                        "replay it every step")
+    p.add_argument("--no-graph", dest="graph", action="store_false",
+                   help="issue every round with hpc_round instead of replaying one round "
+                        "recorded in a CUDA graph (hpc_round_prepare / hpc_round_enqueue)")
     p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=2,
                    help="objective search: 0 CUDA cores, 1 tensor cores wherever built, 2 auto")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -178,8 +179,6 @@ def group_members(ws):
 
 def workload_config(wl, strategy, args):
     st = strategy if strategy != "hybrid" else f"hybrid (competitive for {n_comp(args)} rounds)"
-    if getattr(args, "graph", False):
-        st += "; each round replayed from one CUDA graph"
     return {"workload": f"{wl.name}: {wl.notes}", "n": wl.n, "d": wl.d, "k": list(wl.k),
             "workers": wl.W, "s": list(wl.s), "strategy": st,
             "step": "one HPClust round for every worker + full-data objective of the best "
@@ -455,13 +454,15 @@ def run_mine(args):
     kb0 = int(ws.k[best_log[0][0]]) if best_log else int(ws.k[0])
     split = wl.d in (16, 32) and (args.tensor_cores == 1 or
                                   (args.tensor_cores == 2 and wl.d == 32 and kb0 <= 64))
-    tf32 = args.tensor_cores != 0 and wl.d in (64, 128)
+    tf32 = args.tensor_cores != 0 and wl.d in (64, 128) and kb0 <= 128
     obj_kernel = "tcs_objective_kernel" if split else "tc_objective_kernel" if tf32 \
         else "objective_kernel"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(wl, args.strategy, args),
+            "round_issue": ("one round recorded in a CUDA graph, replayed every step" if args.graph
+                            else "calls issued one by one"),
             "roofline": {"kernel": f"{obj_kernel} (full-data objective, Eq. 1)",
                          "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "peak_source": f"{src} hbm_gbs", "unit": "GB/s",
