@@ -37,11 +37,13 @@ struct Tile {
   static constexpr int THREADS = 256;
 };
 
-// Lloyd: samples are small (10^4 - 10^6 rows), so one row per thread spreads
-// an iteration over every SM; the accumulation maps lanes to dimensions.
+// Lloyd: samples are small (10^4 - 10^6 rows): one or two rows per thread
+// spread an iteration over every SM (two at d <= 16, so that a 10^5-row
+// sample takes one row group per block); the accumulation maps lanes to
+// dimensions.
 template <int D>
 struct LTile {
-  static constexpr int R = 1;
+  static constexpr int R = D <= 16 ? 2 : 1;
   static constexpr int THREADS = 256;
   static constexpr int MINB = D <= 32 ? 2 : 1;
   static constexpr int LPR = D < 32 ? D : 32;          // lanes per row
@@ -232,7 +234,15 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
       const int j = e / CS, t = e - j * CS;
       if (dead[j] || t >= d) continue;
       const unsigned cnt = __ldcg(gc + j);
-      if (cnt == 0u) continue;
+      if (cnt == 0u) {  // emptied: degenerate for the rest of the run
+        // (every thread of centroid j sees cnt == 0 and skips it, so the
+        // flag written here changes no other thread's work in this loop)
+        if (t == 0) {
+          dead[j] = 1;
+          if (lb == 0) tk.deg[j] = 1;
+        }
+        continue;
+      }
       const long long q = (long long)__ldcg(gs + (size_t)j * d + t);
       const float v = (float)(((double)q * qinv) / (double)cnt);
       cs.cm[e] = -2.0f * v;
@@ -242,13 +252,6 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
       const int zb = (it + 2) % 3;
       for (int e = threadIdx.x; e < k * d; e += THREADS) tk.gsum[(size_t)zb * k * d + e] = 0ull;
       for (int j = threadIdx.x; j < k; j += THREADS) tk.gcount[(size_t)zb * k + j] = 0u;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < k; j += THREADS) {
-      if (!dead[j] && __ldcg(gc + j) == 0u) {  // emptied: degenerate for the rest of the run
-        dead[j] = 1;
-        if (lb == 0) tk.deg[j] = 1;
-      }
     }
     __syncthreads();
     hpc_cent_finish<D>(cs, k, s_red, [&](int j) { return dead[j] != 0; });
