@@ -28,6 +28,7 @@ import statistics
 import sys
 import threading
 import time
+from dataclasses import replace
 from pathlib import Path
 
 ROOT = Path(__file__).resolve().parent
@@ -60,6 +61,9 @@ def parse_args():
                         "recorded in a CUDA graph (hpc_round_prepare / hpc_round_enqueue)")
     p.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=2,
                    help="objective search: 0 CUDA cores, 1 tensor cores wherever built, 2 auto")
+    p.add_argument("--rows", type=int, default=None,
+                   help="a smaller case of the workload: this many data rows instead of n "
+                        "(for profiler captures; not a bench configuration)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
     return p.parse_args()
@@ -187,6 +191,13 @@ def workload_config(wl, strategy, args):
             "lloyd_max_iter": 300, "lloyd_rel_tol": 1e-4, "kmeanspp_candidates": 3}
 
 
+def bench_workload(args):
+    wl = synth.workload(args.workload)
+    if args.rows is not None:
+        wl = replace(wl, n=int(args.rows))
+    return wl
+
+
 def n_comp(args):
     if args.n_competitive is not None:
         return args.n_competitive
@@ -259,7 +270,7 @@ def run_reference(args):
         return
     import oracle as orc
     orc.build()
-    wl = synth.workload(args.workload)
+    wl = bench_workload(args)
     ws = synth.worker_setup(wl)
     X = load_data(wl, "cpu", wl.seed).numpy()
     strat = {"cooperative": orc.COOPERATIVE, "hybrid": orc.HYBRID}.get(args.strategy,
@@ -308,7 +319,7 @@ def run_mine(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    wl = synth.workload(args.workload)
+    wl = bench_workload(args)
     ws = synth.worker_setup(wl)
     seed = wl.seed + rank            # independent replica per rank
     X = load_data(wl, dev, seed)
