@@ -75,3 +75,37 @@ def test_prepared_round_replays_from_a_cuda_graph(ctx, strategy):
         ctx.set_stream(old if isinstance(old, torch.cuda.Stream) else torch.cuda.current_stream())
     ctx.check_status()
     same(ref, gb)
+
+
+def test_round_arguments_are_checked(ctx):
+    X = mixture(1000, 8, 3, 7)
+    b = H.Batch(8, [100, 100], [3, 3])
+    with pytest.raises(H.HPCError):
+        H.hpc_round(ctx, X, b, 7, 0, 0)                       # unknown strategy
+    with pytest.raises(H.HPCError):
+        H.hpc_round(ctx, X, b, H.HPC_COMPETITIVE, 0, 0, max_iter=100_001)
+    with pytest.raises(H.HPCError):
+        H.hpc_round(ctx, X, b, H.HPC_COMPETITIVE, 0, 0, n_candidates=9)
+    with pytest.raises(H.HPCError):
+        H.hpc_round(ctx, X, H.Batch(8, [0, 100], [3, 3]), H.HPC_COMPETITIVE, 0, 0)  # s = 0
+    fresh = H.Context(0)
+    try:
+        with pytest.raises(H.HPCError):
+            H.hpc_round_enqueue(fresh)                         # nothing prepared
+    finally:
+        fresh.close()
+    ctx.check_status()
+
+
+def test_readme_example_runs(ctx):
+    from paper_2311_04517_gb300 import synth
+    X = synth.make_data("tiny", "cuda")
+    batch = H.Batch(2, s=[2000] * 4, k=[5] * 4)
+    for r in range(3):
+        H.hpc_round(ctx, X, batch, H.HPC_COMPETITIVE, seed=0, round_=r)
+    best = int(torch.argmin(batch.fhat))
+    C, deg = batch.centroids(best)
+    labels = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
+    f = H.hpc_objective(ctx, X, C, deg, labels_out=labels)
+    ctx.check_status()
+    assert float(f.item()) > 0 and int(labels.max()) < 5
