@@ -423,7 +423,7 @@ def run_mine(args):
     # end to end: host-resident (pinned) data copied in every step, results read back
     E = args.e2e_steps if args.e2e_steps is not None else max(3, min(K, 20))
     X_host = X.cpu().pin_memory()
-    res_host = torch.empty(len(groups) + wl.W, dtype=torch.float64).pin_memory()
+    res_host = torch.empty(len(groups) * 8 + wl.W, dtype=torch.float64).pin_memory()
     C_host = torch.empty_like(batch.C, device="cpu").pin_memory()
     e_iters = torch.zeros((E, wl.W), dtype=torch.int32, device=dev)
     e_best = []
@@ -431,17 +431,40 @@ def run_mine(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
+    # Each step copies X in row chunks; the objective of the current best
+    # incumbents runs on every chunk as soon as it has arrived (it is a sum
+    # over rows), behind the copy; the round then runs on the complete X.
+    # Work per step: one full copy, one full objective per group, one round.
+    nck = 8
+    rows = (wl.n + nck - 1) // nck
+    rows = (rows + 3) // 4 * 4                      # 16-byte aligned chunk starts
+    f_chunks = torch.zeros((len(groups), nck), dtype=torch.float64, device=dev)
+    main = torch.cuda.current_stream(dev)
+    copy_stream = torch.cuda.Stream(dev)
+    arrived = [torch.cuda.Event() for _ in range(nck)]
     for i in range(E):
-        X.copy_(X_host, non_blocking=True)
-        run_round(r0 + i)
-        e_iters[i].copy_(batch.iters, non_blocking=True)
         bs = bests()
         e_best.append(bs)
-        for gi, b in enumerate(bs):
-            C, deg = batch.centroids(b)
-            H.hpc_objective(ctx, X, C, deg, f_out=f_sse[gi:gi + 1])
-        res_host[:len(groups)].copy_(f_sse, non_blocking=True)
-        res_host[len(groups):].copy_(batch.fhat, non_blocking=True)
+        copy_stream.wait_stream(main)               # X is free once the last step is done
+        with torch.cuda.stream(copy_stream):
+            for c in range(nck):
+                a, b_ = c * rows, min(wl.n, (c + 1) * rows)
+                if a < b_:
+                    X[a:b_].copy_(X_host[a:b_], non_blocking=True)
+                arrived[c].record(copy_stream)
+        for c in range(nck):
+            a, b_ = c * rows, min(wl.n, (c + 1) * rows)
+            main.wait_event(arrived[c])
+            if a >= b_:
+                continue
+            for gi, b in enumerate(bs):
+                C, deg = batch.centroids(b)
+                H.hpc_objective(ctx, X[a:b_], C, deg, f_out=f_chunks[gi, c:c + 1])
+        run_round(r0 + i)
+        e_iters[i].copy_(batch.iters, non_blocking=True)
+        # per-chunk objectives are read back and added on the host
+        res_host[:len(groups) * nck].copy_(f_chunks.view(-1), non_blocking=True)
+        res_host[len(groups) * nck:].copy_(batch.fhat, non_blocking=True)
         C_host.copy_(batch.C, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
