@@ -10,7 +10,8 @@
 //
 // Exactness: with E = (D + 4) u (||x|| + max||c||)^2, u = 2^-24, D the padded
 // dimension, every computed value lies within E of the exact one; keys add at
-// most 2^-18 |v|.  A row whose top-2 margin exceeds 2E + 2^-17 (|k1| + |k2|)
+// most 2^(IB-23) |v| (IB = 5 or 7 index bits).  A row whose top-2 margin
+// exceeds 2E + 2^(IB-22) (|k1| + |k2|)
 // therefore has the true nearest centroid.  Rows at or under it are rescored
 // by the whole warp: FP32 direct form against every centroid, with its
 // relative bound (D + 3) u, and rows still unresolved in FP64 direct form in
@@ -160,11 +161,20 @@ __device__ __forceinline__ float hpc_key(float v, int j) {
   return __int_as_float((__float_as_int(v) & ~31) | j);
 }
 
-// Top-2 search of R register rows over all centroids.  PACKED (k <= 32):
-// d1/d2 are (value, index) keys and j1 is read from d1's low bits.
-template <int D, int R, bool PACKED>
+// (value, index) key with the index in the low IB mantissa bits: the key is
+// within 2^(IB-23) |v| of v.
+template <int IB>
+__device__ __forceinline__ float hpc_key_b(float v, int j) {
+  return __int_as_float((__float_as_int(v) & ~((1 << IB) - 1)) | j);
+}
+
+// Top-2 search of R register rows over all centroids.  IB > 0 (k <= 2^IB):
+// d1/d2 are (value, index) keys with the index in the low IB bits, and j1
+// is read from d1's low bits; IB = 0: values and a tracked index.
+template <int D, int R, int IB>
 __device__ __forceinline__ void hpc_top2(const float (&x)[R][D], const hpc_cent_smem &cs,
                                          float (&d1)[R], int (&j1)[R], float (&d2)[R]) {
+  constexpr bool PACKED = IB > 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     d1[r] = __int_as_float(0x7f7fffff);
@@ -178,7 +188,7 @@ __device__ __forceinline__ void hpc_top2(const float (&x)[R][D], const hpc_cent_
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if constexpr (PACKED) {
-        const float ka = hpc_key(va[r], j), kb = hpc_key(vb[r], j + 1);
+        const float ka = hpc_key_b<IB>(va[r], j), kb = hpc_key_b<IB>(vb[r], j + 1);
         d2[r] = fminf(d2[r], fmaxf(d1[r], ka));
         d1[r] = fminf(d1[r], ka);
         d2[r] = fminf(d2[r], fmaxf(d1[r], kb));
@@ -197,7 +207,7 @@ __device__ __forceinline__ void hpc_top2(const float (&x)[R][D], const hpc_cent_
   }
   if constexpr (PACKED) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) j1[r] = min(__float_as_int(d1[r]) & 31, cs.kp - 1);
+    for (int r = 0; r < R; ++r) j1[r] = min(__float_as_int(d1[r]) & ((1 << IB) - 1), cs.kp - 1);
   }
 }
 
@@ -328,7 +338,7 @@ __device__ __noinline__ int hpc_exact_row32(const float (&x)[D], const hpc_cent_
 // base + r * THREADS + tid).  Every thread of the block must call it with
 // the same base.  Returns the FP32 sum of the direct-form distances of the
 // thread's valid rows; valid[r] / lab[r] describe each row.
-template <int D, int R, int THREADS, bool PACKED>
+template <int D, int R, int THREADS, int IB>
 __device__ __forceinline__ float hpc_assign_group(const float *__restrict__ X, int64_t n, int d,
                                                   int64_t base, const hpc_cent_smem &cs,
                                                   int (&lab)[R], bool (&valid)[R], int *status) {
@@ -346,7 +356,7 @@ __device__ __forceinline__ float hpc_assign_group(const float *__restrict__ X, i
     }
   }
   float d1[R], d2[R];
-  hpc_top2<D, R, PACKED>(x, cs, d1, lab, d2);
+  hpc_top2<D, R, IB>(x, cs, d1, lab, d2);
   float dd[R];
   bool flag[R];
 #pragma unroll
@@ -358,7 +368,8 @@ __device__ __forceinline__ float hpc_assign_group(const float *__restrict__ X, i
     // ||x|| <= sqrt(dd) + ||c_j1|| <= sqrt(dd) + cmax
     const float rad = sqrtf(dd[r]) * 1.0001f + 2.0f * cs.cmax * 1.00001f;
     float bound = 2.001f * (float)(D + 4) * HPC_U32 * rad * rad;
-    if (PACKED) bound += 7.7e-6f * (fabsf(d1[r]) + fabsf(d2[r]));  // 2^-17 (|k1| + |k2|)
+    // keys: 2 * 2^(IB-23) (|k1| + |k2|)
+    if (IB > 0) bound += 1.0001f * ldexpf(1.0f, IB - 22) * (fabsf(d1[r]) + fabsf(d2[r]));
     const bool ok = found && isfinite(dd[r]);
     flag[r] = valid[r] && ok && !(d2[r] - d1[r] > bound);
     if (valid[r] && !ok) {  // NaN/inf row or out-of-range distance

@@ -68,7 +68,7 @@ struct LloydSmem {
   }
 };
 
-template <int D, int R, int THREADS, bool PACKED>
+template <int D, int R, int THREADS, int IB>
 __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_red[2];
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
       const int64_t base = g * TR;
       int lab[R];
       bool valid[R];
-      fpart += (double)hpc_assign_group<D, R, THREADS, PACKED>(tk.S, s, d, base, cs, lab, valid,
+      fpart += (double)hpc_assign_group<D, R, THREADS, IB>(tk.S, s, d, base, cs, lab, valid,
                                                                a.status);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -274,7 +274,7 @@ struct ObjArgs {
   unsigned *done_count;
 };
 
-template <int D, int R, int THREADS, bool PACKED>
+template <int D, int R, int THREADS, int IB>
 __global__ void __launch_bounds__(THREADS, D <= 16 ? 2 : 1) objective_kernel(ObjArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float s_red[2];
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, D <= 16 ? 2 : 1) objective_kernel(Obj
       const int64_t base = g * TR;
       int lab[R];
       bool valid[R];
-      fpart += (double)hpc_assign_group<D, R, THREADS, PACKED>(a.X, a.n, a.d, base, cs, lab, valid,
+      fpart += (double)hpc_assign_group<D, R, THREADS, IB>(a.X, a.n, a.d, base, cs, lab, valid,
                                                                a.status);
       if (a.labels) {
 #pragma unroll
@@ -320,10 +320,10 @@ __global__ void __launch_bounds__(THREADS, D <= 16 ? 2 : 1) objective_kernel(Obj
   }
 }
 
-template <int D, bool PACKED>
+template <int D, int IB>
 int lloyd_plan_t(const hpc_launch &L, LloydLaunch &h) {
   using T = LTile<D>;
-  auto kern = lloyd_kernel<D, T::R, T::THREADS, PACKED>;
+  auto kern = lloyd_kernel<D, T::R, T::THREADS, IB>;
   const LloydSmem with(D, T::R, T::THREADS, h.kmax, h.d, true);
   const LloydSmem without(D, T::R, T::THREADS, h.kmax, h.d, false);
   const bool smem_sums = with.total <= (size_t)L.smem_optin;
@@ -364,10 +364,10 @@ int lloyd_plan_t(const hpc_launch &L, LloydLaunch &h) {
   return HPC_OK;
 }
 
-template <int D, bool PACKED>
+template <int D, int IB>
 int lloyd_run_t(const hpc_launch &L, const LloydLaunch &h) {
   using T = LTile<D>;
-  auto kern = lloyd_kernel<D, T::R, T::THREADS, PACKED>;
+  auto kern = lloyd_kernel<D, T::R, T::THREADS, IB>;
   LloydArgs a;
   a.W = h.W;
   a.single = h.tasks[0];
@@ -384,10 +384,10 @@ int lloyd_run_t(const hpc_launch &L, const LloydLaunch &h) {
   return e == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 
-template <int D, bool PACKED>
+template <int D, int IB>
 int objective_launch_t(const hpc_launch &L, const ObjArgsHost &h) {
   using T = Tile<D>;
-  auto kern = objective_kernel<D, T::R, T::THREADS, PACKED>;
+  auto kern = objective_kernel<D, T::R, T::THREADS, IB>;
   const size_t smem = hpc_cent_smem_bytes(D, h.k);
   if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -418,19 +418,22 @@ int objective_launch_t(const hpc_launch &L, const ObjArgsHost &h) {
   return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 
+// index bits of the packed top-2 keys: 5 for k <= 32; larger k keeps values
+// and a tracked index (7-bit keys for k <= 128 were measured slower: their
+// wider error window sends more rows to the exact stages)
 template <int D>
 int lloyd_plan_d(const hpc_launch &L, LloydLaunch &h) {
-  return h.kmax <= 32 ? lloyd_plan_t<D, true>(L, h) : lloyd_plan_t<D, false>(L, h);
+  return h.kmax <= 32 ? lloyd_plan_t<D, 5>(L, h) : lloyd_plan_t<D, 0>(L, h);
 }
 
 template <int D>
 int lloyd_run_d(const hpc_launch &L, const LloydLaunch &h) {
-  return h.kmax <= 32 ? lloyd_run_t<D, true>(L, h) : lloyd_run_t<D, false>(L, h);
+  return h.kmax <= 32 ? lloyd_run_t<D, 5>(L, h) : lloyd_run_t<D, 0>(L, h);
 }
 
 template <int D>
 int objective_dispatch(const hpc_launch &L, const ObjArgsHost &h) {
-  return h.k <= 32 ? objective_launch_t<D, true>(L, h) : objective_launch_t<D, false>(L, h);
+  return h.k <= 32 ? objective_launch_t<D, 5>(L, h) : objective_launch_t<D, 0>(L, h);
 }
 
 }  // namespace
