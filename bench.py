@@ -191,6 +191,26 @@ def workload_config(wl, strategy, args):
             "lloyd_max_iter": 300, "lloyd_rel_tol": 1e-4, "kmeanspp_candidates": 3}
 
 
+def replica_seed(wl, rank: int) -> int:
+    """Ranks run independent replicas of the workload (weak scaling): each
+    draws its own data and samples from its own seed."""
+    return wl.seed + rank
+
+
+def job_totals(ms: float, dist_total: float, device):
+    """Whole-job figures over the ranks of an initialised process group: the
+    slowest rank's time and the sum of the distances every rank evaluated
+    (no collective on the data path; this is the only exchange)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, dist_total
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dd = torch.tensor([dist_total], dtype=torch.float64, device=device)
+    dist.all_reduce(dd)
+    return float(t.item()), float(dd.item())
+
+
 def bench_workload(args):
     wl = synth.workload(args.workload)
     if args.rows is not None:
@@ -321,7 +341,7 @@ def run_mine(args):
     dev = torch.device("cuda", local)
     wl = bench_workload(args)
     ws = synth.worker_setup(wl)
-    seed = wl.seed + rank            # independent replica per rank
+    seed = replica_seed(wl, rank)
     X = load_data(wl, dev, seed)
     strategy = {"cooperative": H.HPC_COOPERATIVE, "hybrid": H.HPC_HYBRID}.get(
         args.strategy, H.HPC_COMPETITIVE)
@@ -411,13 +431,7 @@ def run_mine(args):
     iters = iters_log.cpu().numpy()
     dist_total = sum(dist_count(iters[i], ws.s, ws.k, wl.n, [int(ws.k[b]) for b in best_log[i]])
                      for i in range(K))
-    if dist_ok:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dd = torch.tensor([dist_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(dd)
-        dist_total = float(dd.item())
+    ms, dist_total = job_totals(ms, dist_total, dev)
     value = dist_total / (ms / 1e3)
 
     # end to end: host-resident (pinned) data copied in every step, results read back
@@ -472,13 +486,7 @@ def run_mine(args):
     ei = e_iters.cpu().numpy()
     e_dist = sum(dist_count(ei[i], ws.s, ws.k, wl.n, [int(ws.k[b]) for b in e_best[i]])
                  for i in range(E))
-    if dist_ok:
-        t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-        dd = torch.tensor([e_dist], dtype=torch.float64, device=dev)
-        dist.all_reduce(dd)
-        e_dist = float(dd.item())
+    e_ms, e_dist = job_totals(e_ms, e_dist, dev)
     e_value = e_dist / (e_ms / 1e3)
 
     hbm, src = peaks()
