@@ -235,7 +235,7 @@ __device__ __forceinline__ void warp_norm_direct(const float *__restrict__ X, in
   }
 }
 
-template <int D, int NP, bool PACKED>
+template <int D, int NP, int IB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_objective_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
   using Cfg = TcCfg<D>;
@@ -404,17 +404,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const float v0 = cn.x + acc[jj], v1 = cn.y + acc[jj + 1];
           const float v2 = cn.z + acc[jj + 2], v3 = cn.w + acc[jj + 3];
           const int j = c * 32 + jj;
-          if constexpr (PACKED) {
-            const float k0 = hpc_key(v0, j), k1 = hpc_key(v1, j + 1);
-            const float k2 = hpc_key(v2, j + 2), k3 = hpc_key(v3, j + 3);
-            d2 = fminf(d2, fmaxf(d1, k0));
-            d1 = fminf(d1, k0);
-            e2 = fminf(e2, fmaxf(e1, k1));
-            e1 = fminf(e1, k1);
-            d2 = fminf(d2, fmaxf(d1, k2));
-            d1 = fminf(d1, k2);
-            e2 = fminf(e2, fmaxf(e1, k3));
-            e1 = fminf(e1, k3);
+          if constexpr (IB > 0) {
+            hpc_top2_fold4(d1, d2, hpc_key_b<IB>(v0, j), hpc_key_b<IB>(v1, j + 1),
+                           hpc_key_b<IB>(v2, j + 2), hpc_key_b<IB>(v3, j + 3));
           } else {
 #define HPC_TOP2_STEP(V, J, A1, B1, A2, B2) \
   if (V < A1) {                             \
@@ -434,12 +426,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
-      if constexpr (PACKED) {
+      if constexpr (IB > 0) {
         const float lo = fminf(d1, e1);
         d2 = fminf(fmaxf(d1, e1), fminf(d2, e2));
         d1 = lo;
-        j1 = min(__float_as_int(d1) & 31, cs.kp - 1);
-        j2 = min(__float_as_int(d2) & 31, cs.kp - 1);
+        j1 = min(__float_as_int(d1) & ((1 << IB) - 1), cs.kp - 1);
+        j2 = min(__float_as_int(d2) & ((1 << IB) - 1), cs.kp - 1);
       } else {
         // merge (d1 j1, d2 j2) with (e1 je, e2 je2); lower index on equal values
         float m1, m2;
@@ -486,7 +478,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       const float rad = sqrtf(nx) * 1.0001f + cs.cmax * 1.0001f;
       float win = 2.0f * 9.765625e-04f * rad * rad;  // 2E, E = 2^-10 (||x|| + max||c||)^2
-      if (PACKED) win += 7.7e-6f * (fabsf(d1) + fabsf(d2));
+      if (IB > 0) win += 1.0001f * ldexpf(1.0f, IB - 22) * (fabsf(d1) + fabsf(d2));  // keys
       const bool ok = found && isfinite(nx) && isfinite(win);
       if (valid && !ok) {
         hpc_status_set(a.status, HPC_ERR_NONFINITE);
@@ -619,11 +611,11 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <int D, int NP, bool PACKED>
+template <int D, int NP, int IB>
 int tc_launch_t(const hpc_launch &Lc, const ObjArgsHost &h) {
   using Cfg = TcCfg<D>;
   using L = TcSmem<D, NP>;
-  auto kern = tc_objective_kernel<D, NP, PACKED>;
+  auto kern = tc_objective_kernel<D, NP, IB>;
   // as many ring slots as the shared memory allows (2 .. 16, and at least a
   // full tile); at least 120 KB requested so that one block fills an SM
   int nsx = TC_MAX_RING;
@@ -668,11 +660,13 @@ int tc_launch_t(const hpc_launch &Lc, const ObjArgsHost &h) {
   return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 
+// (value, index) keys with 5 index bits for k <= 32, 7 above: the keys'
+// error (2^-16 relative at 7 bits) is far inside the TF32 products' window
 template <int D>
 int tc_dispatch(const hpc_launch &L, const ObjArgsHost &h) {
-  if (h.k <= 32) return tc_launch_t<D, 32, true>(L, h);
-  if (h.k <= 64) return tc_launch_t<D, 64, false>(L, h);
-  return tc_launch_t<D, 128, false>(L, h);
+  if (h.k <= 32) return tc_launch_t<D, 32, 5>(L, h);
+  if (h.k <= 64) return tc_launch_t<D, 64, 7>(L, h);
+  return tc_launch_t<D, 128, 7>(L, h);
 }
 
 }  // namespace

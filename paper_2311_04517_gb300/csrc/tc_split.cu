@@ -136,7 +136,7 @@ __device__ __forceinline__ bool wg_sync_and(bool v, int wg) {
   return r != 0;
 }
 
-template <int D, int NP, bool PACKED>
+template <int D, int NP, int IB>
 __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
     tcs_objective_kernel(const __grid_constant__ CUtensorMap tmap, TsArgs a) {
   using Cfg = TsCfg<D, NP>;
@@ -323,14 +323,16 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
           if (c * 32 >= cs.kp) break;  // same for the whole CTA
           float acc[32];
           hpc_tmem_ld32(tmem + lane_base + d_col + (uint32_t)((i & 1) * NP + 32 * c), acc);
-          if constexpr (PACKED) {
+          if constexpr (IB > 0) {
 #pragma unroll
             for (int jj = 0; jj < 32; jj += 4) {
               if (c * 32 + jj >= cs.kp) break;
               const float4 cn = *reinterpret_cast<const float4 *>(cnv + c * 32 + jj);
               const int j = c * 32 + jj;
-              hpc_top2_fold4(d1, d2, hpc_key(cn.x + acc[jj], j), hpc_key(cn.y + acc[jj + 1], j + 1),
-                             hpc_key(cn.z + acc[jj + 2], j + 2), hpc_key(cn.w + acc[jj + 3], j + 3));
+              hpc_top2_fold4(d1, d2, hpc_key_b<IB>(cn.x + acc[jj], j),
+                             hpc_key_b<IB>(cn.y + acc[jj + 1], j + 1),
+                             hpc_key_b<IB>(cn.z + acc[jj + 2], j + 2),
+                             hpc_key_b<IB>(cn.w + acc[jj + 3], j + 3));
             }
           } else {
 #pragma unroll
@@ -360,9 +362,9 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
             }
           }
         }
-        if constexpr (PACKED) {
-          j1 = min(__float_as_int(d1) & 31, cs.kp - 1);
-          j2 = min(__float_as_int(d2) & 31, cs.kp - 1);
+        if constexpr (IB > 0) {
+          j1 = min(__float_as_int(d1) & ((1 << IB) - 1), cs.kp - 1);
+          j2 = min(__float_as_int(d2) & ((1 << IB) - 1), cs.kp - 1);
         } else {
           // merge the even / odd chains, lower index on equal values
           if (e1 < d1 || (e1 == d1 && je < j1)) {
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
         // root, 2 ulp, covered by the 1.0001 factor)
         const float rad = dd * rsqrtf(dd + 1e-30f) * 1.0001f + 2.0f * cs.cmax * 1.00001f;
         float win = 2.0f * 1.52587890625e-05f * rad * rad;  // 2E, E = 2^-16 (||x|| + cmax)^2
-        if (PACKED) win += 7.7e-6f * (fabsf(d1) + fabsf(d2));
+        if (IB > 0) win += 1.0001f * ldexpf(1.0f, IB - 22) * (fabsf(d1) + fabsf(d2));  // keys
         const bool ok = found && isfinite(dd) && isfinite(win);
         if (valid && !ok) {
           hpc_status_set(a.status, HPC_ERR_NONFINITE);
@@ -552,10 +554,10 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <int D, int NP, bool PACKED>
+template <int D, int NP, int IB>
 int tcs_launch_t(const hpc_launch &Lc, const ObjArgsHost &h) {
   using Cfg = TsCfg<D, NP>;
-  auto kern = tcs_objective_kernel<D, NP, PACKED>;
+  auto kern = tcs_objective_kernel<D, NP, IB>;
   const size_t smem = Cfg::total(h.k);
   if (smem > (size_t)Lc.smem_optin) return HPC_ERR_UNSUPPORTED;
   EncodeTiledFn enc = encode_fn();
@@ -600,9 +602,9 @@ int tcs_launch_t(const hpc_launch &Lc, const ObjArgsHost &h) {
 
 template <int D>
 int tcs_dispatch(const hpc_launch &L, const ObjArgsHost &h) {
-  if (h.k <= 32) return tcs_launch_t<D, 32, true>(L, h);
-  if (h.k <= 64) return tcs_launch_t<D, 64, false>(L, h);
-  return tcs_launch_t<D, 128, false>(L, h);
+  if (h.k <= 32) return tcs_launch_t<D, 32, 5>(L, h);
+  if (h.k <= 64) return tcs_launch_t<D, 64, 7>(L, h);
+  return tcs_launch_t<D, 128, 7>(L, h);
 }
 
 }  // namespace
