@@ -266,100 +266,6 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
   return HPC_OK;
 }
 
-// One worker of a batched round, as the base-selection and incumbent
-// kernels see it.
-struct RoundWorker {
-  int64_t s;
-  int64_t C_off, K_off;
-  int k, group;
-  float *Cn;    // base, then Lloyd's result
-  uint8_t *dn;
-  double *fw;   // Lloyd objective (NaN until written)
-  int32_t *itw;
-};
-
-// Base of every worker (Algorithm 3: its own incumbent; Algorithm 4: the
-// incumbent with the smallest objective per sample point among the workers
-// of its group with its k, lowest index on ties).  All bases are read before
-// any incumbent of this round changes, which is the round-start snapshot.
-__global__ void __launch_bounds__(256) base_select_kernel(const RoundWorker *__restrict__ wk, int W,
-                                                          int strategy, int32_t n_competitive,
-                                                          const uint32_t *round_dev, uint32_t round,
-                                                          const double *__restrict__ fhat,
-                                                          const float *__restrict__ Cpool,
-                                                          const uint8_t *__restrict__ Kpool, int d) {
-  __shared__ double s_f[256];
-  __shared__ int s_v[256];
-  // Algorithm 5: the competitive phase for rounds below n_competitive
-  const uint32_t rnd = round_dev ? *round_dev : round;
-  const bool cooperative = strategy == HPC_COOPERATIVE ||
-                           (strategy == HPC_HYBRID && (int64_t)rnd >= (int64_t)n_competitive);
-  const int w = blockIdx.x;
-  const RoundWorker me = wk[w];
-  double bf = fhat[w];
-  int bv = w;
-  if (cooperative) {
-    for (int v = threadIdx.x; v < W; v += blockDim.x) {
-      const RoundWorker o = wk[v];
-      if (o.group != me.group || o.k != me.k) continue;
-      const double f = fhat[v];
-      if (f < bf || (f == bf && v < bv)) {
-        bf = f;
-        bv = v;
-      }
-    }
-  }
-  s_f[threadIdx.x] = bf;
-  s_v[threadIdx.x] = bv;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) {
-      const double f = s_f[threadIdx.x + h];
-      const int v = s_v[threadIdx.x + h];
-      if (f < s_f[threadIdx.x] || (f == s_f[threadIdx.x] && v < s_v[threadIdx.x])) {
-        s_f[threadIdx.x] = f;
-        s_v[threadIdx.x] = v;
-      }
-    }
-    __syncthreads();
-  }
-  const int b = s_v[0];
-  const int64_t coff = wk[b].C_off, koff = wk[b].K_off;
-  const int kd = me.k * d;
-  for (int e = threadIdx.x; e < kd; e += blockDim.x) me.Cn[e] = Cpool[coff + e];
-  for (int j = threadIdx.x; j < me.k; j += blockDim.x) me.dn[j] = Kpool[koff + j];
-  if (threadIdx.x == 0) {
-    *me.fw = __longlong_as_double(0x7ff8000000000000ll);  // a failed run is never accepted
-    *me.itw = 0;
-  }
-}
-
-// Incumbent rule of Algorithms 3-4: replace C_w when f / s_w < fhat_w.
-__global__ void __launch_bounds__(256) incumbent_kernel(const RoundWorker *__restrict__ wk, int d,
-                                                        double *__restrict__ fhat, float *__restrict__ Cpool,
-                                                        uint8_t *__restrict__ Kpool, double *f_new,
-                                                        int32_t *iters, uint8_t *accepted,
-                                                        uint32_t *round_advance) {
-  const int w = blockIdx.x;
-  // the last kernel of a round moves a prepared round's counter on
-  if (round_advance && w == 0 && threadIdx.x == 0) *round_advance += 1u;
-  const RoundWorker me = wk[w];
-  const double f = *me.fw;
-  const double per = f / (double)me.s;
-  const bool acc = per < fhat[w];
-  if (acc) {
-    const int kd = me.k * d;
-    for (int e = threadIdx.x; e < kd; e += blockDim.x) Cpool[me.C_off + e] = me.Cn[e];
-    for (int j = threadIdx.x; j < me.k; j += blockDim.x) Kpool[me.K_off + j] = me.dn[j];
-  }
-  if (threadIdx.x == 0) {
-    if (acc) fhat[w] = per;
-    if (f_new) f_new[w] = f;
-    if (iters) iters[w] = *me.itw;
-    if (accepted) accepted[w] = acc ? 1 : 0;
-  }
-}
-
 // Block 0 waits at a grid barrier that block 1 never reaches; the bounded
 // wait gives up after limit_ns and records HPC_ERR_TIMEOUT.
 __global__ void selftest_timeout_kernel(hpc_gridbar *bar, int *status, uint64_t limit_ns) {
@@ -426,7 +332,7 @@ struct hpc_round_plan {
   int32_t *iters = nullptr;
   uint8_t *accepted = nullptr;
   TaskHeader *hdr = nullptr;
-  const RoundWorker *rw_d = nullptr;
+  const hpc_round_worker *rw_d = nullptr;
   const hpc_sample_task *st_d = nullptr;
   std::vector<char> host;  // host image of the tables of a prepared round
   std::vector<KppLaunch> kl;
@@ -465,7 +371,7 @@ static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, i
             pad256((size_t)2 * c->grid_bound * 8) + pad256((size_t)s * 4) +
             pad256((size_t)L * s * 4) + pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8);
   }
-  *tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) + pad256((size_t)W * sizeof(RoundWorker)) +
+  *tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) + pad256((size_t)W * sizeof(hpc_round_worker)) +
                pad256((size_t)W * sizeof(hpc_kpp_task)) + pad256((size_t)W * sizeof(hpc_lloyd_task)) +
                2 * (size_t)nchunks * pad256((size_t)c->grid_bound * 4);
   return need + pad256((size_t)W * 8) + pad256((size_t)W * 4) + *tab_bytes + 1024;
@@ -488,8 +394,8 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
   Carver th{tab_host, 0, tab_bytes}, td{tab_dev, 0, tab_bytes};
   hpc_sample_task *st_h = th.take<hpc_sample_task>((size_t)W);
   hpc_sample_task *st_d = td.take<hpc_sample_task>((size_t)W);
-  RoundWorker *rw_h = th.take<RoundWorker>((size_t)W);
-  RoundWorker *rw_d = td.take<RoundWorker>((size_t)W);
+  hpc_round_worker *rw_h = th.take<hpc_round_worker>((size_t)W);
+  hpc_round_worker *rw_d = td.take<hpc_round_worker>((size_t)W);
   hpc_kpp_task *kt_h = th.take<hpc_kpp_task>((size_t)W);
   hpc_kpp_task *kt_d = td.take<hpc_kpp_task>((size_t)W);
   hpc_lloyd_task *lt_h = th.take<hpc_lloyd_task>((size_t)W);
@@ -501,7 +407,7 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     float *Cn = cv.take<float>((size_t)k * d);
     uint8_t *dn = cv.take<uint8_t>((size_t)k);
     st_h[w] = hpc_sample_task{S, nullptr, s, (uint32_t)w};
-    rw_h[w] = RoundWorker{s, b->C_off[w], b->K_off[w], k, b->group ? b->group[w] : 0, Cn, dn,
+    rw_h[w] = hpc_round_worker{s, b->C_off[w], b->K_off[w], k, b->group ? b->group[w] : 0, Cn, dn,
                           fw + w, itw + w};
     hpc_kpp_task &kt = kt_h[w];
     kt = hpc_kpp_task{};
@@ -522,6 +428,13 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     lt.f_out = fw + w;
     lt.iters_out = itw + w;
     lloyd_task_scratch(c, cv, hdr + w, d, k, lt);
+    // the incumbent rule runs at the end of the worker's Lloyd run
+    lt.fhat = b->fhat + w;
+    lt.C_inc = b->C + b->C_off[w];
+    lt.deg_inc = b->degenerate + b->K_off[w];
+    lt.f_new = b->f_new ? b->f_new + w : nullptr;
+    lt.iters_rep = b->iters ? b->iters + w : nullptr;
+    lt.accepted = b->accepted ? b->accepted + w : nullptr;
   }
   // plans of the persistent launches, HPC_ROUND_CHUNK workers each
   p.kl.assign(nchunks, KppLaunch{});
@@ -581,32 +494,43 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
   return HPC_OK;
 }
 
-// One round: a memset of the task headers and 3 + 2 * chunks launches; no
-// host synchronisation, no allocation (a stream capture can record it).  The
-// round index is `round`, or *round_dev when that is given (a prepared round,
-// whose incumbent kernel then advances it).
+// One round: a memset of the task headers and 1 + 2 * chunks launches (the
+// sampling launch also selects every worker's base; each Lloyd task applies
+// the incumbent rule when its run is done); no host synchronisation, no
+// allocation (a stream capture can record it).  The round index is `round`,
+// or *round_dev when that is given (a prepared round, whose last Lloyd
+// launch then advances it).
 static int round_enqueue(hpc_ctx *c, const hpc_round_plan &p, uint32_t *round_dev, uint32_t round) {
   cudaError_t e = cudaMemsetAsync(p.hdr, 0, (size_t)p.W * sizeof(TaskHeader), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "round set-up");
+  hpc_base_args base{};
+  base.wk = p.rw_d;
+  base.W = p.W;
+  base.strategy = p.strategy;
+  base.n_competitive = p.n_competitive;
+  base.round_dev = round_dev;
+  base.round = round;
+  base.fhat = p.fhat;
+  base.Cpool = p.C;
+  base.Kpool = p.deg;
+  base.d = p.d;
+  base.f_new = p.f_new;
+  base.iters = p.iters;
+  base.accepted = p.accepted;
   if (int rc = hpc_sample_batch_launch(c->L, p.X, p.n, p.d, p.seed, round, round_dev, p.W, p.st_d,
-                                       p.smax))
+                                       p.smax, base))
     return plan_fail(c, rc, "sample launch");
-  base_select_kernel<<<p.W, 256, 0, c->stream>>>(p.rw_d, p.W, p.strategy, p.n_competitive, round_dev,
-                                                 round, p.fhat, p.C, p.deg, p.d);
-  if ((e = cudaGetLastError())) return cuda_fail(c, e, "base launch");
-  c->launches += 2;
+  c->launches += 1;
   for (size_t ch = 0; ch < p.kl.size(); ++ch) {
     KppLaunch kh = p.kl[ch];
     kh.round = round;
     kh.round_dev = round_dev;
     if (int rc = hpc_kmeanspp_run(c->L, kh)) return plan_fail(c, rc, "kmeanspp launch");
-    if (int rc = hpc_lloyd_run(c->L, p.ll[ch])) return plan_fail(c, rc, "lloyd launch");
+    LloydLaunch lh = p.ll[ch];
+    lh.round_advance = ch + 1 == p.kl.size() ? round_dev : nullptr;
+    if (int rc = hpc_lloyd_run(c->L, lh)) return plan_fail(c, rc, "lloyd launch");
     c->launches += 2;
   }
-  incumbent_kernel<<<p.W, 256, 0, c->stream>>>(p.rw_d, p.d, p.fhat, p.C, p.deg, p.f_new, p.iters,
-                                               p.accepted, round_dev);
-  if ((e = cudaGetLastError())) return cuda_fail(c, e, "incumbent launch");
-  c->launches += 1;
   return HPC_OK;
 }
 

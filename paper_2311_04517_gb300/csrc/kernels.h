@@ -38,6 +38,13 @@ struct hpc_lloyd_task {
   unsigned long long *gsum;  // 3 * k * d
   unsigned *gcount;          // 3 * k
   double *gpart;             // 2 * blocks of the task
+  // incumbent rule at the end of the run (rounds only; fhat null otherwise)
+  double *fhat;              // this worker's incumbent objective per point
+  float *C_inc;              // its incumbent centroids (k x d) in the pool
+  uint8_t *deg_inc;          // and their flags
+  double *f_new;             // nullable reports
+  int32_t *iters_rep;
+  uint8_t *accepted;
 };
 // Lloyd zeroes gsum / gcount itself; bar and gmaxabs must be zero at launch.
 
@@ -57,6 +64,8 @@ struct LloydLaunch {
   int64_t grid;
   size_t smem;
   int smem_sums;
+  // nullable: a prepared round's counter, advanced once the run is done
+  uint32_t *round_advance;
 };
 
 // ---- K-means++ (one task = one sample) ----
@@ -122,6 +131,34 @@ struct hpc_sample_task {
   uint32_t worker;
 };
 
+// ---- round bookkeeping (Algorithms 3-5) ----
+struct hpc_round_worker {
+  int64_t s;
+  int64_t C_off, K_off;
+  int k, group;
+  float *Cn;    // base, then Lloyd's result
+  uint8_t *dn;
+  double *fw;   // Lloyd objective (NaN until written)
+  int32_t *itw;
+};
+
+// Base selection, run by extra blocks of the batched sampling launch.
+struct hpc_base_args {
+  const hpc_round_worker *wk;  // device [W]; null: no base selection
+  int W;
+  int strategy;
+  int32_t n_competitive;
+  const uint32_t *round_dev;   // nullable
+  uint32_t round;
+  const double *fhat;
+  const float *Cpool;
+  const uint8_t *Kpool;
+  int d;
+  double *f_new;               // nullable reports, reset for the round
+  int32_t *iters;
+  uint8_t *accepted;
+};
+
 // Plan: chooses the kernel variant and the grid, splits the blocks over the
 // tasks (tasks[w].block0 / nblocks, block_task_host).  Run: one cooperative
 // launch; for W > 1 the caller has copied tasks and block_task_host to
@@ -142,7 +179,8 @@ int hpc_sample_launch(const hpc_launch &L, const float *X, int64_t n, int d, uin
 // the round is *round_dev when that is not null.
 int hpc_sample_batch_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
                             uint32_t round, const uint32_t *round_dev, int W,
-                            const hpc_sample_task *tasks_dev, int64_t smax);
+                            const hpc_sample_task *tasks_dev, int64_t smax,
+                            const hpc_base_args &base);
 
 // Blocks the cooperative kernels may use at most (upper bound for scratch
 // sizing): resident blocks per SM times SMs.

@@ -15,6 +15,7 @@
 
 #include "assign.cuh"
 #include "kernels.h"
+#include "round.cuh"
 
 namespace {
 
@@ -28,6 +29,7 @@ struct LloydArgs {
   double tol;
   int *status;
   int smem_sums;  // 1: per-block sums in shared memory
+  uint32_t *round_advance;  // nullable: a prepared round's counter (see the kernel's start)
 };
 
 // Objective: several rows per thread amortise the centroid reads.
@@ -77,6 +79,10 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   __shared__ unsigned s_umax;
   constexpr int LPR = LTile<D>::LPR, RPP = LTile<D>::RPP, TPL = LTile<D>::TPL, NB = LTile<D>::NB;
 
+  // The round's last launch moves a prepared round's counter on: every
+  // reader of the round index (sampling, K-means++) ran in earlier launches,
+  // and Lloyd itself does not read it.
+  if (a.round_advance && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.round_advance, 1u);
   // this block's task (one worker's sample) and its place in the task's group
   const hpc_lloyd_task tk = a.W == 1 ? a.single : a.tasks[a.block_task[blockIdx.x]];
   const int k = tk.k, d = a.d;
@@ -224,9 +230,12 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
     const double f = s_f;
     const bool done = (it > 0 && (f_prev == 0.0 || (f_prev - f) < a.tol * f_prev)) || it == a.max_iter;
     if (done) {
-      if (lb == 0 && threadIdx.x == 0) {
-        *tk.f_out = f;
-        if (tk.iters_out) *tk.iters_out = it;
+      if (lb == 0) {
+        if (threadIdx.x == 0) {
+          *tk.f_out = f;
+          if (tk.iters_out) *tk.iters_out = it;
+        }
+        if (tk.fhat) hpc_incumbent_block(tk, d, f, it);  // block-uniform branch
       }
       return;
     }
@@ -378,6 +387,7 @@ int lloyd_run_t(const hpc_launch &L, const LloydLaunch &h) {
   a.tol = h.tol;
   a.status = h.status;
   a.smem_sums = h.smem_sums;
+  a.round_advance = h.round_advance;
   void *args[] = {&a};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)h.grid),
                                                     dim3(T::THREADS), args, h.smem, L.stream);

@@ -5,6 +5,7 @@
 // gathered with 16-byte accesses where the row width allows it.
 #include "common.cuh"
 #include "kernels.h"
+#include "round.cuh"
 
 namespace {
 
@@ -48,8 +49,12 @@ constexpr int SB_THREADS = 256, SB_ROWS = 4 * SB_THREADS;
 template <bool VEC4>
 __global__ void __launch_bounds__(SB_THREADS) sample_batch_kernel(
     const float *__restrict__ X, int64_t n, int d, uint64_t seed, uint32_t round,
-    const uint32_t *round_dev, const hpc_sample_task *__restrict__ tasks) {
+    const uint32_t *round_dev, const hpc_sample_task *__restrict__ tasks, hpc_base_args base) {
   __shared__ int64_t s_idx[SB_ROWS];
+  if (base.wk && blockIdx.x == gridDim.x - 1) {  // the extra block: this worker's base
+    hpc_base_select_block(base, (int)blockIdx.y);
+    return;
+  }
   if (round_dev) round = *round_dev;
   const hpc_sample_task t = tasks[blockIdx.y];
   const int64_t r0 = (int64_t)blockIdx.x * SB_ROWS;
@@ -90,16 +95,18 @@ __global__ void __launch_bounds__(SB_THREADS) sample_batch_kernel(
 
 int hpc_sample_batch_launch(const hpc_launch &L, const float *X, int64_t n, int d, uint64_t seed,
                             uint32_t round, const uint32_t *round_dev, int W,
-                            const hpc_sample_task *tasks_dev, int64_t smax) {
+                            const hpc_sample_task *tasks_dev, int64_t smax,
+                            const hpc_base_args &base) {
   if (W < 1 || smax < 1) return HPC_OK;
   if (W > 65535) return HPC_ERR_ARG;
-  const dim3 grid((unsigned)((smax + SB_ROWS - 1) / SB_ROWS), (unsigned)W);
+  // one extra block per worker selects its base when base.wk is given
+  const dim3 grid((unsigned)((smax + SB_ROWS - 1) / SB_ROWS + (base.wk ? 1 : 0)), (unsigned)W);
   if (d % 4 == 0)
     sample_batch_kernel<true><<<grid, SB_THREADS, 0, L.stream>>>(X, n, d, seed, round, round_dev,
-                                                                 tasks_dev);
+                                                                 tasks_dev, base);
   else
     sample_batch_kernel<false><<<grid, SB_THREADS, 0, L.stream>>>(X, n, d, seed, round, round_dev,
-                                                                  tasks_dev);
+                                                                  tasks_dev, base);
   return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 
