@@ -338,12 +338,13 @@ __device__ __noinline__ int hpc_exact_row32(const float (&x)[D], const hpc_cent_
 // base + r * THREADS + tid).  Every thread of the block must call it with
 // the same base.  Returns the FP32 sum of the direct-form distances of the
 // thread's valid rows; valid[r] / lab[r] describe each row.
+// (x receives the thread's rows, zero-padded, for callers that reuse them.)
 template <int D, int R, int THREADS, int IB>
-__device__ __forceinline__ float hpc_assign_group(const float *__restrict__ X, int64_t n, int d,
-                                                  int64_t base, const hpc_cent_smem &cs,
-                                                  int (&lab)[R], bool (&valid)[R], int *status) {
+__device__ __forceinline__ float hpc_assign_group_x(const float *__restrict__ X, int64_t n, int d,
+                                                    int64_t base, const hpc_cent_smem &cs,
+                                                    float (&x)[R][D], int (&lab)[R],
+                                                    bool (&valid)[R], int *status) {
   const int tid = threadIdx.x;
-  float x[R][D];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int64_t i = base + (int64_t)r * THREADS + tid;
@@ -397,6 +398,14 @@ __device__ __forceinline__ float hpc_assign_group(const float *__restrict__ X, i
   for (int r = 0; r < R; ++r)
     if (valid[r]) fsum += dd[r];
   return fsum;
+}
+
+template <int D, int R, int THREADS, int IB>
+__device__ __forceinline__ float hpc_assign_group(const float *__restrict__ X, int64_t n, int d,
+                                                  int64_t base, const hpc_cent_smem &cs,
+                                                  int (&lab)[R], bool (&valid)[R], int *status) {
+  float x[R][D];
+  return hpc_assign_group_x<D, R, THREADS, IB>(X, n, d, base, cs, x, lab, valid, status);
 }
 
 // Fixed-order sum of n doubles by the whole block (thread 0 gets the result).

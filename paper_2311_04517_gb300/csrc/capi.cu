@@ -111,13 +111,14 @@ struct TaskHeader {
   hpc_gridbar kbar;
   unsigned mx[2];
   unsigned long long phi[2 * 8];
-  unsigned char pad1[256 - 32 - 128];
+  unsigned long long gobj[3];  // Lloyd's fixed-point sample objectives
+  unsigned char pad1[256 - 32 - 128 - 24];
 };
 static_assert(sizeof(TaskHeader) == 256, "task header is one 256-byte line");
 
 size_t lloyd_ws(const hpc_ctx *c, int d, int k) {
   return sizeof(TaskHeader) + pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
-         pad256((size_t)2 * c->grid_bound * 8) + pad256((size_t)k) + 256;
+         pad256((size_t)k) + 256;
 }
 
 size_t kpp_ws(const hpc_ctx *c, int64_t s, int L) {
@@ -140,7 +141,7 @@ void lloyd_task_scratch(const hpc_ctx *c, Carver &cv, TaskHeader *hd, int d, int
   t.gmaxabs = &hd->gmaxabs;
   t.gsum = cv.take<unsigned long long>((size_t)3 * k * d);
   t.gcount = cv.take<unsigned>((size_t)3 * k);
-  t.gpart = cv.take<double>((size_t)2 * c->grid_bound);
+  t.gobj = hd->gobj;
 }
 
 void kpp_task_scratch(const hpc_ctx *c, Carver &cv, TaskHeader *hd, int64_t s, int L,
@@ -187,7 +188,7 @@ int run_lloyd(hpc_ctx *c, Carver &cv, const float *S, int64_t s, int d, int k, f
   h.tol = tol;
   h.status = c->dwords;
   h.max_blocks = c->grid_bound;
-  h.gpart_cap = 2 * c->grid_bound;
+  h.task_blocks = c->grid_bound;
   int rc = hpc_lloyd_plan(c->L, h);
   if (rc) return plan_fail(c, rc, "lloyd: unsupported shape");
   if ((rc = hpc_lloyd_run(c->L, h))) return plan_fail(c, rc, "lloyd launch");
@@ -470,7 +471,7 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     lh.tol = rel_tol;
     lh.status = c->dwords;
     lh.max_blocks = c->grid_bound;
-    lh.gpart_cap = 2 * c->grid_bound;
+    lh.task_blocks = c->grid_bound;
     if (int rc = hpc_lloyd_plan(c->L, lh)) return plan_fail(c, rc, "lloyd: unsupported shape");
   }
   if (cv.off > cv.cap || th.off > th.cap) return fail(c, HPC_ERR_NOMEM, "round scratch layout overflow");

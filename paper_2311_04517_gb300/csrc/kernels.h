@@ -37,7 +37,7 @@ struct hpc_lloyd_task {
   unsigned *gmaxabs;    // zero at launch
   unsigned long long *gsum;  // 3 * k * d
   unsigned *gcount;          // 3 * k
-  double *gpart;             // 2 * blocks of the task
+  unsigned long long *gobj;  // 3 rotating fixed-point sample objectives, zero at launch
   // incumbent rule at the end of the run (rounds only; fhat null otherwise)
   double *fhat;              // this worker's incumbent objective per point
   float *C_inc;              // its incumbent centroids (k x d) in the pool
@@ -59,11 +59,12 @@ struct LloydLaunch {
   double tol;
   int *status;
   int64_t max_blocks;          // blocks the caller's scratch allows in total
-  int64_t gpart_cap;           // doubles of gpart reserved per task (2 per block)
+  int64_t task_blocks;         // most blocks one task may use
   // written by the plan
   int64_t grid;
   size_t smem;
   int smem_sums;
+  int xstage;
   // nullable: a prepared round's counter, advanced once the run is done
   uint32_t *round_advance;
 };

@@ -29,6 +29,7 @@ struct LloydArgs {
   double tol;
   int *status;
   int smem_sums;  // 1: per-block sums in shared memory
+  int xstage;     // 1: the block's rows are kept in shared memory for the accumulation
   uint32_t *round_advance;  // nullable: a prepared round's counter (see the kernel's start)
 };
 
@@ -56,17 +57,20 @@ struct LTile {
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// Shared-memory layout of the Lloyd kernel.
+// Shared-memory layout of the Lloyd kernel: centroid block, flags, labels,
+// optionally the block's k x d sums and counts, optionally the block's rows
+// (R x THREADS rows of hpc_cstride(D) floats) for the accumulation.
 struct LloydSmem {
-  size_t cent, dead, lab, sums, cnt, total;
-  __host__ __device__ LloydSmem(int D, int R, int THREADS, int k, int d, bool smem_sums) {
+  size_t cent, dead, lab, sums, cnt, xs, total;
+  __host__ __device__ LloydSmem(int D, int R, int THREADS, int k, int d, bool smem_sums, bool xstage) {
     const int kp = (k + 1) & ~1;
     cent = 0;
     dead = align16(hpc_cent_smem_bytes(D, k));
     lab = dead + align16((size_t)kp);
     sums = lab + align16((size_t)R * THREADS * 4);
     cnt = sums + (smem_sums ? align16((size_t)k * d * 8) : 0);
-    total = cnt + (smem_sums ? align16((size_t)k * 4) : 0);
+    xs = cnt + (smem_sums ? align16((size_t)k * 4) : 0);
+    total = xs + (xstage ? align16((size_t)R * THREADS * hpc_cstride(D) * 4) : 0);
   }
 };
 
@@ -76,7 +80,7 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   __shared__ float s_red[2];
   __shared__ double s_dsum[32];
   __shared__ double s_f;
-  __shared__ unsigned s_umax;
+  __shared__ unsigned s_umax, s_cmax;
   constexpr int LPR = LTile<D>::LPR, RPP = LTile<D>::RPP, TPL = LTile<D>::TPL, NB = LTile<D>::NB;
 
   // The round's last launch moves a prepared round's counter on: every
@@ -88,13 +92,15 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   const int k = tk.k, d = a.d;
   const int64_t s = tk.s;
   const int G = tk.nblocks, lb = (int)blockIdx.x - tk.block0;
-  const LloydSmem L(D, R, THREADS, k, d, a.smem_sums != 0);
+  const LloydSmem L(D, R, THREADS, k, d, a.smem_sums != 0, a.xstage != 0);
   hpc_cent_smem cs;
   hpc_cent_bind(cs, smem_raw, D, k);
   uint8_t *dead = smem_raw + L.dead;
   int *wlab = reinterpret_cast<int *>(smem_raw + L.lab);
   unsigned long long *ssum = reinterpret_cast<unsigned long long *>(smem_raw + L.sums);
   unsigned *scnt = reinterpret_cast<unsigned *>(smem_raw + L.cnt);
+  float *xs = reinterpret_cast<float *>(smem_raw + L.xs);
+  constexpr int XS = hpc_cstride(D);
 
   const int64_t TR = (int64_t)THREADS * R;
   const int64_t ngroups = (s + TR - 1) / TR;
@@ -102,7 +108,7 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
 
   // Phase 0: largest |x| of the sample (sets the fixed-point grid and
   // detects non-finite rows: NaN/inf bit patterns compare above finite).
-  if (threadIdx.x == 0) s_umax = 0u;
+  if (threadIdx.x == 0) s_umax = s_cmax = 0u;
   for (int j = threadIdx.x; j < cs.kp; j += THREADS) dead[j] = (j >= k) || tk.deg[j] != 0;
   // sum slots 0 and 1 start at zero (slot 2 is cleared in iteration 0)
   for (int64_t e = (int64_t)lb * THREADS + threadIdx.x; e < 2ll * k * d; e += (int64_t)G * THREADS)
@@ -123,9 +129,18 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
     if (threadIdx.x == 0) atomicMax(tk.gmaxabs, s_umax);
   }
   constexpr int CS = hpc_cstride(D);
-  for (int e = threadIdx.x; e < cs.kp * CS; e += THREADS) {
-    const int j = e / CS, t = e - j * CS;
-    cs.cm[e] = (j < k && t < d) ? -2.0f * tk.C[(int64_t)j * d + t] : 0.0f;
+  {
+    unsigned m = 0u;  // largest |c| of the live starting centroids
+    for (int e = threadIdx.x; e < cs.kp * CS; e += THREADS) {
+      const int j = e / CS, t = e - j * CS;
+      const float c = (j < k && t < d) ? tk.C[(int64_t)j * d + t] : 0.0f;
+      cs.cm[e] = -2.0f * c;
+      if (!dead[j]) {
+        const unsigned b = __float_as_uint(c) & 0x7fffffffu;
+        m = b > m ? b : m;
+      }
+    }
+    atomicMax(&s_cmax, m);
   }
   __syncthreads();
   hpc_cent_finish<D>(cs, k, s_red, [&](int j) { return dead[j] != 0; });
@@ -144,6 +159,24 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   if (mabs != 0u) Fs = min(126, 62 - hpc_bit_length(s) - hpc_frexp_exp(__uint_as_float(mabs)));
   const float qscale = ldexpf(1.0f, Fs);
   const double qinv = ldexp(1.0, -Fs);
+  // the sample objective as an integer sum on the grid 2^-Fo: with M the
+  // largest |x| or starting |c| (later centroids are means of rows, so M
+  // bounds them too) every distance is at most d (2M)^2, and with a factor
+  // 2 of slack the s rows fit 2^62.  Blocks add their rounded partials and
+  // every block reads back the one word (the same f everywhere, in any
+  // order of arrival).  The sample has no inf/NaN here; the starting
+  // centroids are the caller's, and one of them being non-finite is an error.
+  const unsigned mc = s_cmax;
+  if (mc >= 0x7f800000u) {
+    hpc_status_set(a.status, HPC_ERR_NONFINITE);
+    return;
+  }
+  int Fo = 126;
+  {
+    const double M = (double)__uint_as_float(max(mabs, mc));
+    if (M > 0.0) Fo = min(126, 62 - (int)ceil(log2((double)s * 8.0 * (double)d * M * M)));
+  }
+  const double oscale = ldexp(1.0, Fo), oinv = ldexp(1.0, -Fo);
 
   double f_prev = 0.0;
   for (int it = 0;; ++it) {
@@ -163,12 +196,25 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
       const int64_t base = g * TR;
       int lab[R];
       bool valid[R];
-      fpart += (double)hpc_assign_group<D, R, THREADS, IB>(tk.S, s, d, base, cs, lab, valid,
-                                                               a.status);
+      float x[R][D];
+      fpart += (double)hpc_assign_group_x<D, R, THREADS, IB>(tk.S, s, d, base, cs, x, lab, valid,
+                                                                 a.status);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         wlab[r * THREADS + threadIdx.x] = valid[r] ? lab[r] : -1;
         if (valid[r] && tk.labels) tk.labels[base + (int64_t)r * THREADS + threadIdx.x] = lab[r];
+        if (a.xstage) {  // the row, for this warp's accumulation below
+          float *xr = xs + (size_t)(r * THREADS + threadIdx.x) * XS;
+          if constexpr (D % 4 == 0) {  // XS = D + 4: rows start on 16 bytes
+#pragma unroll
+            for (int t = 0; t < D; t += 4)
+              *reinterpret_cast<float4 *>(xr + t) =
+                  make_float4(x[r][t], x[r][t + 1], x[r][t + 2], x[r][t + 3]);
+          } else {
+#pragma unroll
+            for (int t = 0; t < D; ++t) xr[t] = x[r][t];
+          }
+        }
       }
       __syncwarp();
       // lane (rsub, t0) takes dimensions t0, t0 + LPR, ... of rows
@@ -186,7 +232,8 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
           for (int i = 0; i < NB; ++i) {
             const int rr = rsub + RPP * (b0 + i);
             jj[i] = (b0 + i < 32 / RPP) ? wl[rr] : -1;
-            const float *xr = tk.S + (row0 + rr) * d;
+            const float *xr = a.xstage ? xs + (size_t)(r * THREADS + warp * 32 + rr) * XS
+                                       : tk.S + (row0 + rr) * d;
 #pragma unroll
             for (int u = 0; u < TPL; ++u) {
               const int t = t0 + u * LPR;
@@ -218,14 +265,12 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
         if (scnt[j] != 0u) atomicAdd(&gc[j], scnt[j]);
     }
     const double bsum = hpc_block_sum(fpart, s_dsum);
-    if (threadIdx.x == 0) tk.gpart[(size_t)(it & 1) * G + lb] = bsum;
+    if (threadIdx.x == 0 && bsum != 0.0)
+      atomicAdd(tk.gobj + buf, (unsigned long long)__double2ll_rn(bsum * oscale));
     if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
 
     // Phase B (every block): objective, stop test, new centroids
-    {
-      const double f = hpc_block_sum_array(tk.gpart + (size_t)(it & 1) * G, G, s_dsum);
-      if (threadIdx.x == 0) s_f = f;
-    }
+    if (threadIdx.x == 0) s_f = (double)(long long)__ldcg(tk.gobj + buf) * oinv;
     __syncthreads();
     const double f = s_f;
     const bool done = (it > 0 && (f_prev == 0.0 || (f_prev - f) < a.tol * f_prev)) || it == a.max_iter;
@@ -261,6 +306,7 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
       const int zb = (it + 2) % 3;
       for (int e = threadIdx.x; e < k * d; e += THREADS) tk.gsum[(size_t)zb * k * d + e] = 0ull;
       for (int j = threadIdx.x; j < k; j += THREADS) tk.gcount[(size_t)zb * k + j] = 0u;
+      if (threadIdx.x == 0) tk.gobj[zb] = 0ull;
     }
     __syncthreads();
     hpc_cent_finish<D>(cs, k, s_red, [&](int j) { return dead[j] != 0; });
@@ -333,18 +379,27 @@ template <int D, int IB>
 int lloyd_plan_t(const hpc_launch &L, LloydLaunch &h) {
   using T = LTile<D>;
   auto kern = lloyd_kernel<D, T::R, T::THREADS, IB>;
-  const LloydSmem with(D, T::R, T::THREADS, h.kmax, h.d, true);
-  const LloydSmem without(D, T::R, T::THREADS, h.kmax, h.d, false);
-  const bool smem_sums = with.total <= (size_t)L.smem_optin;
-  const size_t smem = smem_sums ? with.total : without.total;
-  if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  // per-block sums in shared memory when they fit; then the staged rows,
+  // when they fit and cost no resident block
+  const size_t cap = (size_t)L.smem_optin;
+  const bool smem_sums = LloydSmem(D, T::R, T::THREADS, h.kmax, h.d, true, false).total <= cap;
+  const size_t plain = LloydSmem(D, T::R, T::THREADS, h.kmax, h.d, smem_sums, false).total;
+  const size_t staged = LloydSmem(D, T::R, T::THREADS, h.kmax, h.d, smem_sums, true).total;
+  if (plain > cap) return HPC_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(staged <= cap ? staged : plain)) != cudaSuccess)
     return HPC_ERR_CUDA;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T::THREADS, smem) != cudaSuccess ||
+  int per_sm = 0, per_sm_staged = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T::THREADS, plain) != cudaSuccess ||
       per_sm < 1)
     return HPC_ERR_UNSUPPORTED;
-  const int64_t per_task = h.gpart_cap / 2;
+  if (staged <= cap &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_staged, kern, T::THREADS, staged) !=
+          cudaSuccess)
+    return HPC_ERR_CUDA;
+  const bool xstage = per_sm_staged >= per_sm;
+  const size_t smem = xstage ? staged : plain;
+  const int64_t per_task = h.task_blocks;
   int64_t total = (int64_t)per_sm * L.num_sms;
   if (total > h.max_blocks) total = h.max_blocks;
   if (total > per_task * h.W) total = per_task * h.W;
@@ -370,6 +425,7 @@ int lloyd_plan_t(const hpc_launch &L, LloydLaunch &h) {
   h.grid = grid;
   h.smem = smem;
   h.smem_sums = smem_sums ? 1 : 0;
+  h.xstage = xstage ? 1 : 0;
   return HPC_OK;
 }
 
@@ -387,6 +443,7 @@ int lloyd_run_t(const hpc_launch &L, const LloydLaunch &h) {
   a.tol = h.tol;
   a.status = h.status;
   a.smem_sums = h.smem_sums;
+  a.xstage = h.xstage;
   a.round_advance = h.round_advance;
   void *args[] = {&a};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)h.grid),
