@@ -60,6 +60,12 @@ typedef enum hpc_precision {
   HPC_FP8 = 2   /* reserved: FP8 e4m3 tensor-core search with rescoring */
 } hpc_precision;
 
+typedef enum hpc_search {
+  HPC_SEARCH_SIMT = 0,       /* FP32 expanded form on the CUDA cores */
+  HPC_SEARCH_SPLIT_TF32 = 1, /* tensor cores, three TF32 products per K step (d in {16, 32}) */
+  HPC_SEARCH_TF32 = 2        /* tensor cores, one TF32 product (d in {16, 32, 64, 128}) */
+} hpc_search;
+
 typedef enum hpc_strategy {
   HPC_COMPETITIVE = 0, /* Algorithm 3: each worker starts from its own incumbent */
   HPC_COOPERATIVE = 1, /* Algorithm 4: from the best incumbent of its group */
@@ -100,11 +106,38 @@ int hpc_reserve(hpc_ctx *ctx, int64_t bytes);
  * tensor cores instead of the FP32 CUDA-core form: mode 0 never; 1 wherever
  * built (d in {16, 32}: split-TF32 products, three MMAs per K step, row
  * operand written to tensor memory; d in {64, 128}: TF32 products; k <= 128
- * for both); 2 (default) where it was measured faster on GB300: d = 32 with
- * k <= 64 (split TF32) and d in {64, 128} (TF32).  Every form proves its
- * winner against its products' error bound or settles the row exactly, so
- * all return the same labels and objectives within rounding. */
+ * for both); 2 (default) the form set for (d, k) by hpc_set_objective_form
+ * or hpc_autotune_objective, else where it was measured faster on GB300:
+ * d = 32 with k <= 64 (split TF32) and d in {64, 128} (TF32).  Every form
+ * proves its winner against its products' error bound or settles the row
+ * exactly, so all return the same labels and objectives within rounding;
+ * they differ in speed only, and the speed depends on the data (rows near
+ * a tie between two centroids take the exact path). */
 int hpc_set_tensor_cores(hpc_ctx *ctx, int mode);
+
+/* Sets the search form (hpc_search) hpc_objective uses for shape (d, k) in
+ * mode 2; form -1 removes the setting.  Errors: HPC_ERR_ARG for a bad shape
+ * or form, HPC_ERR_UNSUPPORTED if the form is not built for the shape. */
+int hpc_set_objective_form(hpc_ctx *ctx, int32_t d, int32_t k, int32_t form);
+
+/* The search form hpc_objective would run for (n, d, k) now, or
+ * HPC_ERR_ARG for a bad shape. */
+int hpc_objective_form(hpc_ctx *ctx, int64_t n, int32_t d, int32_t k);
+
+/* Tile-schedule choice by measurement (the search form is the one choice
+ * that changes the objective's speed several-fold): times every form built
+ * for (d, k) on the caller's rows X (n x d; a prefix larger than L2, 129 MB,
+ * gives representative times) and centroids C (k x d, flags as in
+ * hpc_objective), reps timed calls each after one warm-up, with CUDA events
+ * on the context's stream; keeps the fastest for (d, k) as
+ * hpc_set_objective_form would.  *form_out (nullable) receives it,
+ * ms_out (host float[3], nullable) the average milliseconds per call of each
+ * form, -1 where not built.  Synchronises the stream.  Errors: as
+ * hpc_objective; a device error recorded during the sweep ends it and is
+ * returned. */
+int hpc_autotune_objective(hpc_ctx *ctx, const float *X, int64_t n, int32_t d, const float *C,
+                           int32_t k, const uint8_t *degenerate, int32_t reps,
+                           int32_t *form_out, float *ms_out);
 
 /* ---- the hot path ------------------------------------------------------ */
 
@@ -236,6 +269,38 @@ int hpc_round_prepare(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
                       int32_t n_candidates, int32_t prec);
 int hpc_round_enqueue(hpc_ctx *ctx);
 
+/* ---- checkpoint ----------------------------------------------------------- */
+
+/* The state an HPClust run resumes from is its workers' incumbents (C_w,
+ * their degenerate flags, fhat_w) plus the next round index and the seed:
+ * every random draw of round r is a function of (seed, worker, r), so a run
+ * resumed from a checkpoint continues exactly as the uninterrupted run
+ * would (Algorithms 3-5 keep no other state between rounds).
+ *
+ * hpc_batch_save writes that state into the HOST buffer host_buf (cap
+ * bytes): a 64-byte header (magic "HPCBATCH", version 1, W, d, strategy,
+ * next_round, n_competitive, seed, counts, FNV-1a checksum of the rest),
+ * then per worker (s_w int64, k_w int32, group_w int32), the centroids of
+ * every worker in worker order (k_w x d float each), their flags (k_w bytes
+ * each) and fhat (W doubles); little-endian, no padding.  *bytes_out
+ * receives the size; host_buf NULL only queries it.  It reads the device
+ * arrays on the context's stream after the work queued before it, and
+ * synchronises the stream.
+ * hpc_batch_load checks a buffer written by hpc_batch_save against `batch`
+ * (same W, d, s_w, k_w, group_w, and n_competitive for HPC_HYBRID) and its
+ * checksum, writes C, degenerate and fhat of `batch`, and returns the
+ * recorded next round, seed and strategy (each out-pointer nullable); it
+ * synchronises the stream.  A prepared round reads the device round counter
+ * it was prepared with: prepare again from the loaded round.
+ * Errors: HPC_ERR_ARG for a malformed batch, a short buffer, a foreign or
+ * corrupted checkpoint or one of another batch; HPC_ERR_CUDA on a copy
+ * failure. */
+int hpc_batch_save(hpc_ctx *ctx, const hpc_batch *batch, int32_t d, uint32_t next_round,
+                   uint64_t seed, int32_t strategy, void *host_buf, int64_t cap,
+                   int64_t *bytes_out);
+int hpc_batch_load(hpc_ctx *ctx, const hpc_batch *batch, int32_t d, const void *host_buf,
+                   int64_t bytes, uint32_t *next_round, uint64_t *seed, int32_t *strategy);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* The full-data objective of hpc_objective (CUDA-core search; same labels,
@@ -260,6 +325,26 @@ int hpc_objective_noalloc(const float *X, int64_t n, int32_t d, const float *C, 
                           int32_t *status_out, void *stream);
 
 /* ---- diagnostics -------------------------------------------------------- */
+
+/* Throughput probes (the paper has no counterpart): the rates against which
+ * the CUDA-core kernels' rooflines are stated.  Kinds: FP32 FMA (fma.rn.f32,
+ * FMA/s), packed FP32 FMA (fma.rn.f32x2, FMA/s counting both lanes), FP64
+ * FMA (FMA/s), FP32 min (ops/s; the top-2 search's compare pipe), L2 read
+ * (bytes/s, a 64 MiB buffer read 40 times) and HBM read (bytes/s, a 4 GiB
+ * buffer read once).  Runs on `device` and `stream` (a cudaStream_t; NULL =
+ * the legacy default stream): one warm-up launch, then three launches timed
+ * with CUDA events; *rate_out receives the rate, *ms_out (nullable) the time
+ * of one launch.  Allocates and frees its buffers; synchronises the stream.
+ * Errors: HPC_ERR_ARG (kind, device), HPC_ERR_NOMEM, HPC_ERR_CUDA. */
+typedef enum hpc_probe {
+  HPC_PROBE_FFMA = 0,
+  HPC_PROBE_FFMA2 = 1,
+  HPC_PROBE_DFMA = 2,
+  HPC_PROBE_FMIN = 3,
+  HPC_PROBE_L2_READ = 4,
+  HPC_PROBE_HBM_READ = 5
+} hpc_probe;
+int hpc_peak_probe(int32_t kind, int32_t device, void *stream, double *rate_out, double *ms_out);
 
 /* Failure-detection self-test (the paper has no counterpart).  Launches a
  * two-block cooperative kernel in which one block never reaches the grid

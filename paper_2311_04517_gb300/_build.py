@@ -14,7 +14,8 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 OUT = PKG / "libhpclust.so"
 OBJ = PKG / "_build"
-SOURCES = ["capi.cu", "lloyd.cu", "kmeanspp.cu", "sample.cu", "tc_objective.cu", "tc_split.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "lloyd.cu", "kmeanspp.cu", "sample.cu", "tc_objective.cu", "tc_split.cu", "noalloc.cu",
+           "peaks.cu"]
 HEADERS = ["common.cuh", "assign.cuh", "kernels.h", "tc.cuh", "round.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

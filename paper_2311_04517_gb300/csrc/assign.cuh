@@ -157,6 +157,17 @@ __device__ __forceinline__ void hpc_top2_fold4(float &d1, float &d2, float k0, f
   d1 = fminf(d1, m);
 }
 
+// Adds v to the unevaluated FP32 pair hi + lo with an error-free TwoSum
+// (Knuth): hi + lo equals the running sum up to the rounding of the lo adds,
+// about m 2^-48 of the sum after m nonnegative terms, with no FP64
+// instruction (FP64 runs at a small fraction of the FP32 rate on GB300).
+__device__ __forceinline__ void hpc_sum2_add(float &hi, float &lo, float v) {
+  const float t = hi + v;
+  const float bv = t - hi;
+  lo += (hi - (t - bv)) + (v - bv);
+  hi = t;
+}
+
 __device__ __forceinline__ float hpc_key(float v, int j) {
   return __int_as_float((__float_as_int(v) & ~31) | j);
 }

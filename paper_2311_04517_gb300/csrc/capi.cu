@@ -30,6 +30,10 @@ struct hpc_ctx {
   size_t ws_bytes;
   int64_t launches;
   int use_tc;  // 0 never, 1 wherever built, 2 (default): where measured faster
+  // objective search forms chosen by hpc_autotune_objective / set by the
+  // caller, per (d, k); consulted in mode 2 before the built-in choice
+  std::vector<std::pair<int64_t, int>> forms;
+  int force_form;  // >= 0 while hpc_autotune_objective times one form
   // pinned staging ring for the per-round descriptor tables: slot i is
   // rewritten only after the copy issued from it last time has run
   void *stage_host[4];
@@ -227,6 +231,36 @@ int run_kmeanspp(hpc_ctx *c, Carver &cv, const float *S, int64_t s, int d, int k
   return HPC_OK;
 }
 
+bool form_supported(int form, int d, int k, int64_t n) {
+  switch (form) {
+    case HPC_SEARCH_SIMT: return true;
+    case HPC_SEARCH_SPLIT_TF32: return hpc_tcs_objective_supported(d, k, n);
+    case HPC_SEARCH_TF32: return hpc_tc_objective_supported(d, k, n);
+    default: return false;
+  }
+}
+
+int64_t form_key(int d, int k) { return (int64_t)d << 32 | (uint32_t)k; }
+
+// The search form hpc_objective runs for (d, k, n) in the context's mode.
+int objective_form(const hpc_ctx *c, int d, int k, int64_t n) {
+  if (c->force_form >= 0) return c->force_form;
+  if (c->use_tc == 0) return HPC_SEARCH_SIMT;
+  if (c->use_tc == 1) {
+    if (hpc_tcs_objective_supported(d, k, n)) return HPC_SEARCH_SPLIT_TF32;
+    if (hpc_tc_objective_supported(d, k, n) && d >= 64) return HPC_SEARCH_TF32;
+    return HPC_SEARCH_SIMT;
+  }
+  for (const auto &f : c->forms)
+    if (f.first == form_key(d, k) && form_supported(f.second, d, k, n)) return f.second;
+  // built-in choice, from measurements on GB300: split TF32 for d = 32 with
+  // k <= 64 (1.5x the CUDA-core search at k = 25); TF32 for d = 64 / 128; at
+  // d = 16, or d = 32 with k > 64, the CUDA-core search is as fast or faster
+  if (d == 32 && k <= 64 && hpc_tcs_objective_supported(d, k, n)) return HPC_SEARCH_SPLIT_TF32;
+  if (d >= 64 && hpc_tc_objective_supported(d, k, n)) return HPC_SEARCH_TF32;
+  return HPC_SEARCH_SIMT;
+}
+
 int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, const float *C, int k,
                   const uint8_t *deg, double *f_out, int32_t *labels) {
   double *part = cv.take<double>((size_t)c->grid_bound);
@@ -247,19 +281,13 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
   h.part = part;
   h.done_count = reinterpret_cast<unsigned *>(c->dwords + 1);
   h.max_blocks = c->grid_bound;
-  // Tensor-core searches (measured on GB300): TF32 with exact resolution
-  // for d = 64 / 128; split TF32 for d = 32 with k <= 64, where it beats the
-  // CUDA-core search (1.5x at k = 25).  At d = 16, or k > 64 with d = 32,
-  // the CUDA-core search is as fast or faster; mode 1 forces the split form.
+  int form = objective_form(c, d, k, n);
+  if (!X || !aligned16(X)) form = HPC_SEARCH_SIMT;
   int rc = HPC_ERR_UNSUPPORTED;
-  if (c->use_tc != 0 && X && aligned16(X)) {
-    const bool split = hpc_tcs_objective_supported(d, k, n) &&
-                       (c->use_tc == 1 || (d == 32 && k <= 64));
-    if (split)
-      rc = hpc_tcs_objective_launch(c->L, h);
-    else if (hpc_tc_objective_supported(d, k, n) && d >= 64)
-      rc = hpc_tc_objective_launch(c->L, h);
-  }
+  if (form == HPC_SEARCH_SPLIT_TF32)
+    rc = hpc_tcs_objective_launch(c->L, h);
+  else if (form == HPC_SEARCH_TF32)
+    rc = hpc_tc_objective_launch(c->L, h);
   if (rc == HPC_ERR_UNSUPPORTED) rc = hpc_objective_launch(c->L, h);
   if (rc == HPC_ERR_CUDA) return cuda_fail(c, cudaGetLastError(), "objective launch");
   if (rc) return fail(c, rc, "objective: unsupported shape");
@@ -368,8 +396,7 @@ static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, i
     const int64_t s = b->s[w];
     const int k = b->k[w];
     need += pad256((size_t)s * d * 4) + pad256((size_t)k * d * 4) + pad256((size_t)k) +
-            pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
-            pad256((size_t)2 * c->grid_bound * 8) + pad256((size_t)s * 4) +
+            pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) + pad256((size_t)s * 4) +
             pad256((size_t)L * s * 4) + pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8);
   }
   *tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) + pad256((size_t)W * sizeof(hpc_round_worker)) +
@@ -556,6 +583,7 @@ int hpc_create(hpc_ctx **ctx, int device, void *stream) {
   c->L.smem_optin -= 2048;  // keep room for the kernels' static shared memory
   c->grid_bound = hpc_grid_bound(c->L);
   c->use_tc = 2;
+  c->force_form = -1;
   if (cudaMalloc(&c->dwords, 256) != cudaSuccess) {
     delete c;
     return HPC_ERR_NOMEM;
@@ -689,6 +717,231 @@ int hpc_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float 
   if (int rc = ensure_ws(c, obj_ws(c))) return rc;
   Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
   return run_objective(c, cv, X, n, d, C, k, degenerate, f_out, labels_out);
+}
+
+int hpc_set_objective_form(hpc_ctx *c, int32_t d, int32_t k, int32_t form) {
+  if (!c || d < 1 || d > 128 || k < 1 || form < -1 || form > HPC_SEARCH_TF32)
+    return fail(c, HPC_ERR_ARG, "bad objective form");
+  if (form >= 0 && !form_supported(form, d, k, 1))
+    return fail(c, HPC_ERR_UNSUPPORTED, "objective form not built for this shape");
+  auto &v = c->forms;
+  v.erase(std::remove_if(v.begin(), v.end(),
+                         [&](const std::pair<int64_t, int> &f) { return f.first == form_key(d, k); }),
+          v.end());
+  if (form >= 0) v.emplace_back(form_key(d, k), form);
+  return HPC_OK;
+}
+
+int hpc_objective_form(hpc_ctx *c, int64_t n, int32_t d, int32_t k) {
+  if (!c || d < 1 || d > 128 || k < 1 || n < 0) return HPC_ERR_ARG;
+  return objective_form(c, d, k, n);
+}
+
+int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float *C,
+                           int32_t k, const uint8_t *degenerate, int32_t reps, int32_t *form_out,
+                           float *ms_out) {
+  if (!c) return HPC_ERR_ARG;
+  if (int rc = check_dims(c, d)) return rc;
+  if (n < 1 || k < 1 || !X || !C || reps < 1 || reps > 1000)
+    return fail(c, HPC_ERR_ARG, "bad sizes");
+  if (!aligned16(X) || !aligned16(C)) return fail(c, HPC_ERR_ARG, "unaligned");
+  cudaSetDevice(c->device);
+  if (int rc = ensure_ws(c, obj_ws(c) + 512)) return rc;
+  if (int st = hpc_sync_status(c)) return st;  // start from a clean status
+  Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
+  double *f = cv.take<double>(1);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_fail(c, cudaGetLastError(), "event create");
+  int best = -1;
+  float best_ms = 0.0f;
+  int rc = HPC_OK;
+  for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_TF32 && rc == HPC_OK; ++form) {
+    if (ms_out) ms_out[form] = -1.0f;
+    if (!form_supported(form, d, k, n)) continue;
+    c->force_form = form;
+    Carver cw = cv;
+    rc = run_objective(c, cw, X, n, d, C, k, degenerate, f, nullptr);  // warm-up
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps && rc == HPC_OK; ++r) {
+      cw = cv;
+      rc = run_objective(c, cw, X, n, d, C, k, degenerate, f, nullptr);
+    }
+    cudaEventRecord(e1, c->stream);
+    c->force_form = -1;
+    if (rc != HPC_OK) break;
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(c, e, "autotune timing");
+      break;
+    }
+    if ((rc = hpc_sync_status(c)) != HPC_OK) break;  // a device error ends the sweep
+    ms /= (float)reps;
+    if (ms_out) ms_out[form] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = form;
+      best_ms = ms;
+    }
+  }
+  c->force_form = -1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HPC_OK) return rc;
+  if (form_out) *form_out = best;
+  return hpc_set_objective_form(c, d, k, best);
+}
+
+// ---- checkpoint of a worker batch ----------------------------------------
+
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t W, d, strategy;
+  uint32_t next_round;
+  int32_t n_competitive;
+  uint64_t seed;
+  int64_t floats, flags;
+  uint64_t checksum;  // FNV-1a (64-bit) of every byte after the header
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header layout");
+
+const char kCkptMagic[8] = {'H', 'P', 'C', 'B', 'A', 'T', 'C', 'H'};
+
+uint64_t fnv1a(const unsigned char *p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+// Per-worker descriptor as stored: s, k, group.
+struct CkptWorker {
+  int64_t s;
+  int32_t k, group;
+};
+
+int ckpt_sizes(const hpc_batch *b, int d, int64_t *floats, int64_t *flags) {
+  *floats = *flags = 0;
+  for (int w = 0; w < b->W; ++w) {
+    if (b->k[w] < 1 || b->s[w] < 1 || b->C_off[w] < 0 || b->K_off[w] < 0) return HPC_ERR_ARG;
+    *floats += (int64_t)b->k[w] * d;
+    *flags += b->k[w];
+  }
+  return HPC_OK;
+}
+
+size_t ckpt_bytes(int W, int64_t floats, int64_t flags) {
+  return sizeof(CkptHeader) + (size_t)W * sizeof(CkptWorker) + (size_t)floats * 4 +
+         (size_t)flags + (size_t)W * 8;
+}
+
+}  // namespace
+
+int hpc_batch_save(hpc_ctx *c, const hpc_batch *b, int32_t d, uint32_t next_round, uint64_t seed,
+                   int32_t strategy, void *host_buf, int64_t cap, int64_t *bytes_out) {
+  if (!c || !b || !bytes_out || b->W < 1 || b->W > HPC_MAX_WORKERS || !b->s || !b->k ||
+      !b->C_off || !b->K_off || !b->C || !b->degenerate || !b->fhat || d < 1 || d > 128)
+    return fail(c, HPC_ERR_ARG, "malformed batch");
+  int64_t floats = 0, flags = 0;
+  if (ckpt_sizes(b, d, &floats, &flags)) return fail(c, HPC_ERR_ARG, "malformed batch entry");
+  const size_t need = ckpt_bytes(b->W, floats, flags);
+  *bytes_out = (int64_t)need;
+  if (!host_buf) return HPC_OK;  // size query
+  if (cap < (int64_t)need) return fail(c, HPC_ERR_ARG, "checkpoint buffer too small");
+  cudaSetDevice(c->device);
+  unsigned char *out = static_cast<unsigned char *>(host_buf);
+  CkptHeader h{};
+  memcpy(h.magic, kCkptMagic, 8);
+  h.version = 1;
+  h.W = b->W;
+  h.d = d;
+  h.strategy = strategy;
+  h.next_round = next_round;
+  h.n_competitive = b->n_competitive;
+  h.seed = seed;
+  h.floats = floats;
+  h.flags = flags;
+  CkptWorker *wk = reinterpret_cast<CkptWorker *>(out + sizeof(CkptHeader));
+  float *cf = reinterpret_cast<float *>(wk + b->W);
+  unsigned char *fl = reinterpret_cast<unsigned char *>(cf + floats);
+  unsigned char *fh = fl + flags;
+  cudaError_t e = cudaSuccess;
+  int64_t of = 0, og = 0;
+  for (int w = 0; w < b->W && e == cudaSuccess; ++w) {
+    const int k = b->k[w];
+    CkptWorker x{b->s[w], k, b->group ? b->group[w] : 0};
+    memcpy(&wk[w], &x, sizeof(x));
+    e = cudaMemcpyAsync(cf + of, b->C + b->C_off[w], (size_t)k * d * 4, cudaMemcpyDeviceToHost,
+                        c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(fl + og, b->degenerate + b->K_off[w], (size_t)k, cudaMemcpyDeviceToHost,
+                          c->stream);
+    of += (int64_t)k * d;
+    og += k;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fh, b->fhat, (size_t)b->W * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint read");
+  h.checksum = fnv1a(out + sizeof(CkptHeader), need - sizeof(CkptHeader));
+  memcpy(out, &h, sizeof(h));
+  return HPC_OK;
+}
+
+int hpc_batch_load(hpc_ctx *c, const hpc_batch *b, int32_t d, const void *host_buf, int64_t bytes,
+                   uint32_t *next_round, uint64_t *seed, int32_t *strategy) {
+  if (!c || !b || !host_buf || b->W < 1 || b->W > HPC_MAX_WORKERS || !b->s || !b->k ||
+      !b->C_off || !b->K_off || !b->C || !b->degenerate || !b->fhat || d < 1 || d > 128)
+    return fail(c, HPC_ERR_ARG, "malformed batch");
+  const unsigned char *in = static_cast<const unsigned char *>(host_buf);
+  if (bytes < (int64_t)sizeof(CkptHeader)) return fail(c, HPC_ERR_ARG, "checkpoint truncated");
+  CkptHeader h;
+  memcpy(&h, in, sizeof(h));
+  if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+    return fail(c, HPC_ERR_ARG, "not a batch checkpoint");
+  int64_t floats = 0, flags = 0;
+  if (ckpt_sizes(b, d, &floats, &flags)) return fail(c, HPC_ERR_ARG, "malformed batch entry");
+  if (h.W != b->W || h.d != d || h.floats != floats || h.flags != flags ||
+      (h.strategy == HPC_HYBRID && h.n_competitive != b->n_competitive))
+    return fail(c, HPC_ERR_ARG, "checkpoint does not match the batch");
+  const size_t need = ckpt_bytes(b->W, floats, flags);
+  if (bytes != (int64_t)need) return fail(c, HPC_ERR_ARG, "checkpoint size mismatch");
+  if (fnv1a(in + sizeof(CkptHeader), need - sizeof(CkptHeader)) != h.checksum)
+    return fail(c, HPC_ERR_ARG, "checkpoint checksum mismatch");
+  const CkptWorker *wk = reinterpret_cast<const CkptWorker *>(in + sizeof(CkptHeader));
+  for (int w = 0; w < b->W; ++w) {
+    CkptWorker x;
+    memcpy(&x, &wk[w], sizeof(x));
+    if (x.s != b->s[w] || x.k != b->k[w] || x.group != (b->group ? b->group[w] : 0))
+      return fail(c, HPC_ERR_ARG, "checkpoint workers differ from the batch");
+  }
+  cudaSetDevice(c->device);
+  const float *cf = reinterpret_cast<const float *>(wk + b->W);
+  const unsigned char *fl = reinterpret_cast<const unsigned char *>(cf + floats);
+  const unsigned char *fh = fl + flags;
+  cudaError_t e = cudaSuccess;
+  int64_t of = 0, og = 0;
+  for (int w = 0; w < b->W && e == cudaSuccess; ++w) {
+    const int k = b->k[w];
+    e = cudaMemcpyAsync(b->C + b->C_off[w], cf + of, (size_t)k * d * 4, cudaMemcpyHostToDevice,
+                        c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->degenerate + b->K_off[w], fl + og, (size_t)k, cudaMemcpyHostToDevice,
+                          c->stream);
+    of += (int64_t)k * d;
+    og += k;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->fhat, fh, (size_t)b->W * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint write");
+  if (next_round) *next_round = h.next_round;
+  if (seed) *seed = h.seed;
+  if (strategy) *strategy = h.strategy;
+  return HPC_OK;
 }
 
 int hpc_selftest_wait_timeout(hpc_ctx *c, int64_t limit_ns) {

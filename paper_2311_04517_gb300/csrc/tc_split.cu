@@ -19,9 +19,10 @@
 // exactly (FP32 direct form); every other centroid is at least
 // ||x||^2 + d2 - E away, which settles nearly all of them; the rest are
 // rescored by the warp (FP32 direct form against every centroid, then FP64
-// in the reference's order, ties to the lowest index).  The objective adds the FP32 direct-form distance to the
-// chosen centroid, from the exact row, in FP64 -- the same value the CUDA-core
-// search adds.
+// in the oracle's order, ties to the lowest index).  The objective adds the
+// FP32 direct-form distance to the chosen centroid, from the exact row: per
+// thread as an FP32 TwoSum pair (about 2^-48 relative, no FP64 instruction
+// per row), then per block in FP64.
 //
 // Data path per 128-row tile (thread t owns tile row t = TMEM lane t):
 //   TMA (2-D tile, 64/128-byte swizzle) -> shared-memory ring of 4 tiles
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
     return true;
   };
 
-  double fsum = 0.0;
+  float fs_hi = 0.0f, fs_lo = 0.0f;  // objective partial of this thread's rows (TwoSum pair)
   if (run) {
     if (r == 0) {
       hpc_prefetch_tensormap(&tmap);
@@ -329,7 +330,12 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
               if (c * 32 + jj >= cs.kp) break;
               const float4 cn = *reinterpret_cast<const float4 *>(cnv + c * 32 + jj);
               const int j = c * 32 + jj;
-              hpc_top2_fold4(d1, d2, hpc_key_b<IB>(cn.x + acc[jj], j),
+              // alternate groups of four go to two independent top-2 chains
+              // (d1, d2) and (e1, e2), merged below; one chain at d = 32
+              // with 32 columns, whose registers are short
+              const bool alt = (jj & 4) && !(D == 32 && NP == 32);
+              float &t1 = alt ? e1 : d1, &t2 = alt ? e2 : d2;
+              hpc_top2_fold4(t1, t2, hpc_key_b<IB>(cn.x + acc[jj], j),
                              hpc_key_b<IB>(cn.y + acc[jj + 1], j + 1),
                              hpc_key_b<IB>(cn.z + acc[jj + 2], j + 2),
                              hpc_key_b<IB>(cn.w + acc[jj + 3], j + 3));
@@ -363,6 +369,8 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
           }
         }
         if constexpr (IB > 0) {
+          d2 = hpc_min3(d2, e2, fmaxf(d1, e1));
+          d1 = fminf(d1, e1);
           j1 = min(__float_as_int(d1) & ((1 << IB) - 1), cs.kp - 1);
           j2 = min(__float_as_int(d2) & ((1 << IB) - 1), cs.kp - 1);
         } else {
@@ -450,7 +458,7 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
           }
         }
         if (valid) {
-          fsum += (double)dd;
+          hpc_sum2_add(fs_hi, fs_lo, dd);
           if (a.labels) a.labels[row] = j1;
         }
       } else {
@@ -492,7 +500,7 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
       }
       if (have) {
         const float dd = hpc_dist_direct_cm<D>(xr, cs.cm + j * CS);
-        fsum += (double)dd;
+        hpc_sum2_add(fs_hi, fs_lo, dd);
         if (a.labels) a.labels[row] = j;
       }
     }
@@ -512,7 +520,7 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
   }
 
   // ---- objective partial, last block reduces in a fixed order ----
-  const double bsum = hpc_block_sum(fsum, s_dsum);
+  const double bsum = hpc_block_sum((double)fs_hi + (double)fs_lo, s_dsum);
   if (tid == 0) {
     a.part[blockIdx.x] = bsum;
     __threadfence();

@@ -26,6 +26,14 @@ HPC_ERR_DEGENERATE_ALL = -6
 HPC_ERR_UNSUPPORTED = -7
 HPC_FP32, HPC_BF16, HPC_FP8 = 0, 1, 2
 HPC_COMPETITIVE, HPC_COOPERATIVE, HPC_HYBRID = 0, 1, 2
+HPC_SEARCH_SIMT, HPC_SEARCH_SPLIT_TF32, HPC_SEARCH_TF32 = 0, 1, 2
+SEARCH_NAMES = {HPC_SEARCH_SIMT: "simt", HPC_SEARCH_SPLIT_TF32: "split_tf32",
+                HPC_SEARCH_TF32: "tf32"}
+(HPC_PROBE_FFMA, HPC_PROBE_FFMA2, HPC_PROBE_DFMA, HPC_PROBE_FMIN, HPC_PROBE_L2_READ,
+ HPC_PROBE_HBM_READ) = range(6)
+PROBES = {HPC_PROBE_FFMA: ("fp32 fma", "FMA/s"), HPC_PROBE_FFMA2: ("fp32x2 fma", "FMA/s"),
+          HPC_PROBE_DFMA: ("fp64 fma", "FMA/s"), HPC_PROBE_FMIN: ("fp32 min", "op/s"),
+          HPC_PROBE_L2_READ: ("L2 read", "B/s"), HPC_PROBE_HBM_READ: ("HBM read", "B/s")}
 
 # The paper's hyperparameters (Section 6.5).
 MAX_ITER = 300
@@ -90,6 +98,17 @@ def load() -> ctypes.CDLL:
         "hpc_round_prepare": ([P, P, i64, i32, ctypes.POINTER(hpc_batch), i32, u64, u32, i32,
                                f64, i32, i32], ctypes.c_int),
         "hpc_round_enqueue": ([P], ctypes.c_int),
+        "hpc_set_objective_form": ([P, i32, i32, i32], ctypes.c_int),
+        "hpc_peak_probe": ([i32, i32, P, ctypes.POINTER(f64), ctypes.POINTER(f64)], ctypes.c_int),
+        "hpc_objective_form": ([P, i64, i32, i32], ctypes.c_int),
+        "hpc_autotune_objective": ([P, P, i64, i32, P, i32, P, i32,
+                                    ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "hpc_batch_save": ([P, ctypes.POINTER(hpc_batch), i32, u32, u64, i32, P, i64,
+                            ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "hpc_batch_load": ([P, ctypes.POINTER(hpc_batch), i32, P, i64,
+                            ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
+                            ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -165,6 +184,31 @@ class Context:
         """Tensor-core search: False/0 never, True/1 wherever built, 2 auto
         (the default; see include/hpclust.h)."""
         self._check(self.lib.hpc_set_tensor_cores(self.h, int(mode)))
+
+    def set_objective_form(self, d: int, k: int, form: int):
+        """Search form of hpc_objective for shape (d, k) in mode 2 (-1 clears)."""
+        self._check(self.lib.hpc_set_objective_form(self.h, int(d), int(k), int(form)))
+
+    def objective_form(self, n: int, d: int, k: int) -> int:
+        rc = int(self.lib.hpc_objective_form(self.h, int(n), int(d), int(k)))
+        if rc < 0:
+            self._check(rc)
+        return rc
+
+    def autotune_objective(self, X, C, degenerate=None, reps: int = 5):
+        """Times every search form built for C's shape on rows X, keeps the
+        fastest for (d, k); returns (form, {form name: ms per call})."""
+        n, d = X.shape
+        k = C.shape[0]
+        _need(X, torch.float32, "X", self.device)
+        _need(C, torch.float32, "C", self.device)
+        _need(degenerate, torch.uint8, "degenerate", self.device)
+        form = ctypes.c_int32(-1)
+        ms = (ctypes.c_float * 3)()
+        self._check(self.lib.hpc_autotune_objective(self.h, _ptr(X), n, d, _ptr(C), k,
+                                                    _ptr(degenerate), int(reps),
+                                                    ctypes.byref(form), ms))
+        return int(form.value), {SEARCH_NAMES[i]: float(ms[i]) for i in range(3) if ms[i] >= 0}
 
     def selftest_wait_timeout(self, limit_ns: int):
         """Launches the bounded-wait self-test (see include/hpclust.h)."""
@@ -266,6 +310,14 @@ class Batch:
                          self.degenerate.data_ptr(), self.fhat.data_ptr(), self.f_new.data_ptr(),
                          self.iters.data_ptr(), self.accepted.data_ptr(), self.n_competitive)
 
+    def save(self, ctx: "Context", path, next_round: int, seed: int, strategy: int):
+        """Writes the checkpoint of hpc_batch_save to the file `path`."""
+        Path(path).write_bytes(hpc_batch_save(ctx, self, next_round, seed, strategy))
+
+    def load(self, ctx: "Context", path):
+        """Restores the state saved by save(); returns (next_round, seed, strategy)."""
+        return hpc_batch_load(ctx, self, Path(path).read_bytes())
+
     def centroids(self, w: int):
         k = int(self.k[w])
         o = int(self.C_off[w])
@@ -297,3 +349,39 @@ def hpc_round_prepare(ctx: Context, X, batch: Batch, strategy: int, seed: int, r
 
 def hpc_round_enqueue(ctx: Context):
     ctx._check(ctx.lib.hpc_round_enqueue(ctx.h))
+
+
+def hpc_batch_save(ctx: Context, batch: Batch, next_round: int, seed: int, strategy: int) -> bytes:
+    """The batch's incumbents, flags and fhat with the next round, seed and
+    strategy, as the bytes of the checkpoint format in include/hpclust.h."""
+    b = batch.struct()
+    need = ctypes.c_int64(0)
+    ctx._check(ctx.lib.hpc_batch_save(ctx.h, ctypes.byref(b), batch.d, next_round, seed, strategy,
+                                      None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(int(need.value))
+    ctx._check(ctx.lib.hpc_batch_save(ctx.h, ctypes.byref(b), batch.d, next_round, seed, strategy,
+                                      buf, need.value, ctypes.byref(need)))
+    return buf.raw
+
+
+def hpc_batch_load(ctx: Context, batch: Batch, blob: bytes):
+    """Writes a checkpoint back into the batch; returns (next_round, seed, strategy)."""
+    b = batch.struct()
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    r, sd, st = ctypes.c_uint32(0), ctypes.c_uint64(0), ctypes.c_int32(0)
+    ctx._check(ctx.lib.hpc_batch_load(ctx.h, ctypes.byref(b), batch.d, buf, len(blob),
+                                      ctypes.byref(r), ctypes.byref(sd), ctypes.byref(st)))
+    return int(r.value), int(sd.value), int(st.value)
+
+
+def hpc_peak_probe(kind: int, device: int = 0, stream: torch.cuda.Stream | None = None):
+    """Measured rate of one throughput probe (include/hpclust.h); returns
+    (rate, ms per launch)."""
+    lib = load()
+    st = stream if stream is not None else torch.cuda.current_stream(torch.device("cuda", device))
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib.hpc_peak_probe(int(kind), int(device), ctypes.c_void_p(st.cuda_stream),
+                            ctypes.byref(rate), ctypes.byref(ms))
+    if rc != HPC_OK:
+        raise HPCError(rc, "hpc_peak_probe failed")
+    return float(rate.value), float(ms.value)
