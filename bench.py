@@ -64,6 +64,12 @@ def parse_args():
     p.add_argument("--rows", type=int, default=None,
                    help="a smaller case of the workload: this many data rows instead of n "
                         "(for profiler captures; not a bench configuration)")
+    p.add_argument("--no-autotune", dest="autotune", action="store_false",
+                   help="keep the built-in objective search forms instead of timing every "
+                        "form on the workload before the timed steps (hpc_autotune_objective)")
+    p.add_argument("--tto-rounds", type=int, default=None,
+                   help="rounds of the time-to-objective comparison with the plain FP32 path "
+                        "(default: the workload's rounds, at most 10; 0 skips it)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
     return p.parse_args()
@@ -84,13 +90,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, workload: str):
+def profiled_traffic(kernel: str, workload: str, kernel_name: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+    on the current kernel sources and of the kernel that ran."""
     f = ROOT / "profiles" / f"{kernel}_{workload}.md"
     if not f.exists():
         return None
     txt = f.read_text()
+    if kernel_name not in txt.splitlines()[0]:
+        return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     hs = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
     if not m or not hs or hs.group(1) != kernel_source_hash():
@@ -328,6 +336,69 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev):
+    """Wall time (CUDA events) for R rounds plus the full-data objective of
+    each group's best incumbent after every round, on fresh batches: the
+    plain FP32 path (CUDA-core search everywhere, rounds issued one by one)
+    against the path the bench times (tensor-core search where it was
+    measured faster, rounds replayed from a CUDA graph).  Reports the time at
+    which each reached the plain path's final objectives (per group, within
+    1e-6 relative)."""
+    out = {}
+    logs = {}
+    mode0 = args.tensor_cores
+    for arm in ("fp32", "default"):
+        ctx.set_tensor_cores(0 if arm == "fp32" else mode0)
+        b = H.Batch(wl.d, ws.s, ws.k, ws.group, device=dev, n_competitive=n_comp(args))
+        fh = torch.empty(wl.W, dtype=torch.float64).pin_memory()
+        f_log = torch.zeros((R, len(groups)), dtype=torch.float64, device=dev)
+        graph = None
+        if arm == "default" and args.graph:
+            H.hpc_round_prepare(ctx, X, b, strategy, seed, 0)
+            side = torch.cuda.Stream(dev)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                ctx.set_stream(side)
+                H.hpc_round_enqueue(ctx)
+            ctx.set_stream(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(R + 1)]
+        ev[0].record()
+        for r in range(R):
+            if graph is not None:
+                graph.replay()
+            else:
+                H.hpc_round(ctx, X, b, strategy, seed, r)
+            if wl.W == 1:
+                bs = [0]
+            else:
+                fh.copy_(b.fhat)
+                bs = [int(g[np.argmin(fh.numpy()[g])]) for g in groups]
+            for gi, w in enumerate(bs):
+                C, deg = b.centroids(w)
+                H.hpc_objective(ctx, X, C, deg, f_out=f_log[r, gi:gi + 1])
+            ev[r + 1].record()
+        torch.cuda.synchronize()
+        ctx.check_status()
+        logs[arm] = (f_log.cpu().numpy(), [ev[0].elapsed_time(e) for e in ev[1:]])
+        del graph
+    ctx.set_tensor_cores(mode0)
+    target = logs["fp32"][0][-1]
+    for arm, (f, t) in logs.items():
+        hit = [r for r in range(R) if np.all(f[r] <= target * (1 + 1e-6))]
+        out[f"{arm}_ms"] = t[hit[0]] if hit else None
+        out[f"{arm}_rounds"] = hit[0] + 1 if hit else None
+    out["speedup"] = (out["fp32_ms"] / out["default_ms"]) if out["default_ms"] else None
+    out["final_objectives_rel_diff"] = float(np.max(np.abs(logs["default"][0][-1] - target)
+                                                    / target))
+    out.update({"rounds": R, "target": "the plain FP32 path's full-data objective of each "
+                "group's best incumbent after the last round, within 1e-6 relative",
+                "fp32_path": "CUDA-core search, rounds issued one by one",
+                "default_path": "the bench's path: objective search form per (d, k) as tuned, "
+                                "rounds replayed from a CUDA graph"})
+    return out
+
+
 def run_mine(args):
     from paper_2311_04517_gb300 import hpclust as H
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -403,6 +474,18 @@ def run_mine(args):
     for r in range(Wm):
         step(r)
     ctx.check_status()
+    # the objective's search form per (d, k), measured on this data with the
+    # incumbents the warm-up rounds produced (outside the timed steps)
+    forms = {}
+    if args.autotune and args.tensor_cores == 2:
+        rows = min(wl.n, max(1, 512_000_000 // (4 * wl.d)))   # a prefix larger than L2
+        for b in bests():
+            kb = int(ws.k[b])
+            if kb in forms:
+                continue
+            C, deg = batch.centroids(b)
+            form, tms = ctx.autotune_objective(X[:rows], C, deg, reps=3)
+            forms[kb] = {"form": H.SEARCH_NAMES[form], "ms_per_call": tms, "rows": rows}
     torch.cuda.synchronize()
     if dist_ok:
         dist.barrier()
@@ -494,11 +577,13 @@ def run_mine(args):
     bytes_obj = float(wl.n) * wl.d * 4
     achieved = bytes_obj / (obj_avg_ms / 1e3) / 1e9
     kb0 = int(ws.k[best_log[0][0]]) if best_log else int(ws.k[0])
-    split = wl.d in (16, 32) and (args.tensor_cores == 1 or
-                                  (args.tensor_cores == 2 and wl.d == 32 and kb0 <= 64))
-    tf32 = args.tensor_cores != 0 and wl.d in (64, 128) and kb0 <= 128
-    obj_kernel = "tcs_objective_kernel" if split else "tc_objective_kernel" if tf32 \
-        else "objective_kernel"
+    obj_kernel = {H.HPC_SEARCH_SIMT: "objective_kernel",
+                  H.HPC_SEARCH_SPLIT_TF32: "tcs_objective_kernel",
+                  H.HPC_SEARCH_TF32: "tc_objective_kernel"}[ctx.objective_form(wl.n, wl.d, kb0)]
+    tto = None
+    R = args.tto_rounds if args.tto_rounds is not None else min(wl.rounds, 10)
+    if R > 0 and world == 1:
+        tto = time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -509,7 +594,7 @@ def run_mine(args):
                          "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "peak_source": f"{src} hbm_gbs", "unit": "GB/s",
                          "frac": achieved / hbm,
-                         "traffic": profiled_traffic("objective", wl.name),
+                         "traffic": profiled_traffic("objective", wl.name, obj_kernel),
                          "algorithmic_bytes_per_launch": bytes_obj,
                          "avg_launch_ms": obj_avg_ms},
             "e2e": {"value": e_value, "unit": UNIT,
@@ -519,6 +604,10 @@ def run_mine(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(t0, t1),
             "lloyd_iters_mean": float(iters.mean())}
+    if forms:
+        line["objective_forms"] = {str(k): v for k, v in forms.items()}
+    if tto is not None:
+        line["time_to_objective"] = tto
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the host copy for the oracle: whole X up to 2e8 floats, else a row prefix
         n_host = wl.n if wl.n * wl.d <= 200_000_000 else max(1, 200_000_000 // wl.d)
