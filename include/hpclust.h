@@ -63,7 +63,8 @@ typedef enum hpc_precision {
 typedef enum hpc_search {
   HPC_SEARCH_SIMT = 0,       /* FP32 expanded form on the CUDA cores */
   HPC_SEARCH_SPLIT_TF32 = 1, /* tensor cores, three TF32 products per K step (d in {16, 32}) */
-  HPC_SEARCH_TF32 = 2        /* tensor cores, one TF32 product (d in {16, 32, 64, 128}) */
+  HPC_SEARCH_TF32 = 2        /* tensor cores, one TF32 product (d in {16, 32, 64}: k <= 512;
+                                d = 128: k <= 256) */
 } hpc_search;
 
 typedef enum hpc_strategy {
@@ -108,7 +109,10 @@ int hpc_reserve(hpc_ctx *ctx, int64_t bytes);
  * operand written to tensor memory; d in {64, 128}: TF32 products; k <= 128
  * for both); 2 (default) the form set for (d, k) by hpc_set_objective_form
  * or hpc_autotune_objective, else where it was measured faster on GB300:
- * d = 32 with k <= 64 (split TF32) and d in {64, 128} (TF32).  Every form
+ * d = 32 with k <= 64 (split TF32) and d in {64, 128} with k <= 128 (TF32).
+ * For 128 < k <= 512 the TF32 form splits each row tile's 256 or 512
+ * accumulator columns over four warpgroups; it is chosen only when set or
+ * measured faster (it wins where few rows lie near a tie).  Every form
  * proves its winner against its products' error bound or settles the row
  * exactly, so all return the same labels and objectives within rounding;
  * they differ in speed only, and the speed depends on the data (rows near

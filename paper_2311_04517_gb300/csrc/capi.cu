@@ -133,9 +133,12 @@ size_t kpp_ws(const hpc_ctx *c, int64_t s, int L) {
 // near-tie rows the tensor-core search settles after its main loop, per block
 #define HPC_OBJ_QUEUE_CAP 4096
 
+// the wide tensor-core search's exact centroid block, at its largest shape
+#define HPC_OBJ_CENT_BYTES ((size_t)320 * 1024)
+
 size_t obj_ws(const hpc_ctx *c) {
   return pad256((size_t)c->grid_bound * 8) + pad256((size_t)c->L.num_sms * HPC_OBJ_QUEUE_CAP * 8) +
-         512;
+         HPC_OBJ_CENT_BYTES + 768;
 }
 
 // Lloyd scratch of one task (header zeroed by the caller).
@@ -254,10 +257,14 @@ int objective_form(const hpc_ctx *c, int d, int k, int64_t n) {
   for (const auto &f : c->forms)
     if (f.first == form_key(d, k) && form_supported(f.second, d, k, n)) return f.second;
   // built-in choice, from measurements on GB300: split TF32 for d = 32 with
-  // k <= 64 (1.5x the CUDA-core search at k = 25); TF32 for d = 64 / 128; at
-  // d = 16, or d = 32 with k > 64, the CUDA-core search is as fast or faster
+  // k <= 64 (1.5x the CUDA-core search at k = 25); TF32 for d = 64 / 128 with
+  // k <= 128; at d = 16, or d = 32 with k > 64, the CUDA-core search is as
+  // fast or faster.  For k > 128 the TF32 search wins only where few rows
+  // sit near a tie (5x at k = 500 with one centroid per mixture component,
+  // 2x slower with several per component, as K-means leaves them on skewed
+  // mixtures): the CUDA cores unless a measurement says otherwise
   if (d == 32 && k <= 64 && hpc_tcs_objective_supported(d, k, n)) return HPC_SEARCH_SPLIT_TF32;
-  if (d >= 64 && hpc_tc_objective_supported(d, k, n)) return HPC_SEARCH_TF32;
+  if (d >= 64 && k <= 128 && hpc_tc_objective_supported(d, k, n)) return HPC_SEARCH_TF32;
   return HPC_SEARCH_SIMT;
 }
 
@@ -265,7 +272,10 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
                   const uint8_t *deg, double *f_out, int32_t *labels) {
   double *part = cv.take<double>((size_t)c->grid_bound);
   int64_t *queue = cv.take<int64_t>((size_t)c->L.num_sms * HPC_OBJ_QUEUE_CAP);
+  unsigned char *cent = cv.take<unsigned char>(HPC_OBJ_CENT_BYTES);
   ObjArgsHost h{};
+  h.cent_scratch = cent;
+  h.cent_scratch_bytes = (int64_t)HPC_OBJ_CENT_BYTES;
   h.queue = queue;
   h.queue_cap = HPC_OBJ_QUEUE_CAP;
   h.queue_ctas = c->L.num_sms;

@@ -122,6 +122,10 @@ struct ObjArgsHost {
   int64_t *queue;
   int64_t queue_cap;
   int64_t queue_ctas;
+  // optional: global scratch for the exact centroid block of the wide
+  // (k > 128) tensor-core search, hpc_tc_wide_scratch_bytes(d, k) bytes
+  unsigned char *cent_scratch;
+  int64_t cent_scratch_bytes;
 };
 
 // ---- sampling (one task = one worker's sample) ----
@@ -169,6 +173,11 @@ int hpc_lloyd_run(const hpc_launch &L, const LloydLaunch &h);
 int hpc_kmeanspp_plan(const hpc_launch &L, KppLaunch &h);
 int hpc_kmeanspp_run(const hpc_launch &L, const KppLaunch &h);
 int hpc_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
+// TF32 tensor-core search for 128 < k <= 512 (d in {16, 32, 64}) and
+// 128 < k <= 256 (d = 128); hpc_tc_objective_launch dispatches to it.
+bool hpc_tc_wide_supported(int d, int k, int64_t n);
+int hpc_tc_wide_launch(const hpc_launch &L, const ObjArgsHost &h);
+size_t hpc_tc_wide_scratch_bytes(int d, int k);
 bool hpc_tc_objective_supported(int d, int k, int64_t n);
 int hpc_tc_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
 // split-TF32 tensor-core search for rows of 16 or 32 floats

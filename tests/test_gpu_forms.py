@@ -37,7 +37,7 @@ def built(d, k):
     ok = [H.HPC_SEARCH_SIMT]
     if d in (16, 32) and k <= 128:
         ok.append(H.HPC_SEARCH_SPLIT_TF32)
-    if d in (16, 32, 64, 128) and k <= 128:
+    if (d in (16, 32, 64) and k <= 512) or (d == 128 and k <= 256):
         ok.append(H.HPC_SEARCH_TF32)
     return ok
 
@@ -51,7 +51,11 @@ def objective(ctx, X, C, deg=None):
 
 @pytest.mark.parametrize("n,d,k", [(100037, 16, 25), (40001, 16, 33), (20000, 16, 128),
                                    (77777, 32, 25), (30000, 32, 100), (129, 32, 7),
-                                   (20000, 64, 30), (8191, 128, 20)])
+                                   (20000, 64, 30), (8191, 128, 20),
+                                   # wide TF32 search (k > 128): one or two TMEM banks per tile
+                                   (30011, 16, 129), (20000, 16, 512), (25000, 32, 300),
+                                   (40009, 64, 500), (12345, 64, 256), (300, 64, 200),
+                                   (10007, 128, 256), (4097, 128, 131)])
 def test_every_form_matches_oracle(ctx, n, d, k):
     # centroids near random rows: several per cluster, so that many rows sit
     # inside the TF32 error window and take the exact stages
@@ -92,14 +96,19 @@ def test_form_table_and_modes(ctx):
         ctx.set_objective_form(8, 25, H.HPC_SEARCH_SPLIT_TF32)
     assert e.value.code == H.HPC_ERR_UNSUPPORTED
     with pytest.raises(H.HPCError) as e:
-        ctx.set_objective_form(64, 200, H.HPC_SEARCH_TF32)
+        ctx.set_objective_form(64, 513, H.HPC_SEARCH_TF32)
     assert e.value.code == H.HPC_ERR_UNSUPPORTED
+    with pytest.raises(H.HPCError) as e:
+        ctx.set_objective_form(128, 257, H.HPC_SEARCH_TF32)
+    assert e.value.code == H.HPC_ERR_UNSUPPORTED
+    ctx.set_objective_form(64, 200, H.HPC_SEARCH_TF32)    # the wide search
+    assert ctx.objective_form(n, 64, 200) == H.HPC_SEARCH_TF32
     with pytest.raises(H.HPCError) as e:
         ctx.set_objective_form(16, 25, 7)
     assert e.value.code == H.HPC_ERR_ARG
 
 
-@pytest.mark.parametrize("d,k", [(16, 25), (32, 50), (64, 100), (8, 10)])
+@pytest.mark.parametrize("d,k", [(16, 25), (32, 50), (64, 100), (8, 10), (64, 300)])
 def test_autotune_picks_a_built_form_and_keeps_results(ctx, d, k):
     n = 400_000
     Xh = mixture(n, d, k, seed=d + k, sd=1.0)
@@ -132,3 +141,32 @@ def test_autotune_argument_errors(ctx):
         ctx.autotune_objective(X, C, reps=0)
     with pytest.raises(H.HPCError):
         ctx.autotune_objective(X[:0], C)
+
+
+def test_wide_search_edge_cases(ctx):
+    # k > 128 on the wide TF32 search: no live centroid, a non-finite row,
+    # degenerate slots in both TMEM banks, a ragged last tile, determinism
+    d, k = 64, 300
+    ctx.set_objective_form(d, k, H.HPC_SEARCH_TF32)
+    C = torch.from_numpy(mixture(k, d, 20, 5)).cuda()
+    X = torch.ones((300, d), device="cuda")
+    H.hpc_objective(ctx, X, C, torch.ones(k, dtype=torch.uint8, device="cuda"))
+    assert ctx.sync_status() == H.HPC_ERR_DEGENERATE_ALL
+    Xn = mixture(1000, d, 20, 6)
+    Xn[777, 5] = np.inf
+    H.hpc_objective(ctx, torch.from_numpy(Xn).cuda(), C)
+    assert ctx.sync_status() == H.HPC_ERR_NONFINITE
+    Xh = mixture(50_001, d, 40, 7, sd=2.0)
+    Ch = (Xh[np.random.default_rng(7).choice(50_001, k, replace=False)]).astype(np.float32)
+    deg = np.zeros(k, np.uint8)
+    deg[[0, 100, 255, 256, 299]] = 1
+    lab_o, d1, d2, f_o = orc.assign(Xh, Ch, deg)
+    X, C, D = (torch.from_numpy(a).cuda() for a in (Xh, Ch, deg))
+    fa, la = objective(ctx, X, C, D)
+    fb, lb = objective(ctx, X, C, D)
+    assert fa == fb
+    np.testing.assert_array_equal(la, lb)
+    assert fa == pytest.approx(f_o, rel=RTOL)
+    away = (d2 - d1) > 1e-6 * d1
+    np.testing.assert_array_equal(la[away], lab_o[away])
+    assert not np.isin(la, [0, 100, 255, 256, 299]).any()

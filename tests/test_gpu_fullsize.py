@@ -1,7 +1,8 @@
 """Parity at the full sizes of the measured workloads, through the same calls
 bench.py times: the plain FP32 workload (10^7 x 16), the precision workload
 (2 x 10^7 x 128, k = 100), the batching workload (5 x 10^7 x 32, 64 workers)
-and the large workload (2 x 10^8 x 64, k = 500, 51 GB on the device).
+and the large workload (2 x 10^8 x 64, k = 500, 51 GB on the device; CUDA-core
+and wide TF32 searches).
 
 At these sizes the oracle checks what it can compute one by one -- sampled
 rows of the full-data objective, sampled workers of a full-size round -- and
@@ -109,10 +110,17 @@ def test_batching_workload_objective(ctx, k):
     torch.cuda.empty_cache()
 
 
-def test_large_workload_objective(ctx):
+@pytest.mark.parametrize("form", [H.HPC_SEARCH_SIMT, H.HPC_SEARCH_TF32])
+def test_large_workload_objective(ctx, form):
+    # k = 500: the CUDA-core search (built-in choice) and the wide TF32 search
+    # (four warpgroups over a tile's 512 accumulator columns)
     wl = synth.WORKLOADS["large"]
     X = synth.make_data(wl, "cuda")               # 2e8 x 64 float32, 51 GB
-    objective_case(ctx, wl, X, 500, 5_000, 4)
+    ctx.set_objective_form(wl.d, 500, form)
+    try:
+        objective_case(ctx, wl, X, 500, 5_000, 4)
+    finally:
+        ctx.set_objective_form(wl.d, 500, -1)
     del X
     torch.cuda.empty_cache()
 
