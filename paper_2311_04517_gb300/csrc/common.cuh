@@ -233,6 +233,58 @@ __device__ __forceinline__ unsigned long long hpc_warp_sum_u64(unsigned long lon
   return v;
 }
 
+// Block sum of one unsigned 64-bit integer per thread (two's complement, so
+// signed values add too; blockDim.x a multiple of 32, at most 1024).  Result
+// valid in thread 0.  Integer: exact and independent of the order.
+__device__ __forceinline__ unsigned long long hpc_block_sum_u64(unsigned long long v,
+                                                                unsigned long long *scratch32) {
+  v = hpc_warp_sum_u64(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch32[wid] = v;
+  __syncthreads();
+  unsigned long long r = 0ull;
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int w = 0; w < nw; ++w) r += scratch32[w];
+  }
+  return r;
+}
+
+// 2^e as a float or a double, built from its bits (no arithmetic):
+// -126 <= e <= 127 for the float, -1022 <= e <= 1023 for the double.
+__device__ __forceinline__ float hpc_pow2f(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ double hpc_pow2d(int e) {
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
+// q 2^-F / cnt rounded to float, for |q| < 2^62, 1 <= cnt < 2^32 and
+// 0 <= F <= 126, without an FP64 instruction (FP64 runs at 1/64 of the FP32
+// rate on GB300): q and cnt as unevaluated sums of two floats, one FP32
+// division, and a correction from the first quotient's residual (exact by
+// FMA).  The result is within one unit in the last place of the exact
+// quotient (the FP64 path it replaces rounded twice as well).
+__device__ __forceinline__ float hpc_mean_f32(long long q, unsigned cnt, int F) {
+  if (q == 0) return 0.0f;
+  const bool neg = q < 0;
+  const unsigned long long a = neg ? (unsigned long long)(-q) : (unsigned long long)q;
+  const int L = 64 - __clzll((long long)a);
+  const int sh = L > 24 ? L - 24 : 0;
+  const unsigned long long top = a >> sh;  // < 2^24: exact in a float
+  const unsigned long long rem = a - (top << sh);
+  const float qh = (float)(unsigned)top * hpc_pow2f(sh);
+  const int Lr = rem ? 64 - __clzll((long long)rem) : 0;
+  const int shr = Lr > 31 ? Lr - 31 : 0;
+  const float ql = (float)(unsigned)(rem >> shr) * hpc_pow2f(shr);
+  const float ch = (float)cnt;
+  const float cl = cnt < (1u << 24) ? 0.0f : (float)(int)((long long)cnt - (long long)ch);
+  const float m0 = __fdiv_rn(qh, ch);
+  const float r = (fmaf(-m0, ch, qh) + ql) - m0 * cl;
+  const float m = m0 + __fdiv_rn(r, ch);
+  const float v = m * hpc_pow2f(-F);
+  return neg ? -v : v;
+}
+
 // Fixed-order block sum of one double per thread (blockDim.x multiple of 32,
 // at most 1024).  Result valid in thread 0.
 __device__ __forceinline__ double hpc_block_sum(double v, double *scratch32) {

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   __shared__ float s_red[2];
   __shared__ double s_dsum[32];
   __shared__ double s_f;
+  __shared__ int s_done;
   __shared__ unsigned s_umax, s_cmax;
   constexpr int LPR = LTile<D>::LPR, RPP = LTile<D>::RPP, TPL = LTile<D>::TPL, NB = LTile<D>::NB;
 
@@ -157,8 +158,7 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   // grid 2^Fs with |q| < 2^(62 - bitlen(s)) so that any sum of s values fits
   int Fs = 126;
   if (mabs != 0u) Fs = min(126, 62 - hpc_bit_length(s) - hpc_frexp_exp(__uint_as_float(mabs)));
-  const float qscale = ldexpf(1.0f, Fs);
-  const double qinv = ldexp(1.0, -Fs);
+  const float qscale = hpc_pow2f(Fs);
   // the sample objective as an integer sum on the grid 2^-Fo: with M the
   // largest |x| or starting |c| (later centroids are means of rows, so M
   // bounds them too) every distance is at most d (2M)^2, and with a factor
@@ -171,12 +171,16 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
     hpc_status_set(a.status, HPC_ERR_NONFINITE);
     return;
   }
+  // (in integers: s 8 d M^2 < 2^(bitlen(s) + 3 + bitlen(d) + 2 e(M)))
   int Fo = 126;
   {
-    const double M = (double)__uint_as_float(max(mabs, mc));
-    if (M > 0.0) Fo = min(126, 62 - (int)ceil(log2((double)s * 8.0 * (double)d * M * M)));
+    const unsigned mm = max(mabs, mc);
+    if (mm != 0u)
+      Fo = min(126, 59 - hpc_bit_length(s) - hpc_bit_length(d) - 2 * hpc_frexp_exp(__uint_as_float(mm)));
+    Fo = max(Fo, -126);
   }
-  const double oscale = ldexp(1.0, Fo), oinv = ldexp(1.0, -Fo);
+  const float oscale = hpc_pow2f(Fo);
+  const double oinv = hpc_pow2d(-Fo);
 
   double f_prev = 0.0;
   for (int it = 0;; ++it) {
@@ -191,14 +195,15 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
     }
     __syncthreads();
     // Phase A: assignment, then accumulation with lanes over dimensions
-    double fpart = 0.0;
+    float fp_hi = 0.0f, fp_lo = 0.0f;  // this thread's rows' distances (TwoSum pair)
     for (int64_t g = lb; g < ngroups; g += G) {
       const int64_t base = g * TR;
       int lab[R];
       bool valid[R];
       float x[R][D];
-      fpart += (double)hpc_assign_group_x<D, R, THREADS, IB>(tk.S, s, d, base, cs, x, lab, valid,
-                                                                 a.status);
+      hpc_sum2_add(fp_hi, fp_lo,
+                   hpc_assign_group_x<D, R, THREADS, IB>(tk.S, s, d, base, cs, x, lab, valid,
+                                                         a.status));
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         wlab[r * THREADS + threadIdx.x] = valid[r] ? lab[r] : -1;
@@ -264,16 +269,23 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
       for (int j = threadIdx.x; j < k; j += THREADS)
         if (scnt[j] != 0u) atomicAdd(&gc[j], scnt[j]);
     }
-    const double bsum = hpc_block_sum(fpart, s_dsum);
-    if (threadIdx.x == 0 && bsum != 0.0)
-      atomicAdd(tk.gobj + buf, (unsigned long long)__double2ll_rn(bsum * oscale));
+    // the thread's partial on the grid 2^-Fo, summed over the block in
+    // integers: no FP64 instruction per thread
+    const unsigned long long bq = hpc_block_sum_u64(
+        (unsigned long long)(__float2ll_rn(fp_hi * oscale) + __float2ll_rn(fp_lo * oscale)),
+        reinterpret_cast<unsigned long long *>(s_dsum));
+    if (threadIdx.x == 0 && bq != 0ull) atomicAdd(tk.gobj + buf, bq);
     if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) return;
 
-    // Phase B (every block): objective, stop test, new centroids
-    if (threadIdx.x == 0) s_f = (double)(long long)__ldcg(tk.gobj + buf) * oinv;
+    // Phase B (every block): objective, stop test (thread 0), new centroids
+    if (threadIdx.x == 0) {
+      const double fo = (double)(long long)__ldcg(tk.gobj + buf) * oinv;
+      s_f = fo;
+      s_done = (it > 0 && (f_prev == 0.0 || (f_prev - fo) < a.tol * f_prev)) || it == a.max_iter;
+    }
     __syncthreads();
     const double f = s_f;
-    const bool done = (it > 0 && (f_prev == 0.0 || (f_prev - f) < a.tol * f_prev)) || it == a.max_iter;
+    const bool done = s_done != 0;
     if (done) {
       if (lb == 0) {
         if (threadIdx.x == 0) {
@@ -298,7 +310,7 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
         continue;
       }
       const long long q = (long long)__ldcg(gs + (size_t)j * d + t);
-      const float v = (float)(((double)q * qinv) / (double)cnt);
+      const float v = hpc_mean_f32(q, cnt, Fs);
       cs.cm[e] = -2.0f * v;
       if (lb == 0) tk.C[(int64_t)j * d + t] = v;
     }
@@ -314,8 +326,9 @@ __global__ void __launch_bounds__(THREADS, LTile<D>::MINB) lloyd_kernel(LloydArg
   }
 }
 
-// Full-data objective: grid-stride over row groups, FP64 per-block partial,
-// the last block to finish sums the partials in a fixed order.
+// Full-data objective: grid-stride over row groups, per-thread FP32 TwoSum
+// partial, FP64 per-block partial, the last block to finish sums the
+// partials in a fixed order.
 struct ObjArgs {
   const float *X;
   int64_t n;
@@ -340,7 +353,7 @@ __global__ void __launch_bounds__(THREADS, D <= 16 ? 2 : 1) objective_kernel(Obj
   hpc_load_centroids<D>(cs, a.C, a.deg, a.k, a.d, s_red);
   const int64_t TR = (int64_t)THREADS * R;
   const int64_t ngroups = (a.n + TR - 1) / TR;
-  double fpart = 0.0;
+  float fp_hi = 0.0f, fp_lo = 0.0f;  // this thread's rows' distances (TwoSum pair)
   if (cs.live == 0) {
     if (a.n > 0) hpc_status_set(a.status, HPC_ERR_DEGENERATE_ALL);
   } else {
@@ -348,8 +361,9 @@ __global__ void __launch_bounds__(THREADS, D <= 16 ? 2 : 1) objective_kernel(Obj
       const int64_t base = g * TR;
       int lab[R];
       bool valid[R];
-      fpart += (double)hpc_assign_group<D, R, THREADS, IB>(a.X, a.n, a.d, base, cs, lab, valid,
-                                                               a.status);
+      hpc_sum2_add(fp_hi, fp_lo,
+                   hpc_assign_group<D, R, THREADS, IB>(a.X, a.n, a.d, base, cs, lab, valid,
+                                                       a.status));
       if (a.labels) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -357,7 +371,7 @@ __global__ void __launch_bounds__(THREADS, D <= 16 ? 2 : 1) objective_kernel(Obj
       }
     }
   }
-  const double bsum = hpc_block_sum(fpart, s_dsum);
+  const double bsum = hpc_block_sum((double)fp_hi + (double)fp_lo, s_dsum);
   if (threadIdx.x == 0) {
     a.part[blockIdx.x] = bsum;
     __threadfence();
