@@ -91,13 +91,17 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(kernel: str, workload: str, kernel_name: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources and of the kernel that ran."""
-    f = ROOT / "profiles" / f"{kernel}_{workload}.md"
-    if not f.exists():
-        return None
-    txt = f.read_text()
-    if kernel_name not in txt.splitlines()[0]:
+    """DRAM bytes per launch from the committed ncu summary of this workload
+    whose title names the kernel that ran, if it was taken on the current
+    kernel sources."""
+    txt = None
+    for f in sorted((ROOT / "profiles").glob(f"{kernel}_{workload}*.md")):
+        t = f.read_text()
+        m0 = re.match(r"#\s+(\w+)", t)
+        if m0 and m0.group(1) == kernel_name:
+            txt = t
+            break
+    if txt is None:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     hs = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
