@@ -109,7 +109,7 @@ int hpc_reserve(hpc_ctx *ctx, int64_t bytes);
  * operand written to tensor memory; d in {64, 128}: TF32 products; k <= 128
  * for both); 2 (default) the form set for (d, k) by hpc_set_objective_form
  * or hpc_autotune_objective, else where it was measured faster on GB300:
- * d = 32 with k <= 64 (split TF32) and d in {64, 128} with k <= 128 (TF32).
+ * d = 32 with k <= 128 (split TF32) and d in {64, 128} with k <= 128 (TF32).
  * For 128 < k <= 512 the TF32 form splits each row tile's 256 or 512
  * accumulator columns over four warpgroups; it is chosen only when set or
  * measured faster (it wins where few rows lie near a tie).  Every form

@@ -256,14 +256,14 @@ int objective_form(const hpc_ctx *c, int d, int k, int64_t n) {
   }
   for (const auto &f : c->forms)
     if (f.first == form_key(d, k) && form_supported(f.second, d, k, n)) return f.second;
-  // built-in choice, from measurements on GB300: split TF32 for d = 32 with
-  // k <= 64 (1.5x the CUDA-core search at k = 25); TF32 for d = 64 / 128 with
-  // k <= 128; at d = 16, or d = 32 with k > 64, the CUDA-core search is as
-  // fast or faster.  For k > 128 the TF32 search wins only where few rows
+  // built-in choice, from measurements on GB300 with the incumbents the
+  // method produces: split TF32 for d = 32 (1.5x the CUDA-core search at
+  // k = 25, 1.45x at k = 100); TF32 for d = 64 / 128 with k <= 128; at d = 16
+  // the two are within a few percent and the CUDA cores are kept.  For k > 128 the TF32 search wins only where few rows
   // sit near a tie (5x at k = 500 with one centroid per mixture component,
   // 2x slower with several per component, as K-means leaves them on skewed
   // mixtures): the CUDA cores unless a measurement says otherwise
-  if (d == 32 && k <= 64 && hpc_tcs_objective_supported(d, k, n)) return HPC_SEARCH_SPLIT_TF32;
+  if (d == 32 && hpc_tcs_objective_supported(d, k, n)) return HPC_SEARCH_SPLIT_TF32;
   if (d >= 64 && k <= 128 && hpc_tc_objective_supported(d, k, n)) return HPC_SEARCH_TF32;
   return HPC_SEARCH_SIMT;
 }

@@ -53,8 +53,11 @@ __host__ __device__ constexpr int ts_pow2_cols(int c) {
 
 // One CTA per SM (the occupancy rules give tensor-memory kernels one) with
 // NWG independent warpgroup pipelines; each owns COLS_WG TMEM columns: one or
-// two A buffers (x_h | x_l, 2 D columns each) and two accumulators (NP
-// columns each).
+// two A buffers (x_h | x_l, 2 D columns each) and NACC accumulators (NP
+// columns each).  Two accumulators let the MMAs of tile i + 1 run during the
+// epilogue of tile i; where two would leave a single warpgroup (NP = 128)
+// each warpgroup keeps one and runs its tiles strictly one after another,
+// and two warpgroups overlap each other instead.
 template <int D, int NP>
 struct TsCfg {
   static constexpr uint32_t RB = D * 4;                 // bytes per row: 64 or 128
@@ -62,8 +65,11 @@ struct TsCfg {
   static constexpr uint32_t TILE = TS_M * RB;
   static constexpr uint32_t BPART = NP * RB;  // one B part (hi or lo)
   // a second A buffer when it fits in the same power-of-two column count
-  static constexpr int NBUF_A = ts_pow2_cols(4 * D + 2 * NP) == ts_pow2_cols(2 * D + 2 * NP) ? 2 : 1;
-  static constexpr int COLS_WG = ts_pow2_cols(2 * D * NBUF_A + 2 * NP);
+  static constexpr int NBUF_A2 = ts_pow2_cols(4 * D + 2 * NP) == ts_pow2_cols(2 * D + 2 * NP) ? 2 : 1;
+  static constexpr int NACC = 512 / ts_pow2_cols(2 * D * NBUF_A2 + 2 * NP) >= 2 ? 2 : 1;
+  static constexpr int NBUF_A =
+      NACC == 2 ? NBUF_A2 : (ts_pow2_cols(4 * D + NP) == ts_pow2_cols(2 * D + NP) ? 2 : 1);
+  static constexpr int COLS_WG = ts_pow2_cols(2 * D * NBUF_A + NACC * NP);
   static constexpr int NWG = 512 / COLS_WG > 4 ? 4 : 512 / COLS_WG;
   static constexpr int THREADS = 128 * NWG;
   static constexpr int COLS = COLS_WG * NWG;
@@ -198,7 +204,8 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
   hpc_tc_fence_after();
   const uint32_t tmem = s_tmem + (uint32_t)(wg * Cfg::COLS_WG);  // this warpgroup's columns
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-  const uint32_t d_col = 2 * D * Cfg::NBUF_A;  // A buffer(s), then two accumulators
+  const uint32_t d_col = 2 * D * Cfg::NBUF_A;  // A buffer(s), then the accumulator(s)
+  auto acc_col = [&](int i) { return d_col + (uint32_t)(Cfg::NACC == 2 ? (i & 1) * NP : 0); };
   // with two A buffers the epilogue reads its row back from TMEM
   // (x = x_h + x_l exactly); with one, the row waits in registers
   const bool run = cs.live > 0 && my > 0;
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
       constexpr uint32_t idesc = hpc_umma_idesc(2u, 2u, NP, TS_M);
       const uint32_t B = hpc_smem_u32(bop);
       const uint32_t a0 = tmem + a_col;
-      const uint32_t d0 = tmem + d_col + (uint32_t)((i & 1) * NP);
+      const uint32_t d0 = tmem + acc_col(i);
 #pragma unroll
       for (int ks = 0; ks < D / 8; ++ks) {
         const uint64_t bh = hpc_umma_desc(B + (uint32_t)ks * 32u, 16u, 8u * Cfg::RB, Cfg::SWZ);
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
         for (int c = 0; c < NP / 32; ++c) {
           if (c * 32 >= cs.kp) break;  // same for the whole CTA
           float acc[32];
-          hpc_tmem_ld32(tmem + lane_base + d_col + (uint32_t)((i & 1) * NP + 32 * c), acc);
+          hpc_tmem_ld32(tmem + lane_base + acc_col(i) + (uint32_t)(32 * c), acc);
           if constexpr (IB > 0) {
 #pragma unroll
             for (int jj = 0; jj < 32; jj += 4) {
@@ -467,13 +474,22 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
     };
     // row registers alternate between the two arrays (no copies)
     float xa[XT ? 1 : D], xb[XT ? 1 : D];
-    bool go = stage(0, xa);
-    for (int i = 0; go && i < my; i += 2) {
-      if (i + 1 < my) go = stage(i + 1, xb);
-      epilogue(i, xa);
-      if (!go || i + 1 >= my) break;
-      if (i + 2 < my) go = stage(i + 2, xa);
-      epilogue(i + 1, xb);
+    if constexpr (Cfg::NACC == 2) {
+      bool go = stage(0, xa);
+      for (int i = 0; go && i < my; i += 2) {
+        if (i + 1 < my) go = stage(i + 1, xb);
+        epilogue(i, xa);
+        if (!go || i + 1 >= my) break;
+        if (i + 2 < my) go = stage(i + 2, xa);
+        epilogue(i + 1, xb);
+      }
+    } else {
+      // one accumulator: the MMAs of tile i + 1 are issued (inside stage, after
+      // the warpgroup barrier) only once every thread has read tile i's
+      for (int i = 0; i < my; ++i) {
+        if (!stage(i, xa)) break;
+        epilogue(i, xa);
+      }
     }
   }
 
