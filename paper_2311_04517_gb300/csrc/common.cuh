@@ -70,7 +70,10 @@ __device__ __forceinline__ uint64_t hpc_scale_word(uint64_t r, uint64_t m) {
 // task's blocks) of a cooperative launch, with a bounded wait.  Returns false
 // (in every thread of the block) when the device status word carries an
 // error, including a wait that ran past the limit; the caller then returns.
-// The barrier words are zeroed before each launch.
+// The barrier words are zeroed before each launch.  `arrive` counts every
+// arrival of the launch (generation g is complete at (g + 1) nblocks);
+// `gen` is the generation, bit 31 set when the last block of a generation
+// saw an error in the status word.
 // ---------------------------------------------------------------------------
 struct hpc_gridbar {
   unsigned int arrive;
@@ -85,6 +88,14 @@ __device__ __forceinline__ unsigned hpc_ld_acquire(const unsigned *p) {
 
 __device__ __forceinline__ void hpc_st_release(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// atomic add with acquire-release semantics at GPU scope; returns the old value
+__device__ __forceinline__ unsigned hpc_atom_add_acq_rel(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
 }
 
 __device__ __forceinline__ uint64_t hpc_globaltimer() {
@@ -107,30 +118,37 @@ static __device__ __noinline__ bool hpc_grid_sync(hpc_gridbar *bar, int *status,
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
+    // a block arrives at generation g only after it saw g released, and g
+    // cannot advance before it arrives: this read is the current generation
     const unsigned g = hpc_ld_acquire(&bar->gen);
+    // the fence makes the whole block's writes (ordered before this thread by
+    // __syncthreads) visible at GPU scope, as a grid-wide sync does; the
+    // acquire half of the count lets the last block see every other block's
     __threadfence();
-    const unsigned prev = atomicAdd(&bar->arrive, 1u);
-    if (prev == nblocks - 1) {
-      atomicExch(&bar->arrive, 0u);
-      __threadfence();
-      hpc_st_release(&bar->gen, g + 1);
+    const unsigned prev = hpc_atom_add_acq_rel(&bar->arrive, 1u);
+    if ((prev + 1u) % nblocks == 0u) {
+      const bool err = hpc_status_get(status) != 0;
+      hpc_st_release(&bar->gen, (g + 1u) | (err ? 0x80000000u : 0u));
+      ok = err ? 0 : 1;
     } else {
       const uint64_t t0 = hpc_globaltimer();
-      while (hpc_ld_acquire(&bar->gen) == g) {
-        if (hpc_status_get(status) != 0) {
-          ok = 0;
-          break;
+      unsigned v;
+      for (unsigned n = 1; (v = hpc_ld_acquire(&bar->gen)) == g; ++n) {
+        if ((n & 31u) == 0u) {  // the status word and the clock, now and then
+          if (hpc_status_get(status) != 0) {
+            ok = 0;
+            break;
+          }
+          if (hpc_globaltimer() - t0 > limit_ns) {
+            hpc_status_set(status, HPC_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
         }
-        if (hpc_globaltimer() - t0 > limit_ns) {
-          hpc_status_set(status, HPC_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(100);
+        __nanosleep(32);
       }
+      if (ok && (v & 0x80000000u)) ok = 0;
     }
-    __threadfence();
-    if (hpc_status_get(status) != 0) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
