@@ -36,17 +36,17 @@ struct LloydArgs {
 // Objective: several rows per thread amortise the centroid reads.
 template <int D>
 struct Tile {
-  static constexpr int R = D <= 4 ? 8 : D <= 16 ? 4 : D <= 32 ? 2 : 1;
+  static constexpr int R = D <= 4 ? 8 : D <= 16 ? 4 : D <= 64 ? 2 : 1;
   static constexpr int THREADS = 256;
 };
 
 // Lloyd: samples are small (10^4 - 10^6 rows): one or two rows per thread
-// spread an iteration over every SM (two at d <= 16, so that a 10^5-row
-// sample takes one row group per block); the accumulation maps lanes to
-// dimensions.
+// spread an iteration over every SM (two at d <= 64: every centroid read
+// from shared memory serves two rows; at d = 16 a 10^5-row sample then takes
+// one row group per block); the accumulation maps lanes to dimensions.
 template <int D>
 struct LTile {
-  static constexpr int R = D <= 16 ? 2 : 1;
+  static constexpr int R = D <= 64 ? 2 : 1;
   static constexpr int THREADS = 256;
   static constexpr int MINB = D <= 32 ? 2 : 1;
   static constexpr int LPR = D < 32 ? D : 32;          // lanes per row
