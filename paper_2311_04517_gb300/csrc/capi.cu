@@ -245,6 +245,8 @@ bool form_supported(int form, int d, int k, int64_t n) {
 
 int64_t form_key(int d, int k) { return (int64_t)d << 32 | (uint32_t)k; }
 
+int builtin_form(int d, int k, int64_t n);
+
 // The search form hpc_objective runs for (d, k, n) in the context's mode.
 int objective_form(const hpc_ctx *c, int d, int k, int64_t n) {
   if (c->force_form >= 0) return c->force_form;
@@ -256,6 +258,10 @@ int objective_form(const hpc_ctx *c, int d, int k, int64_t n) {
   }
   for (const auto &f : c->forms)
     if (f.first == form_key(d, k) && form_supported(f.second, d, k, n)) return f.second;
+  return builtin_form(d, k, n);
+}
+
+int builtin_form(int d, int k, int64_t n) {
   // built-in choice, from measurements on GB300 with the incumbents the
   // method produces: split TF32 for d = 32 (1.5x the CUDA-core search at
   // k = 25, 1.45x at k = 100); TF32 for d = 64 / 128 with k <= 128; at d = 16
@@ -764,10 +770,10 @@ int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, con
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_fail(c, cudaGetLastError(), "event create");
   int best = -1;
-  float best_ms = 0.0f;
+  float best_ms = 0.0f, tms[3] = {-1.0f, -1.0f, -1.0f};
   int rc = HPC_OK;
   for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_TF32 && rc == HPC_OK; ++form) {
-    if (ms_out) ms_out[form] = -1.0f;
+    tms[form] = -1.0f;
     if (!form_supported(form, d, k, n)) continue;
     c->force_form = form;
     Carver cw = cv;
@@ -789,7 +795,7 @@ int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, con
     }
     if ((rc = hpc_sync_status(c)) != HPC_OK) break;  // a device error ends the sweep
     ms /= (float)reps;
-    if (ms_out) ms_out[form] = ms;
+    tms[form] = ms;
     if (best < 0 || ms < best_ms) {
       best = form;
       best_ms = ms;
@@ -799,6 +805,12 @@ int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, con
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != HPC_OK) return rc;
+  // within 1% of the fastest, the built-in form stays: timing noise then
+  // does not move the choice from run to run
+  const int bi = builtin_form(d, k, n);
+  if (bi != best && tms[bi] > 0.0f && tms[bi] <= 1.01f * best_ms) best = bi;
+  if (ms_out)
+    for (int f = 0; f < 3; ++f) ms_out[f] = tms[f];
   if (form_out) *form_out = best;
   return hpc_set_objective_form(c, d, k, best);
 }

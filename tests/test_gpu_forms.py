@@ -123,7 +123,8 @@ def test_autotune_picks_a_built_form_and_keeps_results(ctx, d, k):
     assert form in forms
     assert sorted(ms) == sorted(H.SEARCH_NAMES[f] for f in forms)
     assert all(t > 0 for t in ms.values())
-    assert ms[H.SEARCH_NAMES[form]] == min(ms.values())
+    # the fastest, or the built-in form within 1% of it
+    assert ms[H.SEARCH_NAMES[form]] <= 1.01 * min(ms.values())
     assert ctx.objective_form(n, d, k) == form
     f1, lab1 = objective(ctx, X, C)
     assert f1 == pytest.approx(f0, rel=1e-9)
