@@ -432,3 +432,23 @@ def test_bounded_wait_reports_timeout(ctx):
     f = H.hpc_objective(ctx, dev(X), dev(X[:3].copy()))
     ctx.check_status()
     assert float(host(f)[0]) == pytest.approx(orc.objective(X, X[:3]), rel=RTOL)
+
+
+def test_round_with_non_finite_rows_reports_and_recovers(ctx):
+    # 1% of the rows non-finite: every worker's sample draws some, so every
+    # Lloyd task stops at its first barrier and the round ends with
+    # HPC_ERR_NONFINITE (no wait runs out); the incumbents stay as they were
+    # and the next round on finite data matches the oracle
+    X = mixture(20000, 8, 6, 31, sd=1.0)
+    Xd = dev(X)
+    batch = H.Batch(8, [3000, 5000, 4000, 2500], [6, 6, 9, 6], [0, 0, 1, 0])
+    check_round(ctx, X, Xd, batch, H.HPC_COMPETITIVE, 5, 0)
+    before = (host(batch.C).copy(), host(batch.degenerate).copy(), host(batch.fhat).copy())
+    Xn = X.copy()
+    Xn[::100, 3] = np.nan
+    H.hpc_round(ctx, dev(Xn), batch, H.HPC_COMPETITIVE, 5, 1)
+    assert ctx.sync_status() == H.HPC_ERR_NONFINITE
+    np.testing.assert_array_equal(host(batch.C), before[0])
+    np.testing.assert_array_equal(host(batch.degenerate), before[1])
+    np.testing.assert_array_equal(host(batch.fhat), before[2])
+    check_round(ctx, X, Xd, batch, H.HPC_COMPETITIVE, 5, 1)
