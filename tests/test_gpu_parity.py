@@ -255,7 +255,10 @@ def lockstep_divergence(ctx, S, C0, deg0, iters):
 
 
 @pytest.mark.parametrize("s,d,k,seed", [(2000, 2, 5, 0), (100000, 16, 25, 1), (20000, 32, 50, 2),
-                                        (9001, 64, 30, 3), (5000, 128, 10, 4), (30011, 5, 8, 5)])
+                                        (9001, 64, 30, 3), (5000, 128, 10, 4), (30011, 5, 8, 5),
+                                        # d in (64, 128]: the d = 128 kernel, and at d = 100
+                                        # its rows padded with zeros
+                                        (30011, 128, 40, 6), (7001, 100, 17, 7)])
 def test_lloyd_parity(ctx, s, d, k, seed):
     S = mixture(s, d, k, seed, sd=1.5)
     init = orc.kmeanspp(S, np.zeros((k, d), np.float32), np.ones(k, np.uint8), seed=seed)
