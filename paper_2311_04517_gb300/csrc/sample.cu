@@ -75,12 +75,25 @@ __global__ void __launch_bounds__(SB_THREADS) sample_batch_kernel(
   }
   __syncthreads();
   if (VEC4) {
-    const int d4 = d >> 2;
+    // eight independent row loads in flight per thread before their stores
+    const int d4 = d >> 2, tot = rows * d4;
     const float4 *X4 = reinterpret_cast<const float4 *>(X);
     float4 *S4 = reinterpret_cast<float4 *>(t.S) + r0 * d4;
-    for (int e = threadIdx.x; e < rows * d4; e += SB_THREADS) {
-      const int i = e / d4, c = e - i * d4;
-      S4[e] = __ldg(X4 + s_idx[i] * d4 + c);
+    for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * SB_THREADS) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * SB_THREADS;
+        if (e < tot) {
+          const int i = e / d4, c = e - i * d4;
+          v[u] = __ldg(X4 + s_idx[i] * d4 + c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * SB_THREADS;
+        if (e < tot) S4[e] = v[u];
+      }
     }
   } else {
     float *S = t.S + r0 * d;
