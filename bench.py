@@ -83,13 +83,29 @@ def peaks():
     return FALLBACK_HBM, "fallback"
 
 
-def kernel_source_hash() -> str:
-    """Hash of the device sources (every file of csrc/ but the host-side C
-    ABI, capi.cu): a profile taken on other kernel code carries no traffic."""
+# the source files each profiled kernel is compiled from (its translation
+# unit and the kernel headers it includes)
+_COMMON = ["assign.cuh", "common.cuh", "kernels.h"]
+KERNEL_SOURCES = {
+    "objective_kernel": ["lloyd.cu"] + _COMMON,
+    "lloyd_kernel": ["lloyd.cu", "round.cuh"] + _COMMON,
+    "tcs_objective_kernel": ["tc_split.cu", "tc.cuh"] + _COMMON,
+    "tc_objective_kernel": ["tc_objective.cu", "tc_rows.cuh", "tc.cuh"] + _COMMON,
+    "tw_objective_kernel": ["tc_wide.cu", "tc_rows.cuh", "tc.cuh"] + _COMMON,
+}
+
+
+def kernel_source_hash(kernel: str | None = None) -> str:
+    """Hash of the sources of one profiled kernel (KERNEL_SOURCES), or of
+    every device source (csrc/ without the host-side capi.cu): a profile
+    taken on other code of that kernel carries no traffic."""
+    csrc = ROOT / "paper_2311_04517_gb300" / "csrc"
+    if kernel is None:
+        files = [p for p in sorted(csrc.glob("*")) if p.name != "capi.cu"]
+    else:
+        files = [csrc / f for f in KERNEL_SOURCES[kernel]]
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_2311_04517_gb300" / "csrc").glob("*")):
-        if p.name == "capi.cu":
-            continue
+    for p in files:
         h.update(p.read_bytes())
     return h.hexdigest()[:16]
 
@@ -109,7 +125,8 @@ def profiled_traffic(kernel: str, workload: str, kernel_name: str):
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     hs = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
-    if not m or not hs or hs.group(1) != kernel_source_hash():
+    if not m or not hs or kernel_name not in KERNEL_SOURCES or \
+            hs.group(1) != kernel_source_hash(kernel_name):
         return None
     return float(m.group(1))
 

@@ -135,8 +135,9 @@ int hpc_objective_form(hpc_ctx *ctx, int64_t n, int32_t d, int32_t k);
  * hpc_objective), reps timed calls each after one warm-up, with CUDA events
  * on the context's stream; keeps the fastest for (d, k) as
  * hpc_set_objective_form would (the built-in form when it is within 1% of
- * the fastest, so that timing noise does not move the choice).  *form_out (nullable) receives it,
- * ms_out (host float[3], nullable) the average milliseconds per call of each
+ * the fastest, so that timing noise does not move the choice).  *form_out
+ * (nullable) receives it, ms_out (host float[3], nullable) the average
+ * milliseconds per call of each
  * form, -1 where not built.  Synchronises the stream.  Errors: as
  * hpc_objective; a device error recorded during the sweep ends it and is
  * returned. */

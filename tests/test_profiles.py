@@ -34,10 +34,10 @@ def test_summary_has_title_and_command(path):
 
 
 def test_traffic_only_for_the_named_kernel_and_sources():
-    h = bench.kernel_source_hash()
     for p in (ROOT / "profiles").glob("objective_*.md"):
         txt = p.read_text()
         kernel = re.match(r"#\s+(\w+)", txt).group(1)
+        h = bench.kernel_source_hash(kernel)
         workload = p.stem.split("_")[1]
         rec = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
         src = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
