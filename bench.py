@@ -97,11 +97,13 @@ KERNEL_SOURCES = {
 
 def kernel_source_hash(kernel: str | None = None) -> str:
     """Hash of the sources of one profiled kernel (KERNEL_SOURCES), or of
-    every device source (csrc/ without the host-side capi.cu): a profile
-    taken on other code of that kernel carries no traffic."""
+    every device source a benchmark step can launch (csrc/ without the
+    host-side capi.cu and the cost model, which never runs in a step): a
+    profile taken on other code of that kernel carries no traffic."""
     csrc = ROOT / "paper_2311_04517_gb300" / "csrc"
     if kernel is None:
-        files = [p for p in sorted(csrc.glob("*")) if p.name != "capi.cu"]
+        skip = ("capi.cu", "costmodel.cu", "costmodel.h")
+        files = [p for p in sorted(csrc.glob("*")) if p.name not in skip]
     else:
         files = [csrc / f for f in KERNEL_SOURCES[kernel]]
     h = hashlib.sha256()

@@ -330,6 +330,78 @@ int hpc_objective_noalloc(const float *X, int64_t n, int32_t d, const float *C, 
                           const uint8_t *degenerate, double *f_out, int32_t *labels_out,
                           int32_t *status_out, void *stream);
 
+/* ---- learned cost model of the objective's search forms ------------------ */
+
+/* The paper has no learned component (Sections 3-4).  This network serves
+ * only the schedule choice of hpc_autotune_objective (which search form the
+ * full-data objective of Eq. 1 runs); it never touches an assignment or an
+ * objective value.  It is a perceptron with two hidden layers of
+ * HPC_CM_HIDDEN ReLU units that maps HPC_CM_NFEAT inputs to a predicted
+ * ln(nanoseconds per row) of one form:
+ *   y(x) = b3 + w3 . relu(b2 + W2 relu(b1 + W1 x)),
+ * trained on measured times with the mean squared error
+ *   L = (1/N) sum_i (y(x_i) - t_i)^2
+ * and full-batch Adam (Kingma and Ba 2015; beta1 = 0.9, beta2 = 0.999,
+ * eps = 1e-8).  Parameters are one float array of HPC_CM_NPARAM values:
+ * W1[H][F], b1[H], W2[H][H], b2[H], w3[H], b3 (row-major, F = HPC_CM_NFEAT,
+ * H = HPC_CM_HIDDEN).  Inputs per form (hpc_costmodel_features):
+ *   [0] log2(d) / 7            [1] log2(k) / 9
+ *   [2] padded columns / k - 1 (columns: the next of 32, 64, ..., 512)
+ *   [3] centroid separation: log2(max ||c||^2 / min ||c_i - c_j||^2) over
+ *       live centroids, clamped to [0, 40], / 40 (1 if two coincide, 0 with
+ *       fewer than two live)
+ *   [4..6] one-hot form (HPC_SEARCH_SIMT, _SPLIT_TF32, _TF32)
+ *   [7] 1 if k > 128 (the wide tensor-core kernel), else 0. */
+#define HPC_CM_NFEAT 8
+#define HPC_CM_HIDDEN 32
+#define HPC_CM_NPARAM 1377
+
+/* Mean squared error of the network `params` on N samples (feats N x
+ * HPC_CM_NFEAT, targets N) and its gradient: *loss_out (device float) and
+ * grad_out (device, HPC_CM_NPARAM floats).  FP32; the per-sample gradients
+ * are summed in a fixed order, so repeated calls give identical results.
+ * Errors: HPC_ERR_ARG (N < 1 or N > 2^20, NULL pointer), HPC_ERR_NOMEM,
+ * HPC_ERR_CUDA. */
+int hpc_costmodel_loss_grad(hpc_ctx *ctx, const float *params, const float *feats,
+                            const float *targets, int32_t N, float *loss_out, float *grad_out);
+
+/* `steps` full-batch Adam steps on params, with the first and second
+ * moments m and v (device, HPC_CM_NPARAM floats each, zero for a fresh
+ * start) carried by the caller; step s uses the bias corrections of step
+ * number step0 + s + 1, so training resumes exactly where an earlier call
+ * stopped.  loss_out (device, `steps` floats, nullable) receives the loss at
+ * the parameters each step started from.  Two launches per step.  Errors as
+ * hpc_costmodel_loss_grad, and HPC_ERR_ARG for steps < 0, step0 < 0 or a
+ * learning rate that is not positive and finite. */
+int hpc_costmodel_train(hpc_ctx *ctx, float *params, float *m, float *v, const float *feats,
+                        const float *targets, int32_t N, int32_t steps, int32_t step0, float lr,
+                        float *loss_out);
+
+/* Predictions y for N input rows (device feats N x HPC_CM_NFEAT, out N). */
+int hpc_costmodel_predict(hpc_ctx *ctx, const float *params, const float *feats, int32_t N,
+                          float *out);
+
+/* The network inputs of each of the three search forms for centroids C
+ * (device, k x d; degenerate nullable = all live): feats_out (HOST,
+ * 3 x HPC_CM_NFEAT floats, row f = form f) and supported_out (HOST, 3 ints,
+ * nullable: 1 where the form is built for (d, k)).  Copies C and the flags
+ * to the host and synchronises the stream.  Errors: HPC_ERR_ARG, HPC_ERR_CUDA. */
+int hpc_costmodel_features(hpc_ctx *ctx, const float *C, const uint8_t *degenerate, int32_t d,
+                           int32_t k, float *feats_out, int32_t *supported_out);
+
+/* hpc_autotune_objective guided by the network `params` (device): the forms
+ * built for (d, k) are ranked by predicted time; the best-ranked one is
+ * timed, and each other one only if its predicted time is within a factor
+ * (1 + margin) of the best-ranked one's.  The fastest timed form is kept as
+ * hpc_autotune_objective would keep it.  ms_out (host float[3], nullable)
+ * gets the time per call of each timed form, -1 for the others;
+ * timed_out (host, nullable) the number of forms timed.  margin >= 0; a
+ * very large margin times every form (the unguided search). */
+int hpc_autotune_objective_guided(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
+                                  const float *C, int32_t k, const uint8_t *degenerate,
+                                  int32_t reps, const float *params, float margin,
+                                  int32_t *form_out, float *ms_out, int32_t *timed_out);
+
 /* ---- diagnostics -------------------------------------------------------- */
 
 /* Throughput probes (the paper has no counterpart): the rates against which

@@ -7,9 +7,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
+#include "costmodel.h"
 #include "kernels.h"
 
 // Workers of one round launch per persistent kernel (every launch has at
@@ -753,14 +755,49 @@ int hpc_objective_form(hpc_ctx *c, int64_t n, int32_t d, int32_t k) {
   return objective_form(c, d, k, n);
 }
 
-int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float *C,
-                           int32_t k, const uint8_t *degenerate, int32_t reps, int32_t *form_out,
-                           float *ms_out) {
-  if (!c) return HPC_ERR_ARG;
+namespace {
+
+// Times `reps` calls of the objective in search form `form` (after one
+// warm-up call) with CUDA events on the context's stream: *ms per call.
+int time_form(hpc_ctx *c, const Carver &cv, double *f, const float *X, int64_t n, int32_t d,
+              const float *C, int32_t k, const uint8_t *degenerate, int32_t reps, int form,
+              cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+  c->force_form = form;
+  Carver cw = cv;
+  int rc = run_objective(c, cw, X, n, d, C, k, degenerate, f, nullptr);  // warm-up
+  cudaEventRecord(e0, c->stream);
+  for (int r = 0; r < reps && rc == HPC_OK; ++r) {
+    cw = cv;
+    rc = run_objective(c, cw, X, n, d, C, k, degenerate, f, nullptr);
+  }
+  cudaEventRecord(e1, c->stream);
+  c->force_form = -1;
+  if (rc != HPC_OK) return rc;
+  float t = 0.0f;
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune timing");
+  if ((rc = hpc_sync_status(c)) != HPC_OK) return rc;  // a device error ends the sweep
+  *ms = t / (float)reps;
+  return HPC_OK;
+}
+
+int check_autotune_args(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float *C,
+                        int32_t k, int32_t reps) {
   if (int rc = check_dims(c, d)) return rc;
   if (n < 1 || k < 1 || !X || !C || reps < 1 || reps > 1000)
     return fail(c, HPC_ERR_ARG, "bad sizes");
   if (!aligned16(X) || !aligned16(C)) return fail(c, HPC_ERR_ARG, "unaligned");
+  return HPC_OK;
+}
+
+// Times the forms in `order` (count entries; skip[i] true = not timed) and
+// keeps the fastest; within 1% of it the built-in form stays, so that timing
+// noise does not move the choice from run to run.
+int autotune_forms(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float *C, int32_t k,
+                   const uint8_t *degenerate, int32_t reps, const int *order, int count,
+                   const float *pred, float margin, int32_t *form_out, float *ms_out,
+                   int32_t *timed_out) {
   cudaSetDevice(c->device);
   if (int rc = ensure_ws(c, obj_ws(c) + 512)) return rc;
   if (int st = hpc_sync_status(c)) return st;  // start from a clean status
@@ -769,32 +806,18 @@ int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, con
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_fail(c, cudaGetLastError(), "event create");
-  int best = -1;
+  int best = -1, timed = 0;
   float best_ms = 0.0f, tms[3] = {-1.0f, -1.0f, -1.0f};
   int rc = HPC_OK;
-  for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_TF32 && rc == HPC_OK; ++form) {
-    tms[form] = -1.0f;
-    if (!form_supported(form, d, k, n)) continue;
-    c->force_form = form;
-    Carver cw = cv;
-    rc = run_objective(c, cw, X, n, d, C, k, degenerate, f, nullptr);  // warm-up
-    cudaEventRecord(e0, c->stream);
-    for (int r = 0; r < reps && rc == HPC_OK; ++r) {
-      cw = cv;
-      rc = run_objective(c, cw, X, n, d, C, k, degenerate, f, nullptr);
-    }
-    cudaEventRecord(e1, c->stream);
-    c->force_form = -1;
-    if (rc != HPC_OK) break;
+  for (int i = 0; i < count && rc == HPC_OK; ++i) {
+    const int form = order[i];
+    // guided: a form whose predicted time exceeds the best-ranked one's by
+    // more than the margin is not timed
+    if (pred && i > 0 && std::exp(pred[form] - pred[order[0]]) > 1.0 + (double)margin) continue;
     float ms = 0.0f;
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) {
-      rc = cuda_fail(c, e, "autotune timing");
-      break;
-    }
-    if ((rc = hpc_sync_status(c)) != HPC_OK) break;  // a device error ends the sweep
-    ms /= (float)reps;
+    rc = time_form(c, cv, f, X, n, d, C, k, degenerate, reps, form, e0, e1, &ms);
+    if (rc != HPC_OK) break;
+    ++timed;
     tms[form] = ms;
     if (best < 0 || ms < best_ms) {
       best = form;
@@ -805,14 +828,181 @@ int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, con
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != HPC_OK) return rc;
-  // within 1% of the fastest, the built-in form stays: timing noise then
-  // does not move the choice from run to run
   const int bi = builtin_form(d, k, n);
   if (bi != best && tms[bi] > 0.0f && tms[bi] <= 1.01f * best_ms) best = bi;
   if (ms_out)
-    for (int f = 0; f < 3; ++f) ms_out[f] = tms[f];
+    for (int q = 0; q < 3; ++q) ms_out[q] = tms[q];
   if (form_out) *form_out = best;
+  if (timed_out) *timed_out = timed;
   return hpc_set_objective_form(c, d, k, best);
+}
+
+// ---- cost-model inputs (host) ----
+
+// log2(max ||c||^2 / min ||c_i - c_j||^2) over live centroids, clamped to
+// [0, 40] and divided by 40; 1 when two live centroids coincide, 0 with
+// fewer than two live.
+float cm_separation(const float *Ch, const uint8_t *degh, int d, int k) {
+  double cmax2 = 0.0, minsep = -1.0;
+  int live = 0;
+  for (int i = 0; i < k; ++i) {
+    if (degh && degh[i]) continue;
+    ++live;
+    double s = 0.0;
+    for (int t = 0; t < d; ++t) s += (double)Ch[(size_t)i * d + t] * Ch[(size_t)i * d + t];
+    cmax2 = std::max(cmax2, s);
+    for (int j = 0; j < i; ++j) {
+      if (degh && degh[j]) continue;
+      double q = 0.0;
+      for (int t = 0; t < d; ++t) {
+        const double u = (double)Ch[(size_t)i * d + t] - Ch[(size_t)j * d + t];
+        q += u * u;
+      }
+      if (minsep < 0.0 || q < minsep) minsep = q;
+    }
+  }
+  if (live < 2) return 0.0f;
+  if (minsep <= 0.0) return 1.0f;
+  if (cmax2 <= 0.0) return 0.0f;
+  const double r = std::log2(cmax2 / minsep);
+  return (float)(std::min(std::max(r, 0.0), 40.0) / 40.0);
+}
+
+void cm_features(int d, int k, float sep, float *out) {
+  const int cols = k <= 32 ? 32 : k <= 64 ? 64 : k <= 128 ? 128 : k <= 256 ? 256 : 512;
+  for (int form = 0; form < 3; ++form) {
+    float *r = out + form * HPC_CM_NFEAT;
+    r[0] = (float)(std::log2((double)d) / 7.0);
+    r[1] = (float)(std::log2((double)k) / 9.0);
+    r[2] = (float)((double)cols / k - 1.0);
+    r[3] = sep;
+    r[4] = form == HPC_SEARCH_SIMT ? 1.0f : 0.0f;
+    r[5] = form == HPC_SEARCH_SPLIT_TF32 ? 1.0f : 0.0f;
+    r[6] = form == HPC_SEARCH_TF32 ? 1.0f : 0.0f;
+    r[7] = k > 128 ? 1.0f : 0.0f;
+  }
+}
+
+}  // namespace
+
+int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float *C,
+                           int32_t k, const uint8_t *degenerate, int32_t reps, int32_t *form_out,
+                           float *ms_out) {
+  if (!c) return HPC_ERR_ARG;
+  if (int rc = check_autotune_args(c, X, n, d, C, k, reps)) return rc;
+  int order[3], count = 0;
+  for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_TF32; ++form)
+    if (form_supported(form, d, k, n)) order[count++] = form;
+  return autotune_forms(c, X, n, d, C, k, degenerate, reps, order, count, nullptr, 0.0f, form_out,
+                        ms_out, nullptr);
+}
+
+int hpc_costmodel_features(hpc_ctx *c, const float *C, const uint8_t *degenerate, int32_t d,
+                           int32_t k, float *feats_out, int32_t *supported_out) {
+  if (!c) return HPC_ERR_ARG;
+  if (int rc = check_dims(c, d)) return rc;
+  if (k < 1 || k > 1 << 16 || !C || !feats_out) return fail(c, HPC_ERR_ARG, "bad sizes");
+  cudaSetDevice(c->device);
+  std::vector<float> Ch((size_t)k * d);
+  std::vector<uint8_t> dh(degenerate ? (size_t)k : 0);
+  cudaError_t e = cudaMemcpyAsync(Ch.data(), C, Ch.size() * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && degenerate)
+    e = cudaMemcpyAsync(dh.data(), degenerate, dh.size(), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cost-model inputs");
+  cm_features(d, k, cm_separation(Ch.data(), degenerate ? dh.data() : nullptr, d, k), feats_out);
+  if (supported_out)
+    for (int form = 0; form < 3; ++form) supported_out[form] = form_supported(form, d, k, 1) ? 1 : 0;
+  return HPC_OK;
+}
+
+namespace {
+int check_cm_args(hpc_ctx *c, const void *params, const void *feats, int32_t N) {
+  if (!params || !feats) return fail(c, HPC_ERR_ARG, "NULL cost-model array");
+  if (N < 1 || N > (1 << 20)) return fail(c, HPC_ERR_ARG, "cost-model samples in [1, 2^20]");
+  return HPC_OK;
+}
+}  // namespace
+
+int hpc_costmodel_loss_grad(hpc_ctx *c, const float *params, const float *feats,
+                            const float *targets, int32_t N, float *loss_out, float *grad_out) {
+  if (!c) return HPC_ERR_ARG;
+  if (int rc = check_cm_args(c, params, feats, N)) return rc;
+  if (!targets || !loss_out || !grad_out) return fail(c, HPC_ERR_ARG, "NULL cost-model array");
+  cudaSetDevice(c->device);
+  if (int rc = ensure_ws(c, hpc_cm_part_floats(N) * 4 + 256)) return rc;
+  if (hpc_cm_grad_launch(c->L, params, feats, targets, N, reinterpret_cast<float *>(c->ws),
+                         nullptr, nullptr, 0.0f, 1.0f, 1.0f, grad_out, loss_out))
+    return cuda_fail(c, cudaGetLastError(), "cost-model gradient launch");
+  c->launches += 2;
+  return HPC_OK;
+}
+
+int hpc_costmodel_train(hpc_ctx *c, float *params, float *m, float *v, const float *feats,
+                        const float *targets, int32_t N, int32_t steps, int32_t step0, float lr,
+                        float *loss_out) {
+  if (!c) return HPC_ERR_ARG;
+  if (int rc = check_cm_args(c, params, feats, N)) return rc;
+  if (!targets || !m || !v) return fail(c, HPC_ERR_ARG, "NULL cost-model array");
+  if (steps < 0 || step0 < 0 || !(lr > 0.0f) || !std::isfinite(lr))
+    return fail(c, HPC_ERR_ARG, "bad training schedule");
+  cudaSetDevice(c->device);
+  if (int rc = ensure_ws(c, hpc_cm_part_floats(N) * 4 + 256)) return rc;
+  for (int s = 0; s < steps; ++s) {
+    const double t = (double)step0 + s + 1;
+    const float bc1 = (float)(1.0 - std::pow(0.9, t)), bc2 = (float)(1.0 - std::pow(0.999, t));
+    if (hpc_cm_grad_launch(c->L, params, feats, targets, N, reinterpret_cast<float *>(c->ws), m,
+                           v, lr, bc1, bc2, nullptr, loss_out ? loss_out + s : nullptr))
+      return cuda_fail(c, cudaGetLastError(), "cost-model training launch");
+    c->launches += 2;
+  }
+  return HPC_OK;
+}
+
+int hpc_costmodel_predict(hpc_ctx *c, const float *params, const float *feats, int32_t N,
+                          float *out) {
+  if (!c) return HPC_ERR_ARG;
+  if (int rc = check_cm_args(c, params, feats, N)) return rc;
+  if (!out) return fail(c, HPC_ERR_ARG, "NULL cost-model array");
+  cudaSetDevice(c->device);
+  if (hpc_cm_predict_launch(c->L, params, feats, N, out))
+    return cuda_fail(c, cudaGetLastError(), "cost-model prediction launch");
+  c->launches += 1;
+  return HPC_OK;
+}
+
+int hpc_autotune_objective_guided(hpc_ctx *c, const float *X, int64_t n, int32_t d,
+                                  const float *C, int32_t k, const uint8_t *degenerate,
+                                  int32_t reps, const float *params, float margin,
+                                  int32_t *form_out, float *ms_out, int32_t *timed_out) {
+  if (!c) return HPC_ERR_ARG;
+  if (int rc = check_autotune_args(c, X, n, d, C, k, reps)) return rc;
+  if (!params || !(margin >= 0.0f)) return fail(c, HPC_ERR_ARG, "bad cost model or margin");
+  float feats[3 * HPC_CM_NFEAT];
+  int32_t sup[3];
+  if (int rc = hpc_costmodel_features(c, C, degenerate, d, k, feats, sup)) return rc;
+  int order[3], count = 0;
+  for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_TF32; ++form)
+    if (sup[form] && form_supported(form, d, k, n)) order[count++] = form;
+  // predictions for the three forms, by the network on the device
+  if (int rc = ensure_ws(c, 512 + obj_ws(c))) return rc;
+  float *dfeat = reinterpret_cast<float *>(c->ws);
+  float *dpred = dfeat + 3 * HPC_CM_NFEAT;
+  float pred[3];
+  cudaError_t e = cudaMemcpyAsync(dfeat, feats, sizeof(feats), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cost-model inputs");
+  if (hpc_cm_predict_launch(c->L, params, dfeat, 3, dpred))
+    return cuda_fail(c, cudaGetLastError(), "cost-model prediction launch");
+  c->launches += 1;
+  e = cudaMemcpyAsync(pred, dpred, sizeof(pred), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cost-model prediction");
+  for (int q = 0; q < 3; ++q)
+    if (!std::isfinite(pred[q])) return fail(c, HPC_ERR_ARG, "cost model predicts a non-finite time");
+  // rank by predicted time, ties to the lower form index
+  std::stable_sort(order, order + count, [&](int a, int b) { return pred[a] < pred[b]; });
+  return autotune_forms(c, X, n, d, C, k, degenerate, reps, order, count, pred, margin, form_out,
+                        ms_out, timed_out);
 }
 
 // ---- checkpoint of a worker batch ----------------------------------------

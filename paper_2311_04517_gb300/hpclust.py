@@ -35,6 +35,9 @@ PROBES = {HPC_PROBE_FFMA: ("fp32 fma", "FMA/s"), HPC_PROBE_FFMA2: ("fp32x2 fma",
           HPC_PROBE_DFMA: ("fp64 fma", "FMA/s"), HPC_PROBE_FMIN: ("fp32 min", "op/s"),
           HPC_PROBE_L2_READ: ("L2 read", "B/s"), HPC_PROBE_HBM_READ: ("HBM read", "B/s")}
 
+# Cost model of the objective's search forms (include/hpclust.h).
+HPC_CM_NFEAT, HPC_CM_HIDDEN, HPC_CM_NPARAM = 8, 32, 1377
+
 # The paper's hyperparameters (Section 6.5).
 MAX_ITER = 300
 REL_TOL = 1e-4
@@ -104,6 +107,16 @@ def load() -> ctypes.CDLL:
         "hpc_autotune_objective": ([P, P, i64, i32, P, i32, P, i32,
                                     ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "hpc_costmodel_loss_grad": ([P, P, P, P, i32, P, P], ctypes.c_int),
+        "hpc_costmodel_train": ([P, P, P, P, P, P, i32, i32, i32, ctypes.c_float, P],
+                                ctypes.c_int),
+        "hpc_costmodel_predict": ([P, P, P, i32, P], ctypes.c_int),
+        "hpc_costmodel_features": ([P, P, P, i32, i32, ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "hpc_autotune_objective_guided": ([P, P, i64, i32, P, i32, P, i32, P, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "hpc_batch_save": ([P, ctypes.POINTER(hpc_batch), i32, u32, u64, i32, P, i64,
                             ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "hpc_batch_load": ([P, ctypes.POINTER(hpc_batch), i32, P, i64,
@@ -209,6 +222,25 @@ class Context:
                                                     _ptr(degenerate), int(reps),
                                                     ctypes.byref(form), ms))
         return int(form.value), {SEARCH_NAMES[i]: float(ms[i]) for i in range(3) if ms[i] >= 0}
+
+    def autotune_objective_guided(self, X, C, params, degenerate=None, reps: int = 5,
+                                  margin: float = 0.25):
+        """hpc_autotune_objective guided by the cost-model network `params`:
+        returns (form, {form name: ms per call of each timed form}, forms timed)."""
+        n, d = X.shape
+        k = C.shape[0]
+        _need(X, torch.float32, "X", self.device)
+        _need(C, torch.float32, "C", self.device)
+        _need(params, torch.float32, "params", self.device)
+        _need(degenerate, torch.uint8, "degenerate", self.device)
+        form = ctypes.c_int32(-1)
+        timed = ctypes.c_int32(0)
+        ms = (ctypes.c_float * 3)()
+        self._check(self.lib.hpc_autotune_objective_guided(
+            self.h, _ptr(X), n, d, _ptr(C), k, _ptr(degenerate), int(reps), _ptr(params),
+            float(margin), ctypes.byref(form), ms, ctypes.byref(timed)))
+        return (int(form.value), {SEARCH_NAMES[i]: float(ms[i]) for i in range(3) if ms[i] >= 0},
+                int(timed.value))
 
     def selftest_wait_timeout(self, limit_ns: int):
         """Launches the bounded-wait self-test (see include/hpclust.h)."""
@@ -385,3 +417,63 @@ def hpc_peak_probe(kind: int, device: int = 0, stream: torch.cuda.Stream | None 
     if rc != HPC_OK:
         raise HPCError(rc, "hpc_peak_probe failed")
     return float(rate.value), float(ms.value)
+
+
+# ---- cost model of the objective's search forms -------------------------
+
+def _cm_check(params, feats, N, dev):
+    _need(params, torch.float32, "params", dev)
+    _need(feats, torch.float32, "feats", dev)
+    if params.numel() != HPC_CM_NPARAM:
+        raise ValueError(f"params: expected {HPC_CM_NPARAM} values")
+    if feats.numel() != N * HPC_CM_NFEAT:
+        raise ValueError(f"feats: expected {N} x {HPC_CM_NFEAT} values")
+
+
+def hpc_costmodel_loss_grad(ctx: Context, params, feats, targets):
+    """(loss, gradient) device tensors of the network's mean squared error."""
+    N = targets.numel()
+    _cm_check(params, feats, N, ctx.device)
+    _need(targets, torch.float32, "targets", ctx.device)
+    loss = torch.empty(1, dtype=torch.float32, device=ctx.device)
+    grad = torch.empty(HPC_CM_NPARAM, dtype=torch.float32, device=ctx.device)
+    ctx._check(ctx.lib.hpc_costmodel_loss_grad(ctx.h, _ptr(params), _ptr(feats), _ptr(targets),
+                                               N, _ptr(loss), _ptr(grad)))
+    return loss, grad
+
+
+def hpc_costmodel_train(ctx: Context, params, m, v, feats, targets, steps: int, step0: int = 0,
+                        lr: float = 3e-3, loss_out=None):
+    """`steps` Adam steps on params (in place), moments m, v carried."""
+    N = targets.numel()
+    _cm_check(params, feats, N, ctx.device)
+    for t, name in ((m, "m"), (v, "v"), (targets, "targets"), (loss_out, "loss_out")):
+        _need(t, torch.float32, name, ctx.device)
+    if m.numel() != HPC_CM_NPARAM or v.numel() != HPC_CM_NPARAM:
+        raise ValueError("m, v: one value per parameter")
+    if loss_out is not None and loss_out.numel() < steps:
+        raise ValueError("loss_out: one value per step")
+    ctx._check(ctx.lib.hpc_costmodel_train(ctx.h, _ptr(params), _ptr(m), _ptr(v), _ptr(feats),
+                                           _ptr(targets), N, int(steps), int(step0), float(lr),
+                                           _ptr(loss_out)))
+
+
+def hpc_costmodel_predict(ctx: Context, params, feats):
+    N = feats.numel() // HPC_CM_NFEAT
+    _cm_check(params, feats, N, ctx.device)
+    out = torch.empty(N, dtype=torch.float32, device=ctx.device)
+    ctx._check(ctx.lib.hpc_costmodel_predict(ctx.h, _ptr(params), _ptr(feats), N, _ptr(out)))
+    return out
+
+
+def hpc_costmodel_features(ctx: Context, C, degenerate=None):
+    """(3 x HPC_CM_NFEAT host float tensor, [supported per form])."""
+    k, d = C.shape
+    _need(C, torch.float32, "C", ctx.device)
+    _need(degenerate, torch.uint8, "degenerate", ctx.device)
+    feats = (ctypes.c_float * (3 * HPC_CM_NFEAT))()
+    sup = (ctypes.c_int32 * 3)()
+    ctx._check(ctx.lib.hpc_costmodel_features(ctx.h, _ptr(C), _ptr(degenerate), d, k, feats,
+                                              sup))
+    return (torch.tensor(list(feats), dtype=torch.float32).view(3, HPC_CM_NFEAT),
+            [int(x) for x in sup])
