@@ -428,6 +428,7 @@ def time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev):
 
 def run_mine(args):
     from paper_2311_04517_gb300 import hpclust as H
+    from paper_2311_04517_gb300 import costmodel as CM
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -506,6 +507,12 @@ def run_mine(args):
     forms = {}
     if args.autotune and args.tensor_cores == 2:
         rows = min(wl.n, max(1, 512_000_000 // (4 * wl.d)))   # a prefix larger than L2
+        # beside it, the search guided by the shipped cost model (what it
+        # would pick and how many forms it times); the exhaustive choice stays
+        cm_params = None
+        if CM.OUT.exists():
+            cm_params = torch.tensor(json.loads(CM.OUT.read_text())["params"],
+                                     dtype=torch.float32, device=dev)
         for b in bests():
             kb = int(ws.k[b])
             if kb in forms:
@@ -513,6 +520,12 @@ def run_mine(args):
             C, deg = batch.centroids(b)
             form, tms = ctx.autotune_objective(X[:rows], C, deg, reps=3)
             forms[kb] = {"form": H.SEARCH_NAMES[form], "ms_per_call": tms, "rows": rows}
+            if cm_params is not None:
+                gform, gms, timed = ctx.autotune_objective_guided(X[:rows], C, cm_params, deg,
+                                                                  reps=3, margin=CM.MARGIN)
+                ctx.set_objective_form(wl.d, kb, form)
+                forms[kb]["guided"] = {"form": H.SEARCH_NAMES[gform], "forms_timed": timed,
+                                       "forms_built": len(tms), "ms_per_call": gms}
     torch.cuda.synchronize()
     if dist_ok:
         dist.barrier()
