@@ -264,3 +264,25 @@ def test_trained_network_gains_over_the_unguided_search(ctx):
     assert ev["guided_forms_timed"] < ev["exhaustive_forms_timed"]
     assert ev["guided_within_5pct"] >= ev["builtin_within_5pct"]
     assert ev["guided_within_5pct"] >= 0.75
+
+
+def test_guided_autotune_refuses_a_nonfinite_network(ctx):
+    X = torch.randn((4096, 16), device="cuda:0")
+    C = torch.randn((8, 16), device="cuda:0")
+    params = torch.full((NP,), float("nan"), device="cuda:0")
+    with pytest.raises(H.HPCError):
+        ctx.autotune_objective_guided(X, C, params)
+    # the form table is untouched
+    ctx.set_objective_form(16, 8, -1)
+
+
+def test_guided_autotune_single_form(ctx):
+    """d = 8: only the CUDA-core form is built, so exactly one is timed."""
+    X = torch.randn((1 << 16, 8), device="cuda:0")
+    C = torch.randn((12, 8), device="cuda:0")
+    params = _dev(_trained_or_init())
+    form, ms, timed = ctx.autotune_objective_guided(X, C, params, reps=1)
+    assert form == H.HPC_SEARCH_SIMT and timed == 1 and list(ms) == ["simt"]
+    feats, sup = H.hpc_costmodel_features(ctx, C)
+    assert sup == [1, 0, 0]
+    ctx.set_objective_form(8, 12, -1)
