@@ -334,7 +334,11 @@ __global__ void __launch_bounds__(TsCfg<D, NP>::THREADS, 1)
           if constexpr (IB > 0) {
 #pragma unroll
             for (int jj = 0; jj < 32; jj += 4) {
-              if (c * 32 + jj >= cs.kp) break;
+              // columns past the live ones carry HPC_DEAD norms and never
+              // win: scanning the whole chunk without a branch per group is
+              // faster except at d = 32 with 32 columns, whose registers
+              // are short
+              if (D == 32 && NP == 32 && c * 32 + jj >= cs.kp) break;
               const float4 cn = *reinterpret_cast<const float4 *>(cnv + c * 32 + jj);
               const int j = c * 32 + jj;
               // alternate groups of four go to two independent top-2 chains
