@@ -51,7 +51,7 @@ typedef enum hpc_status {
   HPC_ERR_TIMEOUT = -4,        /* a bounded device-side wait gave up */
   HPC_ERR_NONFINITE = -5,      /* NaN or infinity in the input rows */
   HPC_ERR_DEGENERATE_ALL = -6, /* no live centroid to assign to */
-  HPC_ERR_UNSUPPORTED = -7     /* a valid request this build cannot run */
+  HPC_ERR_UNSUPPORTED = -7     /* a valid request the library does not implement */
 } hpc_status;
 
 typedef enum hpc_precision {
