@@ -389,6 +389,17 @@ int hpc_costmodel_predict(hpc_ctx *ctx, const float *params, const float *feats,
 int hpc_costmodel_features(hpc_ctx *ctx, const float *C, const uint8_t *degenerate, int32_t d,
                            int32_t k, float *feats_out, int32_t *supported_out);
 
+/* The guided search's plan, on the host (no GPU needed): the built forms
+ * (supported[f] != 0) ranked by predicted ln time pred[f] (host float[3];
+ * ties to the lower form index) into order_out (host int[3]), and timed_out
+ * (host int[3]) = 1 for the ranked forms that are timed: the best-ranked one
+ * and each other one whose predicted time is within a factor (1 + margin) of
+ * the best-ranked one's.  Returns the number of built forms (entries of
+ * order_out past it are -1), or HPC_ERR_ARG for NULL arrays, a negative or
+ * NaN margin, or a non-finite prediction of a built form. */
+int hpc_costmodel_plan(const float *pred, const int32_t *supported, float margin,
+                       int32_t *order_out, int32_t *timed_out);
+
 /* hpc_autotune_objective guided by the network `params` (device): the forms
  * built for (d, k) are ranked by predicted time; the best-ranked one is
  * timed, and each other one only if its predicted time is within a factor

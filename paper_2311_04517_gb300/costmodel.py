@@ -143,11 +143,12 @@ def train(ctx, feats, targets, steps: int = 4000, lr: float = 3e-3, seed: int = 
 
 
 def guided_choice(pred, ms, supported, margin: float = MARGIN):
-    """The guided search on recorded times: (chosen form, forms timed)."""
-    order = sorted((f for f in range(3) if supported[f]), key=lambda f: (pred[f], f))
+    """The guided search on recorded times, with the library's own plan
+    (hpc_costmodel_plan): (chosen form, forms timed)."""
+    order, timed_mask = H.hpc_costmodel_plan(pred, supported, margin)
     best, timed = None, 0
-    for i, f in enumerate(order):
-        if i > 0 and math.exp(pred[f] - pred[order[0]]) > 1.0 + margin:
+    for f, t in zip(order, timed_mask):
+        if f < 0 or not t:
             continue
         timed += 1
         if best is None or ms[f] < ms[best]:

@@ -791,12 +791,13 @@ int check_autotune_args(hpc_ctx *c, const float *X, int64_t n, int32_t d, const 
   return HPC_OK;
 }
 
-// Times the forms in `order` (count entries; skip[i] true = not timed) and
+// Times the forms in `order` (count entries; those with timed_mask[i] == 0
+// are skipped when the mask is given) and
 // keeps the fastest; within 1% of it the built-in form stays, so that timing
 // noise does not move the choice from run to run.
 int autotune_forms(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float *C, int32_t k,
                    const uint8_t *degenerate, int32_t reps, const int *order, int count,
-                   const float *pred, float margin, int32_t *form_out, float *ms_out,
+                   const int32_t *timed_mask, int32_t *form_out, float *ms_out,
                    int32_t *timed_out) {
   cudaSetDevice(c->device);
   if (int rc = ensure_ws(c, obj_ws(c) + 512)) return rc;
@@ -811,9 +812,7 @@ int autotune_forms(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float
   int rc = HPC_OK;
   for (int i = 0; i < count && rc == HPC_OK; ++i) {
     const int form = order[i];
-    // guided: a form whose predicted time exceeds the best-ranked one's by
-    // more than the margin is not timed
-    if (pred && i > 0 && std::exp(pred[form] - pred[order[0]]) > 1.0 + (double)margin) continue;
+    if (timed_mask && !timed_mask[i]) continue;  // guided: predicted too slow
     float ms = 0.0f;
     rc = time_form(c, cv, f, X, n, d, C, k, degenerate, reps, form, e0, e1, &ms);
     if (rc != HPC_OK) break;
@@ -893,8 +892,31 @@ int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, con
   int order[3], count = 0;
   for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_TF32; ++form)
     if (form_supported(form, d, k, n)) order[count++] = form;
-  return autotune_forms(c, X, n, d, C, k, degenerate, reps, order, count, nullptr, 0.0f, form_out,
+  return autotune_forms(c, X, n, d, C, k, degenerate, reps, order, count, nullptr, form_out,
                         ms_out, nullptr);
+}
+
+int hpc_costmodel_plan(const float *pred, const int32_t *supported, float margin,
+                       int32_t *order_out, int32_t *timed_out) {
+  if (!pred || !supported || !order_out || !timed_out || !(margin >= 0.0f)) return HPC_ERR_ARG;
+  int order[3], count = 0;
+  for (int f = 0; f < 3; ++f) {
+    order_out[f] = -1;
+    timed_out[f] = 0;
+    if (!supported[f]) continue;
+    if (!std::isfinite(pred[f])) return HPC_ERR_ARG;
+    order[count++] = f;
+  }
+  // rank by predicted time, ties to the lower form index
+  std::stable_sort(order, order + count, [&](int a, int b) { return pred[a] < pred[b]; });
+  for (int i = 0; i < count; ++i) {
+    order_out[i] = order[i];
+    timed_out[i] =
+        i == 0 || std::exp((double)pred[order[i]] - (double)pred[order[0]]) <= 1.0 + (double)margin
+            ? 1
+            : 0;
+  }
+  return count;
 }
 
 int hpc_costmodel_features(hpc_ctx *c, const float *C, const uint8_t *degenerate, int32_t d,
@@ -981,9 +1003,8 @@ int hpc_autotune_objective_guided(hpc_ctx *c, const float *X, int64_t n, int32_t
   float feats[3 * HPC_CM_NFEAT];
   int32_t sup[3];
   if (int rc = hpc_costmodel_features(c, C, degenerate, d, k, feats, sup)) return rc;
-  int order[3], count = 0;
   for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_TF32; ++form)
-    if (sup[form] && form_supported(form, d, k, n)) order[count++] = form;
+    sup[form] = sup[form] && form_supported(form, d, k, n) ? 1 : 0;
   // predictions for the three forms, by the network on the device
   if (int rc = ensure_ws(c, 512 + obj_ws(c))) return rc;
   float *dfeat = reinterpret_cast<float *>(c->ws);
@@ -997,12 +1018,12 @@ int hpc_autotune_objective_guided(hpc_ctx *c, const float *X, int64_t n, int32_t
   e = cudaMemcpyAsync(pred, dpred, sizeof(pred), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cost-model prediction");
-  for (int q = 0; q < 3; ++q)
-    if (!std::isfinite(pred[q])) return fail(c, HPC_ERR_ARG, "cost model predicts a non-finite time");
-  // rank by predicted time, ties to the lower form index
-  std::stable_sort(order, order + count, [&](int a, int b) { return pred[a] < pred[b]; });
-  return autotune_forms(c, X, n, d, C, k, degenerate, reps, order, count, pred, margin, form_out,
-                        ms_out, timed_out);
+  int32_t order[3], timed[3];
+  const int count = hpc_costmodel_plan(pred, sup, margin, order, timed);
+  if (count < 0) return fail(c, HPC_ERR_ARG, "cost model predicts a non-finite time");
+  int ord[3] = {order[0], order[1], order[2]};
+  return autotune_forms(c, X, n, d, C, k, degenerate, reps, ord, count, timed, form_out, ms_out,
+                        timed_out);
 }
 
 // ---- checkpoint of a worker batch ----------------------------------------

@@ -111,6 +111,9 @@ def load() -> ctypes.CDLL:
         "hpc_costmodel_train": ([P, P, P, P, P, P, i32, i32, i32, ctypes.c_float, P],
                                 ctypes.c_int),
         "hpc_costmodel_predict": ([P, P, P, i32, P], ctypes.c_int),
+        "hpc_costmodel_plan": ([ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.c_float, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "hpc_costmodel_features": ([P, P, P, i32, i32, ctypes.POINTER(ctypes.c_float),
                                     ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "hpc_autotune_objective_guided": ([P, P, i64, i32, P, i32, P, i32, P, ctypes.c_float,
@@ -477,3 +480,17 @@ def hpc_costmodel_features(ctx: Context, C, degenerate=None):
                                               sup))
     return (torch.tensor(list(feats), dtype=torch.float32).view(3, HPC_CM_NFEAT),
             [int(x) for x in sup])
+
+
+def hpc_costmodel_plan(pred, supported, margin: float):
+    """The guided search's plan (host only): (forms ranked by predicted time,
+    1 where that form is timed), each of length 3 with -1 / 0 past the built
+    forms."""
+    p = (ctypes.c_float * 3)(*[float(x) for x in pred])
+    sp = (ctypes.c_int32 * 3)(*[int(x) for x in supported])
+    order = (ctypes.c_int32 * 3)()
+    timed = (ctypes.c_int32 * 3)()
+    rc = int(load().hpc_costmodel_plan(p, sp, float(margin), order, timed))
+    if rc < 0:
+        raise HPCError(rc, "hpc_costmodel_plan: bad arguments")
+    return list(order), list(timed)

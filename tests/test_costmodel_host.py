@@ -31,6 +31,26 @@ def test_guided_choice_times_within_margin_only():
     assert cm.guided_choice(pred, ms, sup, 1e30) == (1, 3)
 
 
+def test_library_plan():
+    """hpc_costmodel_plan (host code of the library, no GPU): ranking by
+    predicted time with ties to the lower form, unbuilt forms left out, the
+    margin rule, and refusals."""
+    from paper_2311_04517_gb300 import hpclust as H
+    lg = math.log
+    order, timed = H.hpc_costmodel_plan([lg(1.1), lg(1.0), lg(3.0)], [1, 1, 1], 0.25)
+    assert order == [1, 0, 2] and timed == [1, 1, 0]
+    order, timed = H.hpc_costmodel_plan([lg(1.1), lg(1.0), lg(3.0)], [1, 1, 1], 0.0)
+    assert order == [1, 0, 2] and timed == [1, 0, 0]
+    order, timed = H.hpc_costmodel_plan([0.0, 0.0, 0.0], [1, 0, 1], 0.0)
+    assert order == [0, 2, -1] and timed == [1, 1, 0]
+    order, timed = H.hpc_costmodel_plan([5.0, float("nan"), 1.0], [1, 0, 1], 1e30)
+    assert order == [2, 0, -1] and timed == [1, 1, 0]
+    for bad in (([float("nan"), 0.0, 0.0], [1, 1, 1], 0.1), ([0.0] * 3, [1, 1, 1], -0.5),
+                ([0.0] * 3, [1, 1, 1], float("nan")), ([float("inf"), 0.0, 0.0], [1, 0, 0], 0.1)):
+        with pytest.raises(H.HPCError):
+            H.hpc_costmodel_plan(*bad)
+
+
 def test_evaluate_counts():
     recs = [{"ms": [1.0, 2.0, -1.0], "supported": [1, 1, 0], "builtin": 1},
             {"ms": [3.0, 1.0, 1.02], "supported": [1, 1, 1], "builtin": 2}]
