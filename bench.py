@@ -5,9 +5,11 @@ One step = one HPClust round on the benchmark workload (sample draw,
 K-means++ reseeding of degenerate centroids, Lloyd to the Section 6.5 stop
 rule, incumbent test), replayed from a CUDA graph that recorded one round
 (--no-graph: issued call by call), followed by the full-data objective of
-the best incumbent of each sharing group (Eq. 1 over all n rows).  Distances counted per step: (Lloyd assignments) x
-s x k + n x k.  Default workload: "fp32" (n = 10^7 points in 16 dims, 25
-Gaussians, k = 25, one worker, s = 10^5).
+the best incumbent of each sharing group (Eq. 1 over all n rows).  Distances
+counted per step: (Lloyd assignments) x s x k + n x k.  Default workload:
+"large", the largest configuration that fits one GPU (n = 2 x 10^8 points in
+64 dims, 500 Gaussians with Zipf(1.1) weights, 51 GB; 128 workers with
+k = 500 and samples of 65,536 to 1,048,576 rows).
 
 Prints one JSON line (rank 0).  Arms:
   --impl mine       the CUDA library (default)
@@ -51,7 +53,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    p.add_argument("--workload", default="fp32")
+    p.add_argument("--workload", default="large")
+    p.add_argument("--workers", type=int, default=None,
+                   help="a smaller case of the workload: its first this many workers "
+                        "(for profiler captures; not a bench configuration)")
     p.add_argument("--strategy", choices=["competitive", "cooperative", "hybrid"],
                    default="competitive")
     p.add_argument("--n-competitive", type=int, default=None,
@@ -82,31 +87,51 @@ SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 ALU_PEAK_TFLOPS = 2.0 * SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
 
-def roofline_entry(kernel: str, simt: bool, n: int, d: int, k_mean: float, avg_ms: float,
-                   hbm_gbs: float, hbm_src: str, traffic):
-    """The objective kernel's roofline: HBM (4 n d bytes per launch) unless
-    the CUDA-core search's FMAs (2 n k d flops, k_mean the groups' mean k)
-    take longer at the arithmetic peak than the bytes at the HBM peak; the
-    tensor-core forms do their products on the tensor cores and stay
-    HBM-bound."""
-    bytes_ = float(n) * d * 4
-    flops = 2.0 * n * k_mean * d
+def roofline_bound(label: str, bytes_: float, flops: float, avg_ms: float, simt: bool,
+                   hbm_gbs: float, hbm_src: str, traffic, extra=None):
+    """Roofline of one kernel: HBM (bytes_ per launch) unless its
+    contraction's flops take longer at the arithmetic peak than the bytes at
+    the HBM peak.  CUDA-core kernels (simt) are held against the FP32 FMA
+    peak; the tensor-core kernels do their products on the tensor cores,
+    whose rate is far above both, and stay HBM-bound."""
     t_hbm = bytes_ / (hbm_gbs * 1e9)
     t_alu = flops / (ALU_PEAK_TFLOPS * 1e12)
-    entry = {"kernel": f"{kernel} (full-data objective, Eq. 1)", "traffic": traffic,
-             "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms}
+    entry = {"kernel": label, "traffic": traffic, "algorithmic_bytes_per_launch": bytes_,
+             "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms}
+    if extra:
+        entry.update(extra)
     if simt and t_alu > t_hbm:
         achieved = flops / (avg_ms / 1e3) / 1e12
         entry.update({"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
                       "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz, 2 flops per FMA",
-                      "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
-                      "algorithmic_flops_per_launch": flops})
+                      "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS})
     else:
         achieved = bytes_ / (avg_ms / 1e3) / 1e9
         entry.update({"bound": "hbm", "achieved": achieved, "peak": hbm_gbs,
                       "peak_source": f"{hbm_src} hbm_gbs", "unit": "GB/s",
                       "frac": achieved / hbm_gbs})
     return entry
+
+
+def roofline_entry(kernel: str, simt: bool, n: int, d: int, k_mean: float, avg_ms: float,
+                   hbm_gbs: float, hbm_src: str, traffic):
+    """The full-data objective's roofline: 4 n d bytes and 2 n k d flops per
+    launch (k_mean the groups' mean k)."""
+    return roofline_bound(f"{kernel} (full-data objective, Eq. 1)", float(n) * d * 4,
+                          2.0 * n * k_mean * d, avg_ms, simt, hbm_gbs, hbm_src, traffic)
+
+
+def lloyd_roofline(kernel: str, simt: bool, passes_rows_k, d: int, launches: int, avg_ms: float,
+                   hbm_gbs: float, hbm_src: str, traffic):
+    """The Lloyd launch's roofline: each assignment pass of worker w reads
+    its sample (4 s_w d bytes) and evaluates s_w k_w distances of 2 d flops
+    (the x.c contraction); passes_rows_k = [(passes, s_w, k_w)] summed over
+    the steps, divided over the launches."""
+    rows = sum(float(p) * float(s_) for p, s_, _ in passes_rows_k)
+    dists = sum(float(p) * float(s_) * float(k_) for p, s_, k_ in passes_rows_k)
+    return roofline_bound(f"{kernel} (Lloyd iterations, Algorithm 1)", 4.0 * d * rows / launches,
+                          2.0 * d * dists / launches, avg_ms, simt, hbm_gbs, hbm_src, traffic,
+                          {"launches_timed": launches})
 
 
 def peaks():
@@ -284,6 +309,8 @@ def bench_workload(args):
     wl = synth.workload(args.workload)
     if args.rows is not None:
         wl = replace(wl, n=int(args.rows))
+    if args.workers is not None:
+        wl = replace(wl, W=int(args.workers))
     return wl
 
 
@@ -301,19 +328,89 @@ def load_data(wl, device, seed):
     return synth.make_data(wl, device, seed)
 
 
+def host_prefix(wl, seed, rows):
+    """The first `rows` rows of the workload's data on the host, the same
+    rows the GPU arm uses: drawn on the CPU up to 2e8 floats, else with the
+    device generator the GPU arm uses (whole 4e6-row chunks, so the rows are
+    the full data's first rows), or on the CPU (other draws of the same
+    mixture) when no GPU is present."""
+    if wl.n * wl.d <= 200_000_000:
+        return synth.make_data(wl, "cpu", seed)[:rows].numpy(), "same rows as the GPU arm"
+    chunk = 4_000_000
+    n_gen = min(wl.n, -(-rows // chunk) * chunk)
+    if torch.cuda.is_available():
+        X = synth.make_data(wl, "cuda", seed, n=n_gen)
+        out = X[:rows].cpu().numpy()
+        del X
+        torch.cuda.empty_cache()
+        return out, "same rows as the GPU arm"
+    return synth.make_data(wl, "cpu", seed, n=n_gen)[:rows].numpy(), \
+        "other draws of the same mixture (no GPU for the device generator)"
+
+
+class BoundedOracle:
+    """A bounded sample of one step of a workload whose whole oracle step
+    would take minutes (each step of the large workload evaluates about
+    5e11 distances): per-component timing on the host cores.  Set-up
+    (untimed): eight seed-selected workers' samples, drawn by the oracle
+    from a row prefix of X, and K-means++ on the smallest of them (its time
+    is reported apart).  Step r: one Lloyd update (two assignment passes and
+    one update, Algorithm 1) on worker sel[r mod 8]'s sample from those
+    centroids, and the full-data objective (Eq. 1) over the next block of
+    `block` prefix rows."""
+
+    def __init__(self, orc, Xp, wl, ws, seed, block=100_000):
+        self.orc, self.Xp, self.block = orc, Xp, block
+        rng = np.random.default_rng(seed + 4321)
+        self.sel = sorted(int(w) for w in rng.choice(wl.W, min(8, wl.W), replace=False))
+        self.S = {w: orc.draw_sample(Xp, seed, w, 0, int(ws.s[w]))[0] for w in self.sel}
+        self.ws = ws
+        w0 = min(self.sel, key=lambda w: int(ws.s[w]))
+        k0 = int(ws.k[w0])
+        t0 = time.perf_counter()
+        kp = orc.kmeanspp(self.S[w0], np.zeros((k0, wl.d), np.float32), np.ones(k0, np.uint8),
+                          3, seed, w0, 0)
+        self.kpp_s = time.perf_counter() - t0
+        self.kpp_worker = (w0, int(ws.s[w0]), k0)
+        self.C, self.deg = kp["C"], kp["degenerate"]
+        self.row = 0
+
+    def step(self, r):
+        w = self.sel[r % len(self.sel)]
+        S = self.S[w]
+        k = self.C.shape[0]
+        self.orc.lloyd(S, self.C, self.deg, max_iter=1, rel_tol=0.0)
+        a = self.row
+        b = min(self.Xp.shape[0], a + self.block)
+        self.orc.objective(self.Xp[a:b], self.C, self.deg)
+        self.row = b if b < self.Xp.shape[0] else 0
+        return 2.0 * S.shape[0] * k + float(b - a) * k
+
+    def describe(self, steps, el):
+        w0, s0, k0 = self.kpp_worker
+        return (f"bounded sample: {steps} steps of one Lloyd update (2 assignment passes) on one "
+                f"of 8 seed-selected workers' samples (workers {self.sel}, s = "
+                f"{[int(self.ws.s[w]) for w in self.sel]}, drawn from a {self.Xp.shape[0]}-row "
+                f"prefix of X) + the objective over {self.block} rows, {el:.1f} s; K-means++ "
+                f"for worker {w0} (s = {s0}, k = {k0}) took {self.kpp_s:.1f} s apart")
+
+
+def oracle_step_work(wl, ws):
+    groups = group_members(ws)
+    return (sum((10 + 1) * int(s) * int(k) for s, k in zip(ws.s, ws.k)) +
+            wl.n * sum(int(ws.k[g[0]]) for g in groups)) * wl.d
+
+
 def cpu_oracle_rate(X_np, wl, ws, strategy, seed, budget_s=12.0, max_rounds=5):
     """Oracle distances/s on the host cores.  Small workloads: whole steps
     (round + objectives) from the all-degenerate start.  Workloads whose one
-    oracle step would take minutes: a bounded sample of the same work -- one
-    worker's round (K-means++ and Lloyd on its sample) and the objective over
-    a row subset -- with the distances it evaluated counted."""
+    oracle step would take minutes: steps of BoundedOracle until the
+    budget."""
     import oracle as orc
     orc.build()
     strat = {"cooperative": orc.COOPERATIVE, "hybrid": orc.HYBRID}.get(strategy, orc.COMPETITIVE)
     groups = group_members(ws)
-    step_work = sum((10 + 1) * int(s) * int(k) for s, k in zip(ws.s, ws.k)) + wl.n * sum(
-        int(ws.k[g[0]]) for g in groups)
-    if step_work * wl.d < 2e10:
+    if oracle_step_work(wl, ws) < 2e10:
         st = orc.RoundState(wl.d, ws.s, ws.k, ws.group)
         dist = 0.0
         t0 = time.perf_counter()
@@ -333,24 +430,15 @@ def cpu_oracle_rate(X_np, wl, ws, strategy, seed, budget_s=12.0, max_rounds=5):
         el = time.perf_counter() - t0
         return dist / el, el, (f"{rounds} oracle rounds from all-degenerate start "
                                f"(each: round + full-data objectives), {el:.1f} s"), orc.num_threads()
-    # bounded sample: worker 0's first round, then objective rows until the budget
-    w0 = 0
-    st = orc.RoundState(wl.d, ws.s[:1], ws.k[:1], ws.group[:1])
+    bo = BoundedOracle(orc, X_np, wl, ws, seed)
+    dist = 0.0
+    steps = 0
     t0 = time.perf_counter()
-    res = orc.round_(X_np, st, orc.COMPETITIVE, seed, 0)
-    dist = float((int(res["iters"][0]) + 1) * int(ws.s[w0]) * int(ws.k[w0]))
-    C, deg = st.centroids(0)
-    rows = 0
-    chunk = max(1000, int(2e9 / (wl.d * int(ws.k[w0]))))
-    while time.perf_counter() - t0 < budget_s and rows < X_np.shape[0]:
-        b = min(X_np.shape[0], rows + chunk)
-        orc.objective(X_np[rows:b], C, deg)
-        dist += float(b - rows) * int(ws.k[w0])
-        rows = b
+    while steps < 1 or time.perf_counter() - t0 < budget_s:
+        dist += bo.step(steps)
+        steps += 1
     el = time.perf_counter() - t0
-    return dist / el, el, (f"bounded sample: worker 0's first round (s={int(ws.s[w0])}, "
-                           f"k={int(ws.k[w0])}) + objective over {rows} rows, {el:.1f} s"), \
-        orc.num_threads()
+    return dist / el, el, bo.describe(steps, el), orc.num_threads()
 
 
 def run_reference(args):
@@ -361,21 +449,29 @@ def run_reference(args):
     orc.build()
     wl = bench_workload(args)
     ws = synth.worker_setup(wl)
-    X = load_data(wl, "cpu", wl.seed).numpy()
     strat = {"cooperative": orc.COOPERATIVE, "hybrid": orc.HYBRID}.get(args.strategy,
                                                                        orc.COMPETITIVE)
-    st = orc.RoundState(wl.d, ws.s, ws.k, ws.group)
     groups = group_members(ws)
+    if oracle_step_work(wl, ws) < 2e10:
+        X = load_data(wl, "cpu", wl.seed).numpy()
+        st = orc.RoundState(wl.d, ws.s, ws.k, ws.group)
 
-    def step(r):
-        res = orc.round_(X, st, strat, wl.seed, r, n_competitive=n_comp(args))
-        kb = []
-        for g in groups:
-            b = int(g[np.argmin(st.fhat[g])])
-            C, deg = st.centroids(b)
-            orc.objective(X, C, deg)
-            kb.append(int(ws.k[b]))
-        return dist_count(res["iters"], ws.s, ws.k, wl.n, kb)
+        def step(r):
+            res = orc.round_(X, st, strat, wl.seed, r, n_competitive=n_comp(args))
+            kb = []
+            for g in groups:
+                b = int(g[np.argmin(st.fhat[g])])
+                C, deg = st.centroids(b)
+                orc.objective(X, C, deg)
+                kb.append(int(ws.k[b]))
+            return dist_count(res["iters"], ws.s, ws.k, wl.n, kb)
+        sample = f"{args.steps} full oracle steps (round + full-data objective)"
+        bo = None
+    else:
+        n_host = min(wl.n, max(1, 200_000_000 // wl.d))
+        Xp, how = host_prefix(wl, wl.seed, n_host)
+        bo = BoundedOracle(orc, Xp, wl, ws, wl.seed)
+        step = bo.step
 
     for r in range(args.warmup):
         step(r)
@@ -385,14 +481,15 @@ def run_reference(args):
         dist += step(r)
     el = time.perf_counter() - t0
     v = dist / el
+    if bo is not None:
+        sample = bo.describe(args.steps, el) + f"; prefix rows: {how}"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el * 1e3 / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(wl, args.strategy, args),
             "cpu_baseline": {"kind": "oracle", "cores": orc.num_threads(),
-                             "sample": f"{args.steps} full oracle steps (round + full-data objective)",
-                             "value": v, "unit": UNIT},
+                             "sample": sample, "value": v, "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -499,6 +596,9 @@ def run_mine(args):
 
     graph = None
     graph_launches = 0
+    # CUDA events around every launch of a round (graph nodes when recorded
+    # in the graph): per-phase device times of each step
+    ctx.set_phase_timing(True)
     if args.graph:
         # one round recorded once; its round index lives on the device and
         # advances with every replay (rounds 0, 1, 2, ... as below)
@@ -518,6 +618,8 @@ def run_mine(args):
         else:
             H.hpc_round(ctx, X, batch, strategy, seed, r)
 
+    phase_log = []
+
     def step(r, log_row=None, ev=None):
         run_round(r)
         if log_row is not None:
@@ -525,6 +627,10 @@ def run_mine(args):
         bs = bests()
         if log_row is not None:
             best_log.append(bs)
+            if wl.W > 1:
+                # bests() has synchronised with the round: its phase times
+                # are ready (read before the next replay re-records them)
+                phase_log.append(ctx.phase_times())
         if ev is not None:
             ev[0].record()
         for gi, b in enumerate(bs):
@@ -583,6 +689,17 @@ def run_mine(args):
     st = ctx.sync_status()
     if st != 0:
         raise RuntimeError(f"device status {st}")
+    if not phase_log:
+        # one worker: no per-step synchronisation inside the timed region, so
+        # the phase times come from a few more steps after it
+        extra_iters = []
+        for i in range(min(K, 10)):
+            run_round(Wm + K + i)
+            phase_log.append(ctx.phase_times())
+            extra_iters.append(batch.iters.cpu().numpy().copy())
+        Wm_extra = min(K, 10)
+    else:
+        Wm_extra = 0
     ms = start.elapsed_time(end)
     obj_ms = [a.elapsed_time(b) for a, b in evs]
     iters = iters_log.cpu().numpy()
@@ -591,60 +708,71 @@ def run_mine(args):
     ms, dist_total = job_totals(ms, dist_total, dev)
     value = dist_total / (ms / 1e3)
 
-    # end to end: host-resident (pinned) data copied in every step, results read back
-    E = args.e2e_steps if args.e2e_steps is not None else max(3, min(K, 20))
-    X_host = X.cpu().pin_memory()
-    res_host = torch.empty(len(groups) * 8 + wl.W, dtype=torch.float64).pin_memory()
-    C_host = torch.empty_like(batch.C, device="cpu").pin_memory()
-    e_iters = torch.zeros((E, wl.W), dtype=torch.int32, device=dev)
-    e_best = []
-    r0 = Wm + K
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    # Each step copies X in row chunks; the objective of the current best
-    # incumbents runs on every chunk as soon as it has arrived (it is a sum
-    # over rows), behind the copy; the round then runs on the complete X.
-    # Work per step: one full copy, one full objective per group, one round.
-    nck = 8
-    rows = (wl.n + nck - 1) // nck
-    rows = (rows + 3) // 4 * 4                      # 16-byte aligned chunk starts
-    f_chunks = torch.zeros((len(groups), nck), dtype=torch.float64, device=dev)
-    main = torch.cuda.current_stream(dev)
-    copy_stream = torch.cuda.Stream(dev)
-    arrived = [torch.cuda.Event() for _ in range(nck)]
-    for i in range(E):
-        bs = bests()
-        e_best.append(bs)
-        copy_stream.wait_stream(main)               # X is free once the last step is done
-        with torch.cuda.stream(copy_stream):
+    # end to end: host-resident (pinned) data copied in every step, results
+    # read back; about 30 s of steps at most (a step copies all of X)
+    copy_s = wl.n * wl.d * 4 / 200e9
+    E = args.e2e_steps if args.e2e_steps is not None else max(
+        3, min(K, 20, int(30.0 / (ms / K / 1e3 + copy_s))))
+    e2e = None
+    if E > 0:
+        X_host = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
+        X_host.copy_(X)
+        res_host = torch.empty(len(groups) * 8 + wl.W, dtype=torch.float64).pin_memory()
+        C_host = torch.empty_like(batch.C, device="cpu").pin_memory()
+        e_iters = torch.zeros((E, wl.W), dtype=torch.int32, device=dev)
+        e_best = []
+        r0 = Wm + K + Wm_extra
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        # Each step copies X in row chunks; the objective of the current best
+        # incumbents runs on every chunk as soon as it has arrived (it is a sum
+        # over rows), behind the copy; the round then runs on the complete X.
+        # Work per step: one full copy, one full objective per group, one round.
+        nck = 8
+        rows = (wl.n + nck - 1) // nck
+        rows = (rows + 3) // 4 * 4                      # 16-byte aligned chunk starts
+        f_chunks = torch.zeros((len(groups), nck), dtype=torch.float64, device=dev)
+        main = torch.cuda.current_stream(dev)
+        copy_stream = torch.cuda.Stream(dev)
+        arrived = [torch.cuda.Event() for _ in range(nck)]
+        for i in range(E):
+            bs = bests()
+            e_best.append(bs)
+            copy_stream.wait_stream(main)               # X is free once the last step is done
+            with torch.cuda.stream(copy_stream):
+                for c in range(nck):
+                    a, b_ = c * rows, min(wl.n, (c + 1) * rows)
+                    if a < b_:
+                        X[a:b_].copy_(X_host[a:b_], non_blocking=True)
+                    arrived[c].record(copy_stream)
             for c in range(nck):
                 a, b_ = c * rows, min(wl.n, (c + 1) * rows)
-                if a < b_:
-                    X[a:b_].copy_(X_host[a:b_], non_blocking=True)
-                arrived[c].record(copy_stream)
-        for c in range(nck):
-            a, b_ = c * rows, min(wl.n, (c + 1) * rows)
-            main.wait_event(arrived[c])
-            if a >= b_:
-                continue
-            for gi, b in enumerate(bs):
-                C, deg = batch.centroids(b)
-                H.hpc_objective(ctx, X[a:b_], C, deg, f_out=f_chunks[gi, c:c + 1])
-        run_round(r0 + i)
-        e_iters[i].copy_(batch.iters, non_blocking=True)
-        # per-chunk objectives are read back and added on the host
-        res_host[:len(groups) * nck].copy_(f_chunks.view(-1), non_blocking=True)
-        res_host[len(groups) * nck:].copy_(batch.fhat, non_blocking=True)
-        C_host.copy_(batch.C, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    e_ms = e0.elapsed_time(e1)
-    ei = e_iters.cpu().numpy()
-    e_dist = sum(dist_count(ei[i], ws.s, ws.k, wl.n, [int(ws.k[b]) for b in e_best[i]])
-                 for i in range(E))
-    e_ms, e_dist = job_totals(e_ms, e_dist, dev)
-    e_value = e_dist / (e_ms / 1e3)
+                main.wait_event(arrived[c])
+                if a >= b_:
+                    continue
+                for gi, b in enumerate(bs):
+                    C, deg = batch.centroids(b)
+                    H.hpc_objective(ctx, X[a:b_], C, deg, f_out=f_chunks[gi, c:c + 1])
+            run_round(r0 + i)
+            e_iters[i].copy_(batch.iters, non_blocking=True)
+            # per-chunk objectives are read back and added on the host
+            res_host[:len(groups) * nck].copy_(f_chunks.view(-1), non_blocking=True)
+            res_host[len(groups) * nck:].copy_(batch.fhat, non_blocking=True)
+            C_host.copy_(batch.C, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        ei = e_iters.cpu().numpy()
+        e_dist = sum(dist_count(ei[i], ws.s, ws.k, wl.n, [int(ws.k[b]) for b in e_best[i]])
+                     for i in range(E))
+        e_ms, e_dist = job_totals(e_ms, e_dist, dev)
+        e_value = e_dist / (e_ms / 1e3)
+        e2e = {"value": e_value, "unit": UNIT,
+               "h2d_bytes_per_step": int(X_host.numel() * 4),
+               "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4 +
+                                         (wl.W * 8 if wl.W > 1 else 0))}
+        del X_host
 
     hbm, src = peaks()
     obj_avg_ms = float(np.mean(obj_ms)) / len(groups)  # one launch per group per step
@@ -655,6 +783,31 @@ def run_mine(args):
                   H.HPC_SEARCH_SPLIT_TF32: "tcs_objective_kernel",
                   H.HPC_SEARCH_TF32: "tc_objective_kernel" if kb0 <= 128
                   else "tw_objective_kernel"}[form0]
+    obj_entry = roofline_entry(obj_kernel, form0 == H.HPC_SEARCH_SIMT, wl.n, wl.d, k_mean,
+                               obj_avg_ms, hbm, src,
+                               profiled_traffic("objective", wl.name, obj_kernel))
+    # the Lloyd launches of the timed steps (their phase times: one launch
+    # per 128 workers per step)
+    chunks = (wl.W + 127) // 128
+    lloyd_ms = [p["lloyd"] for p in phase_log]
+    lsched = ctx.lloyd_schedule(int(max(ws.s)), wl.d, int(max(ws.k)))
+    lloyd_kernel_name = "lloyd_kernel" if lsched["form"] == "simt" else "tcl_lloyd_kernel"
+    if Wm_extra:
+        it_rows = [(int(it[w]) + 1, int(ws.s[w]), int(ws.k[w]))
+                   for it in extra_iters for w in range(wl.W)]
+    else:
+        it_rows = [(int(iters[i][w]) + 1, int(ws.s[w]), int(ws.k[w]))
+                   for i in range(K) for w in range(wl.W)]
+    lloyd_entry = lloyd_roofline(lloyd_kernel_name, lsched["form"] == "simt", it_rows, wl.d,
+                                 len(lloyd_ms) * chunks,
+                                 float(np.sum(lloyd_ms)) / (len(lloyd_ms) * chunks), hbm, src,
+                                 profiled_traffic("lloyd", wl.name, lloyd_kernel_name))
+    phase_ms = {k: float(np.mean([p[k] for p in phase_log])) for k in phase_log[0]}
+    phase_ms["objective"] = float(np.mean(obj_ms))
+    # the roofline line names the kernel that takes the larger share of a step
+    lloyd_step_ms = phase_ms["lloyd"]
+    dominant, other = ((lloyd_entry, obj_entry) if lloyd_step_ms > phase_ms["objective"]
+                       else (obj_entry, lloyd_entry))
     tto = None
     R = args.tto_rounds if args.tto_rounds is not None else min(wl.rounds, 10)
     if R > 0 and world == 1:
@@ -665,13 +818,11 @@ def run_mine(args):
             "config": workload_config(wl, args.strategy, args),
             "round_issue": ("one round recorded in a CUDA graph, replayed every step" if args.graph
                             else "calls issued one by one"),
-            "roofline": roofline_entry(obj_kernel, form0 == H.HPC_SEARCH_SIMT, wl.n, wl.d,
-                                       k_mean, obj_avg_ms, hbm, src,
-                                       profiled_traffic("objective", wl.name, obj_kernel)),
-            "e2e": {"value": e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": int(X_host.numel() * 4),
-                    "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4 +
-                                              (wl.W * 8 if wl.W > 1 else 0))},
+            "roofline": dominant,
+            "roofline_other": other,
+            "phase_ms_per_step": phase_ms,
+            "lloyd_schedule": lsched,
+            "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(t0, t1),
             "lloyd_iters_mean": float(iters.mean())}

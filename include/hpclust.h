@@ -145,6 +145,38 @@ int hpc_autotune_objective(hpc_ctx *ctx, const float *X, int64_t n, int32_t d, c
                            int32_t k, const uint8_t *degenerate, int32_t reps,
                            int32_t *form_out, float *ms_out);
 
+/* The schedule hpc_lloyd would launch for one sample of s rows (s x d, k
+ * centroids), for reporting and tests (the paper has no counterpart: this
+ * is a launch configuration, not a step of the method).  out (host,
+ * nout int32 entries, up to 5 written):
+ *   [0] blocks of the persistent launch
+ *   [1] 1 if each block sums its rows into k x d fixed-point sums in shared
+ *       memory, 0 if it adds them straight into the global sums (k x d x 8
+ *       bytes above what a block can hold)
+ *   [2] 1 if each block keeps its rows in shared memory between the
+ *       assignment and the accumulation
+ *   [3] dynamic shared memory per block (bytes)
+ *   [4] search form of the assignment (hpc_search)
+ * Errors: HPC_ERR_ARG (sizes, NULL out), HPC_ERR_UNSUPPORTED (no kernel for
+ * the shape). */
+int hpc_lloyd_schedule(hpc_ctx *ctx, int64_t s, int32_t d, int32_t k, int32_t *out,
+                       int32_t nout);
+
+/* Per-phase timing of rounds (the paper has no counterpart: measurement
+ * only).  With timing on, every round enqueued on the context (hpc_round,
+ * hpc_round_enqueue) records CUDA events on the context's stream around
+ * each of its launches; a round enqueued while a stream is captured records
+ * them as nodes of the graph, so each replay of that graph times itself
+ * again.  hpc_phase_times waits for the latest timed round (the last one
+ * enqueued, or the last replay of a graph recorded with timing on) and
+ * writes the milliseconds it spent in each phase to ms_out (host, 3 floats:
+ * sampling with base selection, K-means++, Lloyd with the incumbent rule).
+ * Rounds of more than 31 launch chunks (3968 workers) are not timed.
+ * Errors: HPC_ERR_ARG (bad flag, NULL ms_out, no timed round yet),
+ * HPC_ERR_CUDA. */
+int hpc_set_phase_timing(hpc_ctx *ctx, int32_t on);
+int hpc_phase_times(hpc_ctx *ctx, float *ms_out);
+
 /* ---- the hot path ------------------------------------------------------ */
 
 /* Random sample of size s from X (Section 3: a worker starts every round by
@@ -321,9 +353,14 @@ int hpc_batch_load(hpc_ctx *ctx, const hpc_batch *batch, int32_t d, const void *
  * that receives HPC_OK or the device-side error (HPC_ERR_NONFINITE,
  * HPC_ERR_DEGENERATE_ALL) once `stream` (a cudaStream_t) has run the call.
  * Every call on a device shares that array, so calls that may overlap on
- * the GPU race: serialise them.  The first call on each device looks up the
- * array's address with that device current; make it before any stream
- * capture.  Errors: HPC_ERR_ARG for bad sizes or unaligned pointers,
+ * the GPU race: serialise them.  A call made while `stream` is not being
+ * captured looks the array's address up with the current device; a call
+ * made during a stream capture reuses the address the latest uncaptured call
+ * on that device found (HPC_ERR_ARG if there was none), so make one
+ * uncaptured call first, with the same padded dimension (the next of 2, 4,
+ * 8, 16, 32, 64, 128) and the same k class (k <= 32 or k > 32) as the
+ * captured call: it also loads the kernel and sets its shared-memory limit.
+ * Errors: HPC_ERR_ARG for bad sizes or unaligned pointers,
  * HPC_ERR_UNSUPPORTED if the centroid block does not fit in shared memory,
  * HPC_ERR_CUDA if a launch fails. */
 int hpc_objective_noalloc(const float *X, int64_t n, int32_t d, const float *C, int32_t k,

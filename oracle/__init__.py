@@ -124,6 +124,19 @@ def draw_sample(X, seed: int, worker: int, round_: int, s: int):
     return S, idx
 
 
+def sample_indices(n: int, seed: int, worker: int, round_: int, s: int) -> np.ndarray:
+    """The row indices draw_sample takes (Section 3's random sample, with
+    replacement): index i is floor(r_i * n / 2^64) with r_i draw i of stream
+    (seed, worker, round, tag 0).  For data too large to pass whole to
+    draw_sample; the rows themselves are then X[indices]."""
+    out = np.empty(s, dtype=np.int64)
+    L = lib()
+    for i in range(s):
+        r = int(L.orc_draw(seed, worker, round_, TAG_SAMPLE, i))
+        out[i] = (r * int(n)) >> 64
+    return out
+
+
 def dist32(x, c) -> float:
     x = _f32(x)
     c = _f32(c)

@@ -18,6 +18,8 @@
 // least one block per SM, so at least this many tasks fit).
 #define HPC_ROUND_CHUNK 128
 #define HPC_MAX_WORKERS 65535
+// events of one timed round: rounds of up to 31 launch chunks are timed
+#define HPC_TIMING_EVENTS 64
 
 struct hpc_round_plan;
 
@@ -49,6 +51,14 @@ struct hpc_ctx {
   void *plan_mem;
   size_t plan_bytes;
   uint32_t *plan_round;  // device round counter, advanced by every enqueued round
+  // phase timing of rounds (hpc_set_phase_timing): an event before the
+  // round's first launch and one after each launch; tev_kind[i] is the
+  // phase (0 sampling, 1 K-means++, 2 Lloyd) of the launch that ends at
+  // event i (i >= 1)
+  int timing;
+  cudaEvent_t tev[HPC_TIMING_EVENTS];
+  int tev_kind[HPC_TIMING_EVENTS];
+  int tev_n;
   char err[256];
 };
 
@@ -546,7 +556,28 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
 // allocation (a stream capture can record it).  The round index is `round`,
 // or *round_dev when that is given (a prepared round, whose last Lloyd
 // launch then advances it).
+// Records timing event i of a round on the context's stream; inside a
+// stream capture the record becomes a node of the graph, so that every
+// replay takes the time again.
+static int timing_mark(hpc_ctx *c, int i, int kind) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
+  if (e == cudaSuccess)
+    e = cs == cudaStreamCaptureStatusNone
+            ? cudaEventRecord(c->tev[i], c->stream)
+            : cudaEventRecordWithFlags(c->tev[i], c->stream, cudaEventRecordExternal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "timing event");
+  c->tev_kind[i] = kind;
+  c->tev_n = i + 1;
+  return HPC_OK;
+}
+
 static int round_enqueue(hpc_ctx *c, const hpc_round_plan &p, uint32_t *round_dev, uint32_t round) {
+  const bool timed = c->timing && 2 + 2 * (int)p.kl.size() <= HPC_TIMING_EVENTS;
+  int ev = 0;
+  c->tev_n = 0;
+  if (timed)
+    if (int rc = timing_mark(c, ev++, -1)) return rc;
   cudaError_t e = cudaMemsetAsync(p.hdr, 0, (size_t)p.W * sizeof(TaskHeader), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "round set-up");
   hpc_base_args base{};
@@ -567,14 +598,20 @@ static int round_enqueue(hpc_ctx *c, const hpc_round_plan &p, uint32_t *round_de
                                        p.smax, base))
     return plan_fail(c, rc, "sample launch");
   c->launches += 1;
+  if (timed)
+    if (int rc = timing_mark(c, ev++, 0)) return rc;
   for (size_t ch = 0; ch < p.kl.size(); ++ch) {
     KppLaunch kh = p.kl[ch];
     kh.round = round;
     kh.round_dev = round_dev;
     if (int rc = hpc_kmeanspp_run(c->L, kh)) return plan_fail(c, rc, "kmeanspp launch");
+    if (timed)
+      if (int rc = timing_mark(c, ev++, 1)) return rc;
     LloydLaunch lh = p.ll[ch];
     lh.round_advance = ch + 1 == p.kl.size() ? round_dev : nullptr;
     if (int rc = hpc_lloyd_run(c->L, lh)) return plan_fail(c, rc, "lloyd launch");
+    if (timed)
+      if (int rc = timing_mark(c, ev++, 2)) return rc;
     c->launches += 2;
   }
   return HPC_OK;
@@ -623,6 +660,8 @@ int hpc_destroy(hpc_ctx *c) {
     if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
   }
   if (c->plan_mem) cudaFree(c->plan_mem);
+  for (int i = 0; i < HPC_TIMING_EVENTS; ++i)
+    if (c->tev[i]) cudaEventDestroy(c->tev[i]);
   delete c->plan;
   delete c;
   return HPC_OK;
@@ -753,6 +792,59 @@ int hpc_set_objective_form(hpc_ctx *c, int32_t d, int32_t k, int32_t form) {
 int hpc_objective_form(hpc_ctx *c, int64_t n, int32_t d, int32_t k) {
   if (!c || d < 1 || d > 128 || k < 1 || n < 0) return HPC_ERR_ARG;
   return objective_form(c, d, k, n);
+}
+
+int hpc_lloyd_schedule(hpc_ctx *c, int64_t s, int32_t d, int32_t k, int32_t *out, int32_t nout) {
+  if (!c) return HPC_ERR_ARG;
+  if (int rc = check_dims(c, d)) return rc;
+  if (s < 1 || k < 1 || !out || nout < 1) return fail(c, HPC_ERR_ARG, "bad sizes");
+  cudaSetDevice(c->device);
+  hpc_lloyd_task t{};
+  t.s = s;
+  t.k = k;
+  LloydLaunch h{};
+  h.W = 1;
+  h.tasks = &t;
+  h.d = d;
+  h.kmax = k;
+  h.max_blocks = c->grid_bound;
+  h.task_blocks = c->grid_bound;
+  if (int rc = hpc_lloyd_plan(c->L, h)) return plan_fail(c, rc, "lloyd: unsupported shape");
+  const int32_t v[5] = {(int32_t)h.grid, h.smem_sums, h.xstage, (int32_t)h.smem, 0};
+  for (int i = 0; i < nout && i < 5; ++i) out[i] = v[i];
+  return HPC_OK;
+}
+
+int hpc_set_phase_timing(hpc_ctx *c, int32_t on) {
+  if (!c || on < 0 || on > 1) return HPC_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (on && !c->tev[0]) {
+    for (int i = 0; i < HPC_TIMING_EVENTS; ++i) {
+      cudaError_t e = cudaEventCreate(&c->tev[i]);
+      if (e != cudaSuccess) return cuda_fail(c, e, "timing events");
+    }
+  }
+  c->timing = on;
+  c->tev_n = 0;
+  return HPC_OK;
+}
+
+int hpc_phase_times(hpc_ctx *c, float *ms_out) {
+  if (!c || !ms_out) return HPC_ERR_ARG;
+  if (c->tev_n < 2) return fail(c, HPC_ERR_ARG, "no timed round");
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaEventSynchronize(c->tev[c->tev_n - 1]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "timing wait");
+  float acc[3] = {0.0f, 0.0f, 0.0f};
+  for (int i = 1; i < c->tev_n; ++i) {
+    float ms = 0.0f;
+    if ((e = cudaEventElapsedTime(&ms, c->tev[i - 1], c->tev[i])) != cudaSuccess)
+      return cuda_fail(c, e, "timing read");
+    const int kind = c->tev_kind[i];
+    if (kind >= 0 && kind < 3) acc[kind] += ms;
+  }
+  for (int i = 0; i < 3; ++i) ms_out[i] = acc[i];
+  return HPC_OK;
 }
 
 namespace {

@@ -16,9 +16,15 @@
 //  - every call on a device uses the same array and leaves its last contents
 //    there, so calls that may overlap on the GPU (different streams, or
 //    several host threads) race and give wrong results: serialise them;
-//  - the first call on each device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture starts.
+//  - a call made while its stream is not being captured looks the array's
+//    device address up again (cudaGetSymbolAddress, with the call's device
+//    current), so a context reset between calls is harmless; a call made
+//    while its stream is being captured into a graph reuses the address the
+//    latest uncaptured call on that device found, so make one uncaptured
+//    call on each device first, with the same padded dimension and the same
+//    k class (k <= 32 or k > 32) as the captured call: that first call also
+//    loads the kernel and sets its shared-memory limit, neither of which
+//    should happen inside a capture.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,16 +45,25 @@ static __device__ __align__(256) double g_noalloc_scratch[HPC_NOALLOC_MAX_BLOCKS
 std::mutex g_noalloc_mutex;
 void *g_noalloc_ptr[HPC_NOALLOC_MAX_DEVICES];
 
-// Device address of the array on the current device (looked up once).
-int noalloc_scratch(int device, void **out) {
+// Device address of the array on the current device: looked up afresh when
+// `stream` is not being captured, else the one the latest uncaptured call
+// found (a capture must not trigger the lookup).
+int noalloc_scratch(int device, cudaStream_t stream, void **out) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return HPC_ERR_CUDA;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[device]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return HPC_ERR_CUDA;
     }
     g_noalloc_ptr[device] = p;
+  } else if (!g_noalloc_ptr[device]) {
+    return HPC_ERR_ARG;  // no uncaptured call on this device yet
   }
   *out = g_noalloc_ptr[device];
   return HPC_OK;
@@ -68,7 +83,7 @@ extern "C" int hpc_objective_noalloc(const float *X, int64_t n, int32_t d, const
     return HPC_ERR_CUDA;
   }
   void *scratch = nullptr;
-  if (int rc = noalloc_scratch(device, &scratch)) return rc;
+  if (int rc = noalloc_scratch(device, (cudaStream_t)stream, &scratch)) return rc;
   hpc_launch L;
   L.stream = (cudaStream_t)stream;
   if (cudaDeviceGetAttribute(&L.num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||

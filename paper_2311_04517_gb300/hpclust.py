@@ -104,6 +104,10 @@ def load() -> ctypes.CDLL:
         "hpc_set_objective_form": ([P, i32, i32, i32], ctypes.c_int),
         "hpc_peak_probe": ([i32, i32, P, ctypes.POINTER(f64), ctypes.POINTER(f64)], ctypes.c_int),
         "hpc_objective_form": ([P, i64, i32, i32], ctypes.c_int),
+        "hpc_lloyd_schedule": ([P, i64, i32, i32, ctypes.POINTER(ctypes.c_int32), i32],
+                               ctypes.c_int),
+        "hpc_set_phase_timing": ([P, i32], ctypes.c_int),
+        "hpc_phase_times": ([P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "hpc_autotune_objective": ([P, P, i64, i32, P, i32, P, i32,
                                     ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
@@ -210,6 +214,24 @@ class Context:
         if rc < 0:
             self._check(rc)
         return rc
+
+    def lloyd_schedule(self, s: int, d: int, k: int) -> dict:
+        """The launch hpc_lloyd would make for one sample of s rows (see
+        hpc_lloyd_schedule in include/hpclust.h)."""
+        out = (ctypes.c_int32 * 5)()
+        self._check(self.lib.hpc_lloyd_schedule(self.h, int(s), int(d), int(k), out, 5))
+        return {"blocks": int(out[0]), "smem_sums": bool(out[1]), "xstage": bool(out[2]),
+                "smem_bytes": int(out[3]), "form": SEARCH_NAMES.get(int(out[4]), int(out[4]))}
+
+    def set_phase_timing(self, on: bool):
+        """Record CUDA events around every launch of later rounds."""
+        self._check(self.lib.hpc_set_phase_timing(self.h, int(bool(on))))
+
+    def phase_times(self) -> dict:
+        """Milliseconds of the latest timed round per phase."""
+        ms = (ctypes.c_float * 3)()
+        self._check(self.lib.hpc_phase_times(self.h, ms))
+        return {"sample": float(ms[0]), "kmeanspp": float(ms[1]), "lloyd": float(ms[2])}
 
     def autotune_objective(self, X, C, degenerate=None, reps: int = 5):
         """Times every search form built for C's shape on rows X, keeps the

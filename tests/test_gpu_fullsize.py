@@ -13,8 +13,8 @@ properties that hold at any size check the rest:
     of all rows to their labelled centroids, within 1e-6 relative (the bound
     of the FP32 direct-form distances it adds);
   * a sampled worker's round (sample draw, K-means++, Lloyd) matches the
-    oracle's replay of that worker: objective within 1e-6, centroids within
-    1e-6 of the largest coordinate.
+    oracle's replay of that worker: objective within 1e-6, centroids per
+    coordinate within 1e-6 relative plus 1e-9 of the largest coordinate.
 """
 import numpy as np
 import pytest
@@ -125,6 +125,60 @@ def test_large_workload_objective(ctx, form):
     torch.cuda.empty_cache()
 
 
+def assert_centroids(Cg, Co, what=""):
+    Co64 = np.asarray(Co, np.float64)
+    scale = max(1.0, float(np.abs(Co64).max()))
+    tol = RTOL * np.abs(Co64) + 1e-9 * scale
+    bad = np.abs(np.asarray(Cg, np.float64) - Co64) > tol
+    assert not bad.any(), f"{what}: {int(bad.sum())} centroid coordinates off"
+
+
+def replay_worker(ctx, X, wl, ws, batch, w, seed, rnd, f_new, iters, host_X=None):
+    """The oracle's replay of worker w's round from the all-degenerate start:
+    its sample (indices from the oracle's Philox stream, rows gathered from
+    X), K-means++ and Lloyd; compared with the GPU round's results."""
+    s, k = int(ws.s[w]), int(ws.k[w])
+    if host_X is not None:
+        S, _ = orc.draw_sample(host_X, seed, w, rnd, s)
+    else:
+        idx = orc.sample_indices(X.shape[0], seed, w, rnd, s)
+        S = X[torch.from_numpy(idx).cuda()].cpu().numpy()
+    kp = orc.kmeanspp(S, np.zeros((k, wl.d), np.float32), np.ones(k, np.uint8), 3, seed, w, rnd)
+    lo = orc.lloyd(S, kp["C"], kp["degenerate"])
+    assert f_new[w] == pytest.approx(lo["f"], rel=RTOL), f"worker {w}"
+    if int(iters[w]) == lo["iters"]:
+        C, deg = batch.centroids(w)
+        np.testing.assert_array_equal(deg.cpu().numpy(), lo["degenerate"])
+        assert_centroids(C.cpu().numpy(), lo["C"], f"worker {w}")
+    return lo
+
+
+def test_large_workload_round_sampled_workers(ctx):
+    # one full-size round of the large workload: 128 workers, k = 500,
+    # d = 64, samples of 65,536 to 1,048,576 rows drawn from 2e8 rows; the
+    # Lloyd sums of k x d = 32,000 coordinates exceed a block's shared memory,
+    # so every block adds into the global fixed-point sums.  The workers with
+    # the smallest and the largest sample are replayed by the oracle from the
+    # same all-degenerate start.
+    wl = synth.WORKLOADS["large"]
+    ws = synth.worker_setup(wl)
+    assert not ctx.lloyd_schedule(int(ws.s.max()), wl.d, 500)["smem_sums"]
+    X = synth.make_data(wl, "cuda")               # 2e8 x 64 float32, 51 GB
+    batch = H.Batch(wl.d, ws.s, ws.k, ws.group)
+    seed, rnd = wl.seed, 0
+    H.hpc_round(ctx, X, batch, H.HPC_COMPETITIVE, seed, rnd)
+    ctx.check_status()
+    f_new = batch.f_new.cpu().numpy()
+    iters = batch.iters.cpu().numpy()
+    assert np.isfinite(f_new).all() and (iters >= 1).all()
+    # every worker's incumbent was replaced (the start is +inf)
+    assert batch.accepted.cpu().numpy().all()
+    for w in (int(np.argmin(ws.s)), int(np.argmax(ws.s))):
+        replay_worker(ctx, X, wl, ws, batch, w, seed, rnd, f_new, iters)
+    del X
+    torch.cuda.empty_cache()
+
+
 def test_batching_workload_round_sampled_workers(ctx):
     # one full-size round of all 64 workers (one batched launch per phase);
     # three workers (k = 10, 25, 50) are replayed by the oracle from the
@@ -139,19 +193,9 @@ def test_batching_workload_round_sampled_workers(ctx):
     f_new = batch.f_new.cpu().numpy()
     iters = batch.iters.cpu().numpy()
     Xh = X.cpu().numpy()
-    for kk in (10, 25, 50):
+    for kk in (10, 25, 50, 100):
         cand = [w for w in range(wl.W) if int(ws.k[w]) == kk]
         w = min(cand, key=lambda v: int(ws.s[v]))        # the smallest sample of that k
-        s, k = int(ws.s[w]), int(ws.k[w])
-        S, _ = orc.draw_sample(Xh, seed, w, rnd, s)
-        kp = orc.kmeanspp(S, np.zeros((k, wl.d), np.float32), np.ones(k, np.uint8), 3, seed, w,
-                          rnd)
-        lo = orc.lloyd(S, kp["C"], kp["degenerate"])
-        assert f_new[w] == pytest.approx(lo["f"], rel=RTOL), f"worker {w}"
-        if int(iters[w]) == lo["iters"]:
-            C, deg = batch.centroids(w)
-            np.testing.assert_array_equal(deg.cpu().numpy(), lo["degenerate"])
-            scale = max(1.0, float(np.abs(lo["C"]).max()))
-            assert float(np.abs(C.cpu().numpy().astype(np.float64) - lo["C"]).max()) <= RTOL * scale
+        replay_worker(ctx, X, wl, ws, batch, w, seed, rnd, f_new, iters, host_X=Xh)
     del X
     torch.cuda.empty_cache()

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as orc
 from paper_2311_04517_gb300 import hpclust as H
 
 pytestmark = pytest.mark.gpu
@@ -51,11 +52,31 @@ def test_prepared_round_matches_hpc_round(ctx, strategy):
         same(ref, prep)
 
 
+def assert_matches_oracle(batch, st, res):
+    """The batch's state after a round against the oracle's (Algorithms 3-5):
+    flags, iteration counts and decisions equal, objectives within 1e-6,
+    centroids per coordinate within 1e-6 relative plus 1e-9 of the largest."""
+    d = batch.d
+    for w in range(batch.W):
+        C, deg = batch.centroids(w)
+        Co, dego = st.centroids(w)
+        np.testing.assert_array_equal(deg.cpu().numpy(), dego)
+        Co64 = Co.astype(np.float64)
+        tol = 1e-6 * np.abs(Co64) + 1e-9 * max(1.0, float(np.abs(Co64).max()))
+        assert (np.abs(C.cpu().numpy().astype(np.float64) - Co64) <= tol).all(), f"worker {w}"
+    np.testing.assert_array_equal(batch.iters.cpu().numpy(), res["iters"])
+    np.testing.assert_array_equal(batch.accepted.cpu().numpy().astype(bool), res["accepted"])
+    np.testing.assert_allclose(batch.f_new.cpu().numpy(), res["f_new"], rtol=1e-6)
+    np.testing.assert_allclose(batch.fhat.cpu().numpy(), st.fhat, rtol=1e-6)
+
+
 @pytest.mark.parametrize("strategy", [H.HPC_COOPERATIVE, H.HPC_HYBRID])
 def test_prepared_round_replays_from_a_cuda_graph(ctx, strategy):
     X = mixture(40000, 16, 10, 52, sd=1.3)
+    Xh = X.cpu().numpy()
     ref = H.Batch(16, n_competitive=2, **SETUP)
     gb = H.Batch(16, n_competitive=2, **SETUP)
+    st = orc.RoundState(16, SETUP["s"], SETUP["k"], SETUP["group"])
     R = 5
     for r in range(R):
         H.hpc_round(ctx, X, ref, strategy, 13, r)
@@ -65,16 +86,49 @@ def test_prepared_round_replays_from_a_cuda_graph(ctx, strategy):
     g = torch.cuda.CUDAGraph()
     old = ctx.stream if hasattr(ctx, "stream") else torch.cuda.current_stream()
     try:
+        ctx.set_phase_timing(True)
         with torch.cuda.graph(g, stream=side):
             ctx.set_stream(side)
             H.hpc_round_enqueue(ctx)      # recorded, not run
-        for _ in range(R):
+        for r in range(R):
             g.replay()
+            # every replay times itself: the event records are graph nodes
+            ms = ctx.phase_times()
+            assert ms["sample"] > 0 and ms["kmeanspp"] > 0 and ms["lloyd"] > 0, ms
+            # each replayed round against the oracle's round r, directly
+            res = orc.round_(Xh, st, strategy, 13, r, n_competitive=2)
+            torch.cuda.synchronize()
+            assert_matches_oracle(gb, st, res)
         torch.cuda.synchronize()
     finally:
+        ctx.set_phase_timing(False)
         ctx.set_stream(old if isinstance(old, torch.cuda.Stream) else torch.cuda.current_stream())
     ctx.check_status()
     same(ref, gb)
+
+
+def test_phase_timing_of_issued_rounds(ctx):
+    X = mixture(20000, 8, 6, 53)
+    b = H.Batch(8, [3000, 2000], [5, 7])
+    with pytest.raises(H.HPCError):
+        ctx.phase_times()                 # nothing timed yet
+    ctx.set_phase_timing(True)
+    try:
+        H.hpc_round(ctx, X, b, H.HPC_COMPETITIVE, 1, 0)
+        ms = ctx.phase_times()
+        assert all(v > 0 for v in ms.values()), ms
+    finally:
+        ctx.set_phase_timing(False)
+    ctx.check_status()
+
+
+def test_lloyd_schedule_reports_the_planned_launch(ctx):
+    small = ctx.lloyd_schedule(100_000, 16, 25)
+    assert small["smem_sums"] and small["blocks"] >= 1 and small["smem_bytes"] > 0
+    big = ctx.lloyd_schedule(1_048_576, 64, 500)
+    assert not big["smem_sums"]           # 500 x 64 x 8 bytes exceed a block's shared memory
+    with pytest.raises(H.HPCError):
+        ctx.lloyd_schedule(0, 16, 25)
 
 
 def test_round_arguments_are_checked(ctx):

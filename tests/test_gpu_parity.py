@@ -5,8 +5,12 @@ Bars (from the arithmetic, see each test):
     exact-fixed-point decisions taken in the same precision on both sides);
   * labels: equal, except rows whose two nearest double-precision distances
     differ by less than 1e-6 relative (a near tie);
-  * objectives: within 1e-6 relative; centroids: within 1e-6 of the largest
-    centroid coordinate.
+  * objectives: within 1e-6 relative; centroids: per coordinate within 1e-6
+    relative plus an absolute floor of 1e-9 of the largest coordinate (the
+    GPU sums coordinates exactly on a fixed-point grid 2^-F with
+    F = 62 - bitlen(s) - e(max|x|), so each mean carries at most
+    2^(bitlen(s) + e - 63) <= 2^-42 max|x| of grid rounding for s <= 2^20,
+    and both sides round the mean to float once).
 """
 import numpy as np
 import pytest
@@ -20,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 RTOL = 1e-6
 TIE = 1e-6
+ATOL_REL = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -61,9 +66,16 @@ def assert_labels(lab_g, S, C, deg, what=""):
 
 
 def assert_centroids(Cg, Co, what=""):
-    scale = max(1.0, float(np.abs(Co).max()))
-    err = float(np.abs(Cg.astype(np.float64) - Co.astype(np.float64)).max())
-    assert err <= RTOL * scale, f"{what}: centroid error {err} > {RTOL * scale}"
+    """Per coordinate: |Cg - Co| <= 1e-6 |Co| + 1e-9 max(1, max |Co|)."""
+    Co64 = np.asarray(Co, np.float64)
+    Cg64 = np.asarray(Cg, np.float64)
+    scale = max(1.0, float(np.abs(Co64).max())) if Co64.size else 1.0
+    tol = RTOL * np.abs(Co64) + ATOL_REL * scale
+    bad = np.abs(Cg64 - Co64) > tol
+    if bad.any():
+        i = np.unravel_index(np.argmax(np.abs(Cg64 - Co64) - tol), Co64.shape)
+        raise AssertionError(f"{what}: {int(bad.sum())} centroid coordinates off, worst at {i}: "
+                             f"{Cg64[i]} vs {Co64[i]}")
 
 
 # ---------------------------------------------------------------------------
@@ -254,13 +266,8 @@ def lockstep_divergence(ctx, S, C0, deg0, iters):
     return None
 
 
-@pytest.mark.parametrize("s,d,k,seed", [(2000, 2, 5, 0), (100000, 16, 25, 1), (20000, 32, 50, 2),
-                                        (9001, 64, 30, 3), (5000, 128, 10, 4), (30011, 5, 8, 5),
-                                        # d in (64, 128]: the d = 128 kernel, and at d = 100
-                                        # its rows padded with zeros
-                                        (30011, 128, 40, 6), (7001, 100, 17, 7)])
-def test_lloyd_parity(ctx, s, d, k, seed):
-    S = mixture(s, d, k, seed, sd=1.5)
+def lloyd_case(ctx, S, k, seed):
+    d = S.shape[1]
     init = orc.kmeanspp(S, np.zeros((k, d), np.float32), np.ones(k, np.uint8), seed=seed)
     C0, deg0 = init["C"], init["degenerate"]
     o = orc.lloyd(S, C0, deg0)
@@ -278,8 +285,49 @@ def test_lloyd_parity(ctx, s, d, k, seed):
             it = min(g["iters"], o["iters"])
             ratio = (tr[it - 1] - tr[it]) / tr[it - 1]
             assert abs(ratio - 1e-4) <= 1e-6, "trajectories differ without a near tie"
+            step = it
+        # up to the step where they part, the two runs agree within the
+        # contract: the same number of updates from the same start
+        if step > 0:
+            gs = gpu_lloyd(ctx, S, C0, deg0, max_iter=step, rel_tol=0.0)
+            os_ = orc.lloyd(S, C0, deg0, max_iter=step, rel_tol=0.0)
+            assert gs["iters"] == os_["iters"] == step
+            assert_centroids(gs["C"], os_["C"], f"lloyd up to step {step}")
+            np.testing.assert_array_equal(gs["degenerate"], os_["degenerate"])
+            assert gs["f"] == pytest.approx(os_["f"], rel=RTOL)
     # the reported objective is the objective of the returned centroids
     assert g["f"] == pytest.approx(orc.objective(S, g["C"], g["degenerate"]), rel=RTOL)
+    return g, o
+
+
+@pytest.mark.parametrize("s,d,k,seed", [(2000, 2, 5, 0), (100000, 16, 25, 1), (20000, 32, 50, 2),
+                                        (9001, 64, 30, 3), (5000, 128, 10, 4), (30011, 5, 8, 5),
+                                        # d in (64, 128]: the d = 128 kernel, and at d = 100
+                                        # its rows padded with zeros
+                                        (30011, 128, 40, 6), (7001, 100, 17, 7)])
+def test_lloyd_parity(ctx, s, d, k, seed):
+    S = mixture(s, d, k, seed, sd=1.5)
+    lloyd_case(ctx, S, k, seed)
+
+
+@pytest.mark.parametrize("s,d,k,seed", [(20000, 64, 500, 11), (5000, 128, 256, 12),
+                                        (65536, 64, 500, 13)])
+def test_lloyd_parity_global_sums(ctx, s, d, k, seed):
+    # k x d x 8 bytes of per-block sums above what a block's shared memory
+    # holds (the large workload's k = 500 at d = 64): every block adds its
+    # rows' fixed-point coordinates straight into the global sums
+    sched = ctx.lloyd_schedule(s, d, k)
+    assert not sched["smem_sums"], sched
+    # a Zipf-weighted mixture like the large workload's (several centroids
+    # share the heavy components, light ones get few rows)
+    rng = np.random.default_rng(seed)
+    comps = k
+    mu = 4.0 * rng.standard_normal((comps, d))
+    w = np.arange(1, comps + 1, dtype=np.float64) ** -1.1
+    z = rng.choice(comps, s, p=w / w.sum())
+    sd = rng.uniform(0.5, 2.0, comps)
+    S = (mu[z] + sd[z, None] * rng.standard_normal((s, d))).astype(np.float32)
+    lloyd_case(ctx, S, k, seed)
 
 
 def test_lloyd_edge_cases(ctx):
