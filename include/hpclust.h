@@ -63,8 +63,10 @@ typedef enum hpc_precision {
 typedef enum hpc_search {
   HPC_SEARCH_SIMT = 0,       /* FP32 expanded form on the CUDA cores */
   HPC_SEARCH_SPLIT_TF32 = 1, /* tensor cores, three TF32 products per K step (d in {16, 32}) */
-  HPC_SEARCH_TF32 = 2        /* tensor cores, one TF32 product (d in {16, 32, 64}: k <= 512;
+  HPC_SEARCH_TF32 = 2,       /* tensor cores, one TF32 product (d in {16, 32, 64}: k <= 512;
                                 d = 128: k <= 256) */
+  HPC_SEARCH_SPLIT_BF16 = 3  /* tensor cores, three BF16 products per K step (d = 64: k <= 512;
+                                d = 128: k <= 256); also the Lloyd iterations' search */
 } hpc_search;
 
 typedef enum hpc_strategy {
@@ -136,9 +138,9 @@ int hpc_objective_form(hpc_ctx *ctx, int64_t n, int32_t d, int32_t k);
  * on the context's stream; keeps the fastest for (d, k) as
  * hpc_set_objective_form would (the built-in form when it is within 1% of
  * the fastest, so that timing noise does not move the choice).  *form_out
- * (nullable) receives it, ms_out (host float[3], nullable) the average
- * milliseconds per call of each
- * form, -1 where not built.  Synchronises the stream.  Errors: as
+ * (nullable) receives it, ms_out (host float[4], nullable) the average
+ * milliseconds per call of each form (indexed by hpc_search), -1 where not
+ * built.  Synchronises the stream.  Errors: as
  * hpc_objective; a device error recorded during the sweep ends it and is
  * returned. */
 int hpc_autotune_objective(hpc_ctx *ctx, const float *X, int64_t n, int32_t d, const float *C,
@@ -440,9 +442,11 @@ int hpc_costmodel_plan(const float *pred, const int32_t *supported, float margin
 /* hpc_autotune_objective guided by the network `params` (device): the forms
  * built for (d, k) are ranked by predicted time; the best-ranked one is
  * timed, and each other one only if its predicted time is within a factor
- * (1 + margin) of the best-ranked one's.  The fastest timed form is kept as
- * hpc_autotune_objective would keep it.  ms_out (host float[3], nullable)
- * gets the time per call of each timed form, -1 for the others;
+ * (1 + margin) of the best-ranked one's; HPC_SEARCH_SPLIT_BF16, which the
+ * network's inputs do not describe, is timed whenever it is built.  The
+ * fastest timed form is kept as hpc_autotune_objective would keep it.
+ * ms_out (host float[4], nullable) gets the time per call of each timed
+ * form, -1 for the others;
  * timed_out (host, nullable) the number of forms timed.  margin >= 0; a
  * very large margin times every form (the unguided search). */
 int hpc_autotune_objective_guided(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,

@@ -15,7 +15,7 @@ CSRC = PKG / "csrc"
 OUT = PKG / "libhpclust.so"
 OBJ = PKG / "_build"
 SOURCES = ["capi.cu", "lloyd.cu", "kmeanspp.cu", "sample.cu", "tc_objective.cu", "tc_split.cu", "noalloc.cu",
-           "peaks.cu", "tc_wide.cu", "costmodel.cu"]
+           "peaks.cu", "tc_wide.cu", "costmodel.cu", "tc_bf16.cu"]
 HEADERS = ["common.cuh", "assign.cuh", "kernels.h", "tc.cuh", "round.cuh", "tc_rows.cuh", "costmodel.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -20,6 +20,8 @@
 #define HPC_MAX_WORKERS 65535
 // events of one timed round: rounds of up to 31 launch chunks are timed
 #define HPC_TIMING_EVENTS 64
+// search forms of the objective (hpc_search)
+#define HPC_NFORMS 4
 
 struct hpc_round_plan;
 
@@ -132,9 +134,15 @@ struct TaskHeader {
 };
 static_assert(sizeof(TaskHeader) == 256, "task header is one 256-byte line");
 
-size_t lloyd_ws(const hpc_ctx *c, int d, int k) {
+// what the split-BF16 tensor-core Lloyd adds per task: the rows' previous
+// labels and the exact centroid block
+size_t tcl_ws(int d, int k, int64_t s) {
+  return hpc_tcl_supported(d, k) ? pad256((size_t)s * 4) + pad256(hpc_tcl_gcent_bytes(d, k)) : 0;
+}
+
+size_t lloyd_ws(const hpc_ctx *c, int d, int k, int64_t s) {
   return sizeof(TaskHeader) + pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
-         pad256((size_t)k) + 256;
+         pad256((size_t)k) + tcl_ws(d, k, s) + 256;
 }
 
 size_t kpp_ws(const hpc_ctx *c, int64_t s, int L) {
@@ -161,6 +169,12 @@ void lloyd_task_scratch(const hpc_ctx *c, Carver &cv, TaskHeader *hd, int d, int
   t.gsum = cv.take<unsigned long long>((size_t)3 * k * d);
   t.gcount = cv.take<unsigned>((size_t)3 * k);
   t.gobj = hd->gobj;
+  t.plab = nullptr;
+  t.gcent = nullptr;
+  if (hpc_tcl_supported(d, k)) {
+    t.plab = t.labels ? t.labels : cv.take<int32_t>((size_t)t.s);
+    t.gcent = cv.take<float>(hpc_tcl_gcent_bytes(d, k) / 4);
+  }
 }
 
 void kpp_task_scratch(const hpc_ctx *c, Carver &cv, TaskHeader *hd, int64_t s, int L,
@@ -208,6 +222,7 @@ int run_lloyd(hpc_ctx *c, Carver &cv, const float *S, int64_t s, int d, int k, f
   h.status = c->dwords;
   h.max_blocks = c->grid_bound;
   h.task_blocks = c->grid_bound;
+  h.tc_mode = c->use_tc;
   int rc = hpc_lloyd_plan(c->L, h);
   if (rc) return plan_fail(c, rc, "lloyd: unsupported shape");
   if ((rc = hpc_lloyd_run(c->L, h))) return plan_fail(c, rc, "lloyd launch");
@@ -251,6 +266,7 @@ bool form_supported(int form, int d, int k, int64_t n) {
     case HPC_SEARCH_SIMT: return true;
     case HPC_SEARCH_SPLIT_TF32: return hpc_tcs_objective_supported(d, k, n);
     case HPC_SEARCH_TF32: return hpc_tc_objective_supported(d, k, n);
+    case HPC_SEARCH_SPLIT_BF16: return n >= 1 && hpc_tcl_supported(d, k);
     default: return false;
   }
 }
@@ -265,7 +281,8 @@ int objective_form(const hpc_ctx *c, int d, int k, int64_t n) {
   if (c->use_tc == 0) return HPC_SEARCH_SIMT;
   if (c->use_tc == 1) {
     if (hpc_tcs_objective_supported(d, k, n)) return HPC_SEARCH_SPLIT_TF32;
-    if (hpc_tc_objective_supported(d, k, n) && d >= 64) return HPC_SEARCH_TF32;
+    if (hpc_tc_objective_supported(d, k, n) && d >= 64 && k <= 128) return HPC_SEARCH_TF32;
+    if (form_supported(HPC_SEARCH_SPLIT_BF16, d, k, n)) return HPC_SEARCH_SPLIT_BF16;
     return HPC_SEARCH_SIMT;
   }
   for (const auto &f : c->forms)
@@ -283,6 +300,10 @@ int builtin_form(int d, int k, int64_t n) {
   // mixtures): the CUDA cores unless a measurement says otherwise
   if (d == 32 && hpc_tcs_objective_supported(d, k, n)) return HPC_SEARCH_SPLIT_TF32;
   if (d >= 64 && k <= 128 && hpc_tc_objective_supported(d, k, n)) return HPC_SEARCH_TF32;
+  // above 128 centroids at d = 64 / 128 the split-BF16 products keep the
+  // error window as narrow as split TF32, so that rows near a tie stay rare
+  // with the method's own incumbents
+  if (d >= 64 && form_supported(HPC_SEARCH_SPLIT_BF16, d, k, n)) return HPC_SEARCH_SPLIT_BF16;
   return HPC_SEARCH_SIMT;
 }
 
@@ -316,6 +337,8 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
     rc = hpc_tcs_objective_launch(c->L, h);
   else if (form == HPC_SEARCH_TF32)
     rc = hpc_tc_objective_launch(c->L, h);
+  else if (form == HPC_SEARCH_SPLIT_BF16)
+    rc = hpc_tcb_objective_launch(c->L, h);
   if (rc == HPC_ERR_UNSUPPORTED) rc = hpc_objective_launch(c->L, h);
   if (rc == HPC_ERR_CUDA) return cuda_fail(c, cudaGetLastError(), "objective launch");
   if (rc) return fail(c, rc, "objective: unsupported shape");
@@ -425,7 +448,8 @@ static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, i
     const int k = b->k[w];
     need += pad256((size_t)s * d * 4) + pad256((size_t)k * d * 4) + pad256((size_t)k) +
             pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) + pad256((size_t)s * 4) +
-            pad256((size_t)L * s * 4) + pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8);
+            pad256((size_t)L * s * 4) + pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8) +
+            tcl_ws(d, k, s);
   }
   *tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) + pad256((size_t)W * sizeof(hpc_round_worker)) +
                pad256((size_t)W * sizeof(hpc_kpp_task)) + pad256((size_t)W * sizeof(hpc_lloyd_task)) +
@@ -527,6 +551,7 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     lh.status = c->dwords;
     lh.max_blocks = c->grid_bound;
     lh.task_blocks = c->grid_bound;
+    lh.tc_mode = c->use_tc;
     if (int rc = hpc_lloyd_plan(c->L, lh)) return plan_fail(c, rc, "lloyd: unsupported shape");
   }
   if (cv.off > cv.cap || th.off > th.cap) return fail(c, HPC_ERR_NOMEM, "round scratch layout overflow");
@@ -757,7 +782,7 @@ int hpc_lloyd(hpc_ctx *c, const float *S, int64_t s, int32_t d, int32_t k, float
   if (prec != HPC_FP32) return fail(c, HPC_ERR_UNSUPPORTED, "only HPC_FP32 is built");
   if (!aligned16(S) || !aligned16(C_inout)) return fail(c, HPC_ERR_ARG, "unaligned");
   cudaSetDevice(c->device);
-  if (int rc = ensure_ws(c, lloyd_ws(c, d, k))) return rc;
+  if (int rc = ensure_ws(c, lloyd_ws(c, d, k, s))) return rc;
   Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
   return run_lloyd(c, cv, S, s, d, k, C_inout, degenerate_inout, max_iter, rel_tol, labels_out,
                    f_out, iters_out);
@@ -777,7 +802,7 @@ int hpc_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float 
 }
 
 int hpc_set_objective_form(hpc_ctx *c, int32_t d, int32_t k, int32_t form) {
-  if (!c || d < 1 || d > 128 || k < 1 || form < -1 || form > HPC_SEARCH_TF32)
+  if (!c || d < 1 || d > 128 || k < 1 || form < -1 || form > HPC_SEARCH_SPLIT_BF16)
     return fail(c, HPC_ERR_ARG, "bad objective form");
   if (form >= 0 && !form_supported(form, d, k, 1))
     return fail(c, HPC_ERR_UNSUPPORTED, "objective form not built for this shape");
@@ -809,8 +834,9 @@ int hpc_lloyd_schedule(hpc_ctx *c, int64_t s, int32_t d, int32_t k, int32_t *out
   h.kmax = k;
   h.max_blocks = c->grid_bound;
   h.task_blocks = c->grid_bound;
+  h.tc_mode = c->use_tc;
   if (int rc = hpc_lloyd_plan(c->L, h)) return plan_fail(c, rc, "lloyd: unsupported shape");
-  const int32_t v[5] = {(int32_t)h.grid, h.smem_sums, h.xstage, (int32_t)h.smem, 0};
+  const int32_t v[5] = {(int32_t)h.grid, h.smem_sums, h.xstage, (int32_t)h.smem, h.form};
   for (int i = 0; i < nout && i < 5; ++i) out[i] = v[i];
   return HPC_OK;
 }
@@ -900,7 +926,7 @@ int autotune_forms(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_fail(c, cudaGetLastError(), "event create");
   int best = -1, timed = 0;
-  float best_ms = 0.0f, tms[3] = {-1.0f, -1.0f, -1.0f};
+  float best_ms = 0.0f, tms[HPC_NFORMS] = {-1.0f, -1.0f, -1.0f, -1.0f};
   int rc = HPC_OK;
   for (int i = 0; i < count && rc == HPC_OK; ++i) {
     const int form = order[i];
@@ -922,7 +948,7 @@ int autotune_forms(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float
   const int bi = builtin_form(d, k, n);
   if (bi != best && tms[bi] > 0.0f && tms[bi] <= 1.01f * best_ms) best = bi;
   if (ms_out)
-    for (int q = 0; q < 3; ++q) ms_out[q] = tms[q];
+    for (int q = 0; q < HPC_NFORMS; ++q) ms_out[q] = tms[q];
   if (form_out) *form_out = best;
   if (timed_out) *timed_out = timed;
   return hpc_set_objective_form(c, d, k, best);
@@ -981,8 +1007,8 @@ int hpc_autotune_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, con
                            float *ms_out) {
   if (!c) return HPC_ERR_ARG;
   if (int rc = check_autotune_args(c, X, n, d, C, k, reps)) return rc;
-  int order[3], count = 0;
-  for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_TF32; ++form)
+  int order[HPC_NFORMS], count = 0;
+  for (int form = HPC_SEARCH_SIMT; form <= HPC_SEARCH_SPLIT_BF16; ++form)
     if (form_supported(form, d, k, n)) order[count++] = form;
   return autotune_forms(c, X, n, d, C, k, degenerate, reps, order, count, nullptr, form_out,
                         ms_out, nullptr);
@@ -1113,8 +1139,16 @@ int hpc_autotune_objective_guided(hpc_ctx *c, const float *X, int64_t n, int32_t
   int32_t order[3], timed[3];
   const int count = hpc_costmodel_plan(pred, sup, margin, order, timed);
   if (count < 0) return fail(c, HPC_ERR_ARG, "cost model predicts a non-finite time");
-  int ord[3] = {order[0], order[1], order[2]};
-  return autotune_forms(c, X, n, d, C, k, degenerate, reps, ord, count, timed, form_out, ms_out,
+  // the split-BF16 form is newer than the network's inputs: timed whenever
+  // it is built
+  int ord[HPC_NFORMS] = {order[0], order[1], order[2], HPC_SEARCH_SPLIT_BF16};
+  int32_t tm[HPC_NFORMS] = {timed[0], timed[1], timed[2], 1};
+  const int cnt = count + (form_supported(HPC_SEARCH_SPLIT_BF16, d, k, n) ? 1 : 0);
+  if (cnt > count) {
+    ord[count] = HPC_SEARCH_SPLIT_BF16;
+    tm[count] = 1;
+  }
+  return autotune_forms(c, X, n, d, C, k, degenerate, reps, ord, cnt, tm, form_out, ms_out,
                         timed_out);
 }
 

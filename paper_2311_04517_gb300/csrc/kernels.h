@@ -38,6 +38,11 @@ struct hpc_lloyd_task {
   unsigned long long *gsum;  // 3 * k * d
   unsigned *gcount;          // 3 * k
   unsigned long long *gobj;  // 3 rotating fixed-point sample objectives, zero at launch
+  // tensor-core Lloyd only: each row's label of the previous assignment (s;
+  // the caller's labels array when it gives one) and the exact centroid
+  // block read by its exact stages (hpc_tcl_gcent_bytes(d, k) bytes)
+  int32_t *plab;
+  float *gcent;
   // incumbent rule at the end of the run (rounds only; fhat null otherwise)
   double *fhat;              // this worker's incumbent objective per point
   float *C_inc;              // its incumbent centroids (k x d) in the pool
@@ -67,6 +72,10 @@ struct LloydLaunch {
   int xstage;
   // nullable: a prepared round's counter, advanced once the run is done
   uint32_t *round_advance;
+  // search: 0 CUDA cores only, 1 tensor cores wherever built, 2 where
+  // measured faster (the plan writes the one chosen into `form`)
+  int tc_mode;
+  int form;  // written by the plan: hpc_search (0 CUDA cores, 3 split BF16)
 };
 
 // ---- K-means++ (one task = one sample) ----
@@ -191,6 +200,15 @@ int hpc_sample_batch_launch(const hpc_launch &L, const float *X, int64_t n, int 
                             uint32_t round, const uint32_t *round_dev, int W,
                             const hpc_sample_task *tasks_dev, int64_t smax,
                             const hpc_base_args &base);
+
+// Split-BF16 tensor-core Lloyd (d = 64: k <= 512; d = 128: k <= 256).
+bool hpc_tcl_supported(int d, int kmax);
+size_t hpc_tcl_gcent_bytes(int d, int k);
+int hpc_tcl_plan(const hpc_launch &L, LloydLaunch &h);
+int hpc_tcl_run(const hpc_launch &L, const LloydLaunch &h);
+// Split-BF16 tensor-core full-data objective (same shapes); needs
+// h.cent_scratch of hpc_tcl_gcent_bytes(d, k) + 256 bytes.
+int hpc_tcb_objective_launch(const hpc_launch &L, const ObjArgsHost &h);
 
 // Blocks the cooperative kernels may use at most (upper bound for scratch
 // sizing): resident blocks per SM times SMs.

@@ -549,7 +549,19 @@ void hpc_split_blocks(int W, const int64_t *rows, const int64_t *work, int64_t r
   }
 }
 
+// Where the split-BF16 tensor-core Lloyd runs (mode 2): rows of 64 or 128
+// floats with enough centroids that the k columns of a row tile keep the
+// tensor cores busy.
+static bool tcl_builtin(int d, int kmax) { return hpc_tcl_supported(d, kmax) && kmax >= 48; }
+
 int hpc_lloyd_plan(const hpc_launch &L, LloydLaunch &h) {
+  h.form = HPC_SEARCH_SIMT;
+  if (h.tc_mode != 0 && hpc_tcl_supported(h.d, h.kmax) &&
+      (h.tc_mode == 1 || tcl_builtin(h.d, h.kmax))) {
+    const int rc = hpc_tcl_plan(L, h);
+    if (rc != HPC_ERR_UNSUPPORTED) return rc;
+    h.form = HPC_SEARCH_SIMT;
+  }
   switch (hpc_pad_dim(h.d)) {
     case 2: return lloyd_plan_d<2>(L, h);
     case 4: return lloyd_plan_d<4>(L, h);
@@ -562,6 +574,7 @@ int hpc_lloyd_plan(const hpc_launch &L, LloydLaunch &h) {
 }
 
 int hpc_lloyd_run(const hpc_launch &L, const LloydLaunch &h) {
+  if (h.form == HPC_SEARCH_SPLIT_BF16) return hpc_tcl_run(L, h);
   switch (hpc_pad_dim(h.d)) {
     case 2: return lloyd_run_d<2>(L, h);
     case 4: return lloyd_run_d<4>(L, h);

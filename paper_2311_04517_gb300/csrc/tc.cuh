@@ -155,6 +155,26 @@ __device__ __forceinline__ void hpc_mma_tf32(uint32_t d_tmem, uint64_t adesc, ui
       : "memory");
 }
 
+// D (+)= A . B with A and B both BF16 from shared memory (kind::f16; the
+// instruction descriptor names the BF16 formats), FP32 accumulation.
+__device__ __forceinline__ void hpc_mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                             uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Asks the L2 cache to fetch `bytes` (a multiple of 16) from global memory
+// at `p` (16-byte aligned); completes on its own, nothing waits for it.
+__device__ __forceinline__ void hpc_prefetch_l2_bulk(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)),
+               "r"(bytes)
+               : "memory");
+}
+
 // Arrives once on *bar when every MMA issued so far by this thread is done.
 __device__ __forceinline__ void hpc_mma_commit(uint64_t *bar) {
   asm volatile(

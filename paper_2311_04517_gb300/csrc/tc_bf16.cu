@@ -1,0 +1,1092 @@
+// Nearest-centroid search with the x.c contraction on the tensor cores in
+// split BF16, for rows of 64 or 128 floats and up to 512 (d = 64) or 256
+// (d = 128) centroids: Lloyd's iterations on a sample (Algorithm 1, with the
+// stop rule of Section 6.5) and the full-data objective (Eq. 1).
+//
+// Search value of centroid j for row x: v_j = ||c_j||^2 + x.c'_j, c' = -2c.
+// Both operands are split into two BF16 parts, x = x_h + x_l + r_x and
+// c' = c_h + c_l + r_c (x_h = bf16(x), x_l = bf16(x - x_h); |r| <= 2^-18 of
+// the value), and the tensor cores form three exact BF16 products per K step
+// in FP32: x_h.c_h + x_h.c_l + x_l.c_h.  The dropped terms x_l c_l, r_x c'
+// and x r_c stay below 3.01 * 2^-18 |x_t| |c'_t| per coordinate, and FP32
+// accumulation over the 3 d products adds at most 3 d 2^-23 of
+// sum_t |x_t| |c'_t| <= ||x|| ||c'|| = 2 ||x|| ||c||; with
+// (||x|| + max||c||)^2 >= 4 ||x|| ||c||, every computed v_j lies within
+// 2^-15.8 (||x|| + max||c||)^2 of the exact one at d = 64 (2^-14.9 at
+// d = 128).  The kernels use E = 2^-14 (||x|| + max||c||)^2.  A row whose
+// top-2 margin exceeds 2E (plus the packed keys' 2^(IB-22) (|k1| + |k2|)) has
+// the exact nearest centroid; otherwise its two candidates are computed
+// exactly (FP32 direct form), every other centroid being at least
+// ||x||^2 + d2 - E away, and rows that remain open are settled by their warp
+// against every centroid (FP32 direct form, then FP64 in the oracle's
+// operation order, ties to the lowest index).
+//
+// Data path per 128-row tile (one persistent CTA per SM):
+//   warps 0-1 (converters): coalesced 16-byte loads of the FP32 rows (an L2
+//     bulk prefetch two tiles ahead), split into x_h | x_l, written as the
+//     MMA's A operand (K-major, 128-byte swizzle) into one of two
+//     shared-memory stages;
+//   warp 2 (TMEM owner, MMA issuer, one thread): 3 d / 16 x 3 kind::f16
+//     MMAs per 256-column bank against B = (c_h | c_l) resident in shared
+//     memory; TMEM holds two banks (two tiles in flight for up to 256
+//     centroids, the two halves of one tile for up to 512);
+//   warps 3-18 (four epilogue warpgroups): warpgroup e folds a quarter of a
+//     tile's columns into a partial top-2 per row ((value, index) keys with
+//     7 to 9 index bits) and leaves it in a rotating exchange buffer; the
+//     warpgroup e = tile mod 4 merges the four partials and finishes the
+//     tile's rows (exact distance, margin test, exact stages, objective,
+//     labels, and in Lloyd the centroid sums).
+//
+// Lloyd's centroid sums are kept incrementally: every coordinate goes on the
+// exact 64-bit fixed-point grid 2^-Fs of the CUDA-core kernel, the first
+// assignment adds every row, and each later one adds only the rows whose
+// label changed (to the new centroid) and takes them away from the old one;
+// integer sums make that equal to summing every row again, in any order.
+// An iteration: the pipeline over the CTA's tiles, a bounded barrier of the
+// task's CTAs, the stop test and the new means (every CTA, identical), a
+// second barrier (every CTA has read the sums before any adds to them
+// again).  Every mbarrier wait is bounded (a wait that runs out records
+// HPC_ERR_TIMEOUT and every role stops); in-flight MMAs are drained before
+// TMEM is freed.
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "assign.cuh"
+#include "kernels.h"
+#include "round.cuh"
+#include "tc.cuh"
+#include "tc_rows.cuh"
+
+namespace {
+
+constexpr int TB_M = 128;
+constexpr int TB_CONV = 2;                       // converter warps 0, 1
+constexpr int TB_MMAW = 2;                       // TMEM owner and MMA issuer
+constexpr int TB_EPI0 = 3;                       // first epilogue warp
+constexpr int TB_THREADS = (TB_EPI0 + 16) * 32;  // 608
+constexpr int TB_NX = 4;                         // exchange buffers
+constexpr uint64_t TB_WAIT_NS = 2000000000ull;
+constexpr uint64_t TB_DRAIN_NS = 500000000ull;
+constexpr float TB_E_REL = 6.103515625e-05f;     // 2^-14
+
+template <int D, int NP>
+struct TbCfg {
+  static_assert(D == 64 || D == 128, "rows of 64 or 128 floats");
+  static_assert(NP == 128 || NP == 256 || NP == 512, "128, 256 or 512 columns");
+  static constexpr uint32_t ATILE = TB_M * D * 2;  // one BF16 part of a row tile
+  static constexpr uint32_t BPART = NP * D * 2;    // one BF16 part of B
+  static constexpr int PARTS = NP > 256 ? 2 : 1;   // TMEM banks per tile
+  static constexpr int BANKW = NP > 256 ? 256 : NP;
+  static constexpr int TCOLS = NP > 256 ? 512 : 2 * NP;
+  static constexpr int CPW = NP / 4;               // columns per epilogue warpgroup
+  static constexpr int READERS = NP > 256 ? 8 : 16;
+  static constexpr int IB = NP == 512 ? 9 : NP == 256 ? 8 : 7;
+  static constexpr size_t REST = (size_t)NP * 4 + (size_t)TB_NX * 4 * TB_M * 8 + 512 + 256;
+  static constexpr int NSTAGE = 2 * (size_t)BPART + 4 * (size_t)ATILE + REST + 1024 <= 225 * 1024 ? 2 : 1;
+  static constexpr size_t AOP = 2 * (size_t)BPART;
+  static constexpr size_t CN = AOP + (size_t)NSTAGE * 2 * ATILE;
+  static constexpr size_t XCH = CN + (size_t)NP * 4;
+  static constexpr size_t DEADF = XCH + (size_t)TB_NX * 4 * TB_M * 8;
+  static constexpr size_t BARS = DEADF + 512;
+  static constexpr int NBARS = 2 * NSTAGE + 4 + 2 * TB_NX + 1;
+  static constexpr size_t TOTAL = BARS + NBARS * 8 + 1024;
+};
+
+// Shared-memory views of one CTA.
+struct TbSm {
+  unsigned char *bh, *bl, *a;
+  float *cn;
+  float2 *xch;
+  uint8_t *dead;
+  uint64_t *afull, *afree, *accf, *acce, *xready, *xdone, *drain;
+  volatile int *abort;
+  uint32_t tmem;
+};
+
+template <int D, int NP>
+__device__ __forceinline__ TbSm tb_bind(unsigned char *base, volatile int *abort) {
+  using Cfg = TbCfg<D, NP>;
+  TbSm m;
+  m.bh = base;
+  m.bl = base + Cfg::BPART;
+  m.a = base + Cfg::AOP;
+  m.cn = reinterpret_cast<float *>(base + Cfg::CN);
+  m.xch = reinterpret_cast<float2 *>(base + Cfg::XCH);
+  m.dead = base + Cfg::DEADF;
+  uint64_t *b = reinterpret_cast<uint64_t *>(base + Cfg::BARS);
+  m.afull = b;
+  m.afree = b + Cfg::NSTAGE;
+  m.accf = m.afree + Cfg::NSTAGE;
+  m.acce = m.accf + 2;
+  m.xready = m.acce + 2;
+  m.xdone = m.xready + TB_NX;
+  m.drain = m.xdone + TB_NX;
+  m.abort = abort;
+  m.tmem = 0;
+  return m;
+}
+
+template <int D, int NP>
+__device__ __forceinline__ void tb_init_barriers(const TbSm &m) {
+  using Cfg = TbCfg<D, NP>;
+  for (int s = 0; s < Cfg::NSTAGE; ++s) {
+    hpc_mbar_init(&m.afull[s], TB_CONV);
+    hpc_mbar_init(&m.afree[s], 1);
+  }
+  for (int b = 0; b < 2; ++b) {
+    hpc_mbar_init(&m.accf[b], 1);
+    hpc_mbar_init(&m.acce[b], Cfg::READERS);
+  }
+  for (int b = 0; b < TB_NX; ++b) {
+    hpc_mbar_init(&m.xready[b], 16);
+    hpc_mbar_init(&m.xdone[b], 4);
+  }
+  hpc_mbar_init(m.drain, 1);
+  hpc_fence_barrier_init();
+}
+
+__device__ __forceinline__ uint32_t tb_bits(__nv_bfloat162 v) {
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Byte offset of element t (a multiple of 2) of row r in a K-major BF16
+// operand of `rows` rows: 64-element chunks of rows x 128 bytes, 128-byte
+// swizzle inside each.
+__device__ __forceinline__ uint32_t tb_koff(uint32_t r, uint32_t t, uint32_t rows) {
+  return (t >> 6) * rows * 128u + hpc_swz_offset(r, (t & 63u) * 2u, 128u);
+}
+
+// The split c' = -2c = c_h + c_l of centroid row j's values v[] at dims
+// t0 .. t0 + PER - 1 into B (shared memory), PER even.
+template <int PER, int NP>
+__device__ __forceinline__ void tb_store_b(const TbSm &m, int j, int t0, const float (&c)[PER]) {
+#pragma unroll
+  for (int u = 0; u < PER; u += 2) {
+    const float a0 = -2.0f * c[u], a1 = -2.0f * c[u + 1];
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a0 - hf.x, a1 - hf.y);
+    const uint32_t off = tb_koff((uint32_t)j, (uint32_t)(t0 + u), NP);
+    *reinterpret_cast<uint32_t *>(m.bh + off) = tb_bits(h);
+    *reinterpret_cast<uint32_t *>(m.bl + off) = tb_bits(l);
+  }
+}
+
+// Row source of the pipeline: rows [0, nrows) of `rows` (stride D floats);
+// the i-th tile of this CTA is tile0 + i * tstep.
+struct TbRows {
+  const float *rows;
+  int64_t nrows;
+  int64_t tile0, tstep;
+  int ntiles;
+};
+
+// ---- converters (warps 0, 1) ------------------------------------------------
+template <int D, int NP>
+__device__ __forceinline__ void tb_convert(const TbSm &m, const TbRows &R, uint32_t gbase, int *status) {
+  using Cfg = TbCfg<D, NP>;
+  constexpr int F4 = D / 4;                       // float4 per row
+  constexpr int LDS = 64 * F4 / 32;               // loads per lane per tile
+  constexpr int BATCH = 8;
+  const int cw = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = 0; i < R.ntiles; ++i) {
+    const uint32_t g = gbase + (uint32_t)i;
+    const int st = (int)(g % Cfg::NSTAGE);
+    const uint32_t use = g / Cfg::NSTAGE;
+    const int64_t row0 = (R.tile0 + (int64_t)i * R.tstep) * TB_M;
+    if (cw == 0 && lane == 0 && i + 2 < R.ntiles) {
+      const int64_t p0 = (R.tile0 + (int64_t)(i + 2) * R.tstep) * TB_M;
+      const int64_t nr = min((int64_t)TB_M, R.nrows - p0);
+      if (nr > 0) hpc_prefetch_l2_bulk(R.rows + p0 * D, (uint32_t)(nr * D * 4));
+    }
+    if (use > 0 && !wait_warp(&m.afree[st], (use - 1) & 1u, m.abort, status, TB_WAIT_NS)) break;
+    unsigned char *ah = m.a + (size_t)st * 2 * Cfg::ATILE;
+    unsigned char *al = ah + Cfg::ATILE;
+#pragma unroll 1
+    for (int b0 = 0; b0 < LDS; b0 += BATCH) {
+      float4 v[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = (b0 + u) * 32 + lane;
+        const int r = 64 * cw + e / F4;
+        const int64_t row = row0 + r;
+        v[u] = row < R.nrows ? __ldg(reinterpret_cast<const float4 *>(R.rows + row * D) + e % F4)
+                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = (b0 + u) * 32 + lane;
+        const int r = 64 * cw + e / F4;
+        const int t = 4 * (e % F4);
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[u].x, v[u].y);
+        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[u].z, v[u].w);
+        const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[u].x - f01.x, v[u].y - f01.y);
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[u].z - f23.x, v[u].w - f23.y);
+        const uint32_t off = tb_koff((uint32_t)r, (uint32_t)t, TB_M);
+        *reinterpret_cast<uint2 *>(ah + off) = make_uint2(tb_bits(h01), tb_bits(h23));
+        *reinterpret_cast<uint2 *>(al + off) = make_uint2(tb_bits(l01), tb_bits(l23));
+      }
+    }
+    hpc_fence_proxy_async();  // the stage's generic writes, visible to the tensor core
+    __syncwarp();
+    if (lane == 0) hpc_mbar_arrive(&m.afull[st]);
+  }
+}
+
+// ---- MMA issuer (warp 2, one thread) ------------------------------------------
+template <int D, int NP>
+__device__ __forceinline__ void tb_mma(const TbSm &m, const TbRows &R, uint32_t gbase, int *status) {
+  using Cfg = TbCfg<D, NP>;
+  constexpr uint32_t idesc = hpc_umma_idesc(1u, 1u, Cfg::BANKW, TB_M);
+  constexpr uint32_t SBO = 8u * 128u;
+  const uint32_t BH = hpc_smem_u32(m.bh), BL = hpc_smem_u32(m.bl);
+  for (int i = 0; i < R.ntiles; ++i) {
+    const uint32_t g = gbase + (uint32_t)i;
+    const int st = (int)(g % Cfg::NSTAGE);
+    const uint32_t use = g / Cfg::NSTAGE;
+    if (!hpc_mbar_wait(&m.afull[st], use & 1u, m.abort, status, TB_WAIT_NS)) break;
+    hpc_tc_fence_after();
+    const uint32_t AH = hpc_smem_u32(m.a + (size_t)st * 2 * Cfg::ATILE);
+    const uint32_t AL = AH + Cfg::ATILE;
+    bool ok = true;
+    for (int p = 0; p < Cfg::PARTS; ++p) {
+      const int bk = Cfg::PARTS == 2 ? p : (int)(g & 1u);
+      const uint32_t v = Cfg::PARTS == 2 ? g : (g >> 1);
+      if (v > 0 && !hpc_mbar_wait(&m.acce[bk], (v - 1) & 1u, m.abort, status, TB_WAIT_NS)) {
+        ok = false;
+        break;
+      }
+      hpc_tc_fence_after();
+      const uint32_t dt = m.tmem + (uint32_t)(bk * Cfg::BANKW);
+      const uint32_t boff = (uint32_t)(p * 256) * 128u;
+#pragma unroll
+      for (int ks = 0; ks < D / 16; ++ks) {
+        const uint32_t ka = (uint32_t)(ks >> 2) * TB_M * 128u + (uint32_t)(ks & 3) * 32u;
+        const uint32_t kb = (uint32_t)(ks >> 2) * NP * 128u + boff + (uint32_t)(ks & 3) * 32u;
+        const uint64_t ah = hpc_umma_desc(AH + ka, 16u, SBO, 2u);
+        const uint64_t al = hpc_umma_desc(AL + ka, 16u, SBO, 2u);
+        const uint64_t bh = hpc_umma_desc(BH + kb, 16u, SBO, 2u);
+        const uint64_t bl = hpc_umma_desc(BL + kb, 16u, SBO, 2u);
+        hpc_mma_bf16(dt, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        hpc_mma_bf16(dt, ah, bl, idesc, 1u);
+        hpc_mma_bf16(dt, al, bh, idesc, 1u);
+      }
+      hpc_mma_commit(&m.accf[bk]);
+    }
+    hpc_mma_commit(&m.afree[st]);
+    if (!ok) break;
+  }
+}
+
+// Drains the MMA issuer's work before TMEM is freed (one thread).
+__device__ __forceinline__ void tb_drain(const TbSm &m, uint32_t drain_use, int *status) {
+  int no_abort = 0;
+  hpc_mma_commit(m.drain);
+  hpc_mbar_wait(m.drain, drain_use & 1u, (volatile int *)&no_abort, status, TB_DRAIN_NS);
+}
+
+// Exact centroid block (hpc_cent_smem layout: -2c rows of hpc_cstride(D)
+// floats, then (||c||^2, 0) pairs) in global memory.
+template <int D>
+__device__ __forceinline__ hpc_cent_smem tb_gcs(float *gcent, int k, float cmax, int live) {
+  hpc_cent_smem cs;
+  hpc_cent_bind(cs, reinterpret_cast<unsigned char *>(gcent), D, k);
+  cs.cmax = cmax;
+  cs.live = live;
+  return cs;
+}
+
+// ---- epilogue (warps 3-18) ----------------------------------------------------
+// Folds every tile's columns, and finishes the tiles whose turn it is: for
+// each row `fin(i, r, row, valid, j1, j2, d1, d2)` is called by the whole
+// warp (lane l holds row 32 q + l of the tile).
+template <int D, int NP, typename Fin>
+__device__ __forceinline__ void tb_epilogue(const TbSm &m, const TbRows &R, uint32_t gbase, int kp, int *status,
+                            Fin fin) {
+  using Cfg = TbCfg<D, NP>;
+  constexpr int IB = Cfg::IB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = (warp - TB_EPI0) >> 2, q = warp & 3;
+  const int r_in = 32 * q + lane;
+  const int col0 = e * Cfg::CPW;
+  const int part = Cfg::PARTS == 2 ? col0 / 256 : 0;
+  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+  for (int i = 0; i < R.ntiles; ++i) {
+    const uint32_t g = gbase + (uint32_t)i;
+    const int bk = Cfg::PARTS == 2 ? part : (int)(g & 1u);
+    const uint32_t v = Cfg::PARTS == 2 ? g : (g >> 1);
+    const int xb = (int)(g % TB_NX);
+    const uint32_t xu = g / TB_NX;
+    const bool ok = wait_warp(&m.accf[bk], v & 1u, m.abort, status, TB_WAIT_NS);
+    float d1 = __int_as_float(0x7f7fffff), d2 = d1, e1 = d1, e2 = d1;
+    if (ok) {
+      hpc_tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < Cfg::CPW / 32; ++c) {
+        const int cb = col0 + 32 * c;
+        if (cb >= kp) break;  // same for the whole warp
+        float acc[32];
+        hpc_tmem_ld32(m.tmem + lane_base + (uint32_t)(bk * Cfg::BANKW + cb - part * 256), acc);
+#pragma unroll
+        for (int jj = 0; jj < 32; jj += 4) {
+          const float4 cn = *reinterpret_cast<const float4 *>(m.cn + cb + jj);
+          const int j = cb + jj;
+          float &t1 = (jj & 4) ? e1 : d1, &t2 = (jj & 4) ? e2 : d2;
+          hpc_top2_fold4(t1, t2, hpc_key_b<IB>(cn.x + acc[jj], j),
+                         hpc_key_b<IB>(cn.y + acc[jj + 1], j + 1),
+                         hpc_key_b<IB>(cn.z + acc[jj + 2], j + 2),
+                         hpc_key_b<IB>(cn.w + acc[jj + 3], j + 3));
+        }
+      }
+      d2 = hpc_min3(d2, e2, fmaxf(d1, e1));
+      d1 = fminf(d1, e1);
+    }
+    hpc_tc_fence_before();
+    __syncwarp();
+    if (lane == 0) hpc_mbar_arrive(&m.acce[bk]);  // this warp's columns are in registers
+    if (!ok) break;
+    if (xu > 0 && !wait_warp(&m.xdone[xb], (xu - 1) & 1u, m.abort, status, TB_WAIT_NS)) break;
+    m.xch[(xb * 4 + e) * TB_M + r_in] = make_float2(d1, d2);
+    __syncwarp();
+    if (lane == 0) hpc_mbar_arrive(&m.xready[xb]);
+    if ((int)(g & 3u) != e) continue;
+    if (!wait_warp(&m.xready[xb], xu & 1u, m.abort, status, TB_WAIT_NS)) break;
+    {
+      const float2 p0 = m.xch[(xb * 4) * TB_M + r_in];
+      d1 = p0.x;
+      d2 = p0.y;
+#pragma unroll
+      for (int o = 1; o < 4; ++o) {
+        const float2 po = m.xch[(xb * 4 + o) * TB_M + r_in];
+        d2 = hpc_min3(d2, po.y, fmaxf(d1, po.x));
+        d1 = fminf(d1, po.x);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) hpc_mbar_arrive(&m.xdone[xb]);
+    const int64_t row0 = (R.tile0 + (int64_t)i * R.tstep) * TB_M;
+    const int64_t row = row0 + r_in;
+    const bool valid = row < R.nrows;
+    const int j1 = min(__float_as_int(d1) & ((1 << IB) - 1), kp - 1);
+    const int j2 = min(__float_as_int(d2) & ((1 << IB) - 1), kp - 1);
+    fin(row0 + 32 * q, row, valid, j1, j2, d1, d2);
+  }
+}
+
+// ||x||^2 and the objective's FP32 direct-form distance to the centroid
+// whose -2c row is cm (two interleaved partial sums, relative error
+// <= (D/2 + 4) u), in one read of the row.  Centroid rows are read through
+// L2 (__ldcg): the exact block is rewritten between Lloyd iterations.
+template <int D>
+__device__ __forceinline__ void tb_norm_direct(const float *__restrict__ x, const float *cm,
+                                               float *nx, float *dd) {
+  float2 sx = make_float2(0.0f, 0.0f), sd = make_float2(0.0f, 0.0f);
+  const float2 half = make_float2(0.5f, 0.5f);
+#pragma unroll 4
+  for (int t = 0; t < D; t += 4) {
+    const float4 xv = __ldg(reinterpret_cast<const float4 *>(x + t));
+    const float4 cv = __ldcg(reinterpret_cast<const float4 *>(cm + t));
+    const float2 x01 = make_float2(xv.x, xv.y), x23 = make_float2(xv.z, xv.w);
+    sx = hpc_fma2(x01, x01, sx);
+    sx = hpc_fma2(x23, x23, sx);
+    const float2 e01 = hpc_fma2(half, make_float2(cv.x, cv.y), x01);
+    const float2 e23 = hpc_fma2(half, make_float2(cv.z, cv.w), x23);
+    sd = hpc_fma2(e01, e01, sd);
+    sd = hpc_fma2(e23, e23, sd);
+  }
+  *nx = sx.x + sx.y;
+  *dd = sd.x + sd.y;
+}
+
+template <int D>
+__device__ __forceinline__ float tb_direct(const float *__restrict__ x, const float *cm) {
+  float nx, dd;
+  tb_norm_direct<D>(x, cm, &nx, &dd);
+  return dd;
+}
+
+// Exact assignment of one row by the whole warp (every lane passes the same
+// row; lanes take centroids lane, lane + 32, ...): FP32 direct form in
+// dimension order with its relative bound (D + 3) u, then, if the two best
+// are not separated, FP64 in the oracle's operation order, ties to the
+// lowest index.  The row streams from memory (no D registers per lane).
+template <int D>
+__device__ __forceinline__ int tb_rescore(const float *__restrict__ x, const hpc_cent_smem &cs) {
+  constexpr int CS = hpc_cstride(D);
+  const int lane = threadIdx.x & 31;
+  float a1 = __int_as_float(0x7f800000), a2 = a1;
+  int ja = 0x7fffffff;
+  for (int j = lane; j < cs.kp; j += 32) {
+    if (__ldcg(&cs.cnz[j].x) >= HPC_DEAD) continue;
+    const float *cm = cs.cm + (size_t)j * CS;
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int t = 0; t < D; t += 4) {
+      const float4 xv = __ldg(reinterpret_cast<const float4 *>(x + t));
+      const float4 cv = __ldcg(reinterpret_cast<const float4 *>(cm + t));
+      float df = __fmaf_rn(0.5f, cv.x, xv.x);
+      acc = __fmaf_rn(df, df, acc);
+      df = __fmaf_rn(0.5f, cv.y, xv.y);
+      acc = __fmaf_rn(df, df, acc);
+      df = __fmaf_rn(0.5f, cv.z, xv.z);
+      acc = __fmaf_rn(df, df, acc);
+      df = __fmaf_rn(0.5f, cv.w, xv.w);
+      acc = __fmaf_rn(df, df, acc);
+    }
+    if (acc < a1) {
+      a2 = a1;
+      a1 = acc;
+      ja = j;
+    } else {
+      a2 = fminf(a2, acc);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+    const int jb = __shfl_xor_sync(0xffffffffu, ja, o);
+    const float b2 = __shfl_xor_sync(0xffffffffu, a2, o);
+    hpc_merge_top2(a1, ja, a2, b1, jb, b2);
+  }
+  const float bound = (float)(D + 3) * HPC_U32 * 1.001f * (a1 + a2);
+  if (a2 - a1 > bound) return ja < cs.kp ? ja : 0;
+  double b = __longlong_as_double(0x7ff0000000000000ll);
+  int jb = 0x7fffffff;
+  for (int j = lane; j < cs.kp; j += 32) {
+    if (__ldcg(&cs.cnz[j].x) >= HPC_DEAD) continue;
+    const float *cm = cs.cm + (size_t)j * CS;
+    double acc = 0.0;
+    for (int t = 0; t < D; ++t) {
+      const double c = -0.5 * (double)__ldcg(cm + t);
+      const double diff = __dsub_rn((double)__ldg(x + t), c);
+      acc = __dadd_rn(acc, __dmul_rn(diff, diff));
+    }
+    if (acc < b) {
+      b = acc;
+      jb = j;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, b, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
+    if (ob < b || (ob == b && oj < jb)) {
+      b = ob;
+      jb = oj;
+    }
+  }
+  return jb < cs.kp ? jb : 0;
+}
+
+// The exact stages of one row (whole warp; lane l's row is row0w + l).
+// Returns the exact nearest centroid in *j_out and its FP32 direct-form
+// distance in *dd_out; false for a non-finite row (status recorded).
+template <int D, int IB>
+__device__ __forceinline__ bool tb_exact(const float *__restrict__ rows, int64_t row0w, int64_t row,
+                                         bool valid, int j1, int j2, float d1, float d2,
+                                         const hpc_cent_smem &gcs, int *status, int *j_out,
+                                         float *dd_out) {
+  constexpr int CS = hpc_cstride(D);
+  const int lane = threadIdx.x & 31;
+  const bool found = d1 < HPC_DEAD * 0.5f;
+  if (!found) j1 = 0;
+  const float *xg = rows + (valid ? row : 0) * D;
+  float nx = 0.0f, dd = 0.0f;
+  if (valid) tb_norm_direct<D>(xg, gcs.cm + (size_t)j1 * CS, &nx, &dd);
+  const float rad = sqrtf(nx) * 1.0001f + gcs.cmax * 1.0001f;
+  float win = 2.0f * TB_E_REL * rad * rad;
+  win += 1.0001f * ldexpf(1.0f, IB - 22) * (fabsf(d1) + fabsf(d2));  // keys
+  bool ok = valid;
+  if (valid && !(found && isfinite(nx) && isfinite(win))) {
+    hpc_status_set(status, HPC_ERR_NONFINITE);
+    ok = false;
+  }
+  constexpr float rho = (float)(D + 3) * HPC_U32 * 1.001f;  // FP32 direct-form bound
+  bool full = false;
+  if (ok && !(d2 - d1 > win)) {
+    // the two nearest by the tensor-core values, exactly; every other
+    // centroid is at least ||x||^2 + d2 - E away
+    const bool has2 = d2 < HPC_DEAD * 0.5f && j2 != j1;
+    const float ex2 = has2 ? tb_direct<D>(xg, gcs.cm + (size_t)j2 * CS) : __int_as_float(0x7f800000);
+    const float E = 0.5f * win;
+    const float others = nx * (1.0f - (float)(D + 2) * HPC_U32 * 1.01f) + d2 - E -
+                         4.0f * HPC_U32 * (nx + fabsf(d2) + E);
+    const bool lo1 = dd < ex2 || (dd == ex2 && j1 < j2);
+    const float lo = lo1 ? dd : ex2, hi = lo1 ? ex2 : dd;
+    if (lo * (1.0f + rho) < others && hi * (1.0f - rho) > lo * (1.0f + rho)) {
+      if (!lo1) {
+        j1 = j2;
+        dd = ex2;
+      }
+    } else {
+      full = true;  // a third candidate, or a tie FP32 cannot split
+    }
+  }
+  unsigned mfull = __ballot_sync(0xffffffffu, full);
+  while (mfull) {
+    const int src = __ffs(mfull) - 1;
+    mfull &= mfull - 1;
+    const int j = tb_rescore<D>(rows + (row0w + src) * D, gcs);
+    if (lane == src && j != j1) {
+      j1 = j;
+      dd = tb_direct<D>(xg, gcs.cm + (size_t)j1 * CS);
+    }
+  }
+  if (ok && !isfinite(dd)) {
+    hpc_status_set(status, HPC_ERR_NONFINITE);
+    ok = false;
+  }
+  *j_out = j1;
+  *dd_out = dd;
+  return ok;
+}
+
+// One pass of the pipeline over a CTA's tiles (all 608 threads call it).
+template <int D, int NP, typename Fin>
+__device__ __forceinline__ void tb_pass(const TbSm &m, const TbRows &R, uint32_t gbase, int kp, int *status,
+                        Fin fin) {
+  const int warp = threadIdx.x >> 5;
+  if (warp < TB_CONV) {
+    tb_convert<D, NP>(m, R, gbase, status);
+  } else if (warp == TB_MMAW) {
+    if ((threadIdx.x & 31) == 0) tb_mma<D, NP>(m, R, gbase, status);
+    __syncwarp();
+  } else {
+    tb_epilogue<D, NP>(m, R, gbase, kp, status, fin);
+  }
+}
+
+// B (split c'), the norms and the flags from centroid values given by
+// `val(j, t0, c[])` (PER = D / 32 values of row j from dim t0), for rows
+// j < k that are live; rows beyond k and dead rows get zeros and HPC_DEAD.
+// Warp-per-row; returns through s_nmax / s_live (shared) the largest squared
+// norm (bits) and the live count.  When `ex` is set (the task's first CTA)
+// the exact block (gcent) is written too.
+template <int D, int NP, typename Val>
+__device__ __forceinline__ void tb_build_b(const TbSm &m, int k, float *gcent, bool ex, unsigned *s_nmax,
+                           unsigned *s_live, Val val) {
+  constexpr int PER = D / 32;
+  constexpr int CS = hpc_cstride(D);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = TB_THREADS / 32;
+  const int kp = (k + 1) & ~1;
+  float2 *gcnz = reinterpret_cast<float2 *>(gcent + (size_t)kp * CS);
+  for (int j = warp; j < NP; j += nw) {
+    float c[PER];
+    bool live = j < k && !m.dead[j];
+    if (live) {
+      live = val(j, lane * PER, c);  // false: the centroid just became empty
+    }
+    if (!live) {
+#pragma unroll
+      for (int u = 0; u < PER; ++u) c[u] = 0.0f;
+    }
+    tb_store_b<PER, NP>(m, j, lane * PER, c);
+    float nn = 0.0f;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) nn = fmaf(c[u], c[u], nn);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (ex && live && j < kp) {
+#pragma unroll
+      for (int u = 0; u < PER; ++u) gcent[(size_t)j * CS + lane * PER + u] = -2.0f * c[u];
+    }
+    if (lane == 0) {
+      m.cn[j] = live ? nn : HPC_DEAD;
+      if (ex && j < kp) gcnz[j] = make_float2(live ? nn : HPC_DEAD, 0.0f);
+      if (live) {
+        atomicMax(s_nmax, __float_as_uint(nn));
+        atomicAdd(s_live, 1u);
+      }
+    }
+  }
+  hpc_fence_proxy_async();  // B's generic writes, visible to the tensor core
+}
+
+// ---- Lloyd ----------------------------------------------------------------------
+struct TclArgs {
+  int W;
+  hpc_lloyd_task single;
+  const hpc_lloyd_task *tasks;
+  const int *block_task;
+  int max_iter;
+  double tol;
+  int *status;
+  uint32_t *round_advance;
+};
+
+template <int D, int NP>
+__global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
+  using Cfg = TbCfg<D, NP>;
+  constexpr int CS = hpc_cstride(D);
+  constexpr int PER = D / 32;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ double s_dsum[32];
+  __shared__ double s_f;
+  __shared__ int s_done, s_abort;
+  __shared__ unsigned s_umax, s_cmax, s_nmax, s_live;
+  __shared__ uint32_t s_tmem;
+
+  if (a.round_advance && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.round_advance, 1u);
+  const hpc_lloyd_task tk = a.W == 1 ? a.single : a.tasks[a.block_task[blockIdx.x]];
+  const int k = tk.k, kp = (k + 1) & ~1;
+  const int64_t s = tk.s;
+  const int G = tk.nblocks, lb = (int)blockIdx.x - tk.block0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char *base =
+      reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  TbSm m = tb_bind<D, NP>(base, &s_abort);
+
+  if (threadIdx.x == 0) {
+    tb_init_barriers<D, NP>(m);
+    s_abort = 0;
+    s_umax = s_cmax = s_nmax = s_live = 0u;
+  }
+  if (warp == TB_MMAW) hpc_tmem_alloc(&s_tmem, Cfg::TCOLS);
+  for (int j = threadIdx.x; j < 512; j += TB_THREADS) m.dead[j] = (j >= k) || tk.deg[j] != 0;
+  hpc_tc_fence_before();
+  __syncthreads();
+  hpc_tc_fence_after();
+  m.tmem = s_tmem;
+
+  // Phase 0: largest |x| of the sample (fixed-point grid, non-finite rows),
+  // zero sums, B from the starting centroids
+  const int64_t ntiles = (s + TB_M - 1) / TB_M;
+  {
+    unsigned mx = 0u;
+    for (int64_t e = (int64_t)lb * TB_THREADS + threadIdx.x; e < s * D;
+         e += (int64_t)G * TB_THREADS) {
+      const unsigned b = __float_as_uint(tk.S[e]) & 0x7fffffffu;
+      mx = b > mx ? b : mx;
+    }
+    atomicMax(&s_umax, mx);
+    for (int64_t e = (int64_t)lb * TB_THREADS + threadIdx.x; e < (int64_t)k * D;
+         e += (int64_t)G * TB_THREADS)
+      tk.gsum[e] = 0ull;
+    for (int j = lb * TB_THREADS + threadIdx.x; j < k; j += G * TB_THREADS) tk.gcount[j] = 0u;
+  }
+  __syncthreads();
+  tb_build_b<D, NP>(m, k, tk.gcent, lb == 0, &s_nmax, &s_live, [&](int j, int t0, float(&c)[PER]) {
+    unsigned mc = 0u;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      c[u] = tk.C[(int64_t)j * D + t0 + u];
+      const unsigned b = __float_as_uint(c[u]) & 0x7fffffffu;
+      mc = b > mc ? b : mc;
+    }
+    atomicMax(&s_cmax, mc);
+    return true;
+  });
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(tk.gmaxabs, s_umax);
+  float cmax = sqrtf(__uint_as_float(s_nmax));
+  int live = (int)s_live;
+  bool run = hpc_grid_sync(tk.bar, a.status, (unsigned)G);
+  const unsigned mabs = run ? __ldcg(tk.gmaxabs) : 0u;
+  if (run && (mabs >= 0x7f800000u || s_cmax >= 0x7f800000u)) {
+    if (threadIdx.x == 0) hpc_status_set(a.status, HPC_ERR_NONFINITE);
+    run = false;
+  }
+  if (run && live == 0) {
+    if (threadIdx.x == 0) hpc_status_set(a.status, HPC_ERR_DEGENERATE_ALL);
+    run = false;
+  }
+  int Fs = 126;
+  if (mabs != 0u) Fs = min(126, 62 - hpc_bit_length(s) - hpc_frexp_exp(__uint_as_float(mabs)));
+  const float qscale = hpc_pow2f(Fs);
+  int Fo = 126;
+  {
+    const unsigned mm = max(mabs, s_cmax);
+    if (mm != 0u && mm < 0x7f800000u)
+      Fo = min(126, 59 - hpc_bit_length(s) - hpc_bit_length(D) - 2 * hpc_frexp_exp(__uint_as_float(mm)));
+    Fo = max(Fo, -126);
+  }
+  const float oscale = hpc_pow2f(Fo);
+  const double oinv = hpc_pow2d(-Fo);
+
+  TbRows R;
+  R.rows = tk.S;
+  R.nrows = s;
+  R.tile0 = lb;
+  R.tstep = G;
+  R.ntiles = lb < ntiles ? (int)((ntiles - 1 - lb) / G + 1) : 0;
+  uint32_t gbase = 0, drains = 0;
+  double f_prev = 0.0;
+  for (int it = 0; run; ++it) {
+    // Phase A: assignment of the CTA's rows, sums of the rows that moved
+    float fs_hi = 0.0f, fs_lo = 0.0f;
+    const hpc_cent_smem gcs = tb_gcs<D>(tk.gcent, k, cmax, live);
+    tb_pass<D, NP>(m, R, gbase, kp, a.status,
+                   [&](int64_t row0w, int64_t row, bool valid, int j1, int j2, float d1, float d2) {
+      int j = 0;
+      float dd = 0.0f;
+      const bool ok =
+          tb_exact<D, Cfg::IB>(tk.S, row0w, row, valid, j1, j2, d1, d2, gcs, a.status, &j, &dd);
+      if (ok) hpc_sum2_add(fs_hi, fs_lo, dd);
+      int old = -1;
+      bool moved = false;
+      if (ok) {
+        old = it > 0 ? tk.plab[row] : -1;
+        moved = old != j;
+        tk.plab[row] = j;
+      }
+      unsigned mv = __ballot_sync(0xffffffffu, moved);
+      while (mv) {
+        const int src = __ffs(mv) - 1;
+        mv &= mv - 1;
+        const int jn = __shfl_sync(0xffffffffu, j, src);
+        const int jo = __shfl_sync(0xffffffffu, old, src);
+        const float *xp = tk.S + (row0w + src) * D + lane * PER;
+        float xv[PER];
+        if constexpr (PER == 4) {
+          const float4 q4 = __ldg(reinterpret_cast<const float4 *>(xp));
+          xv[0] = q4.x;
+          xv[1] = q4.y;
+          xv[2] = q4.z;
+          xv[3] = q4.w;
+        } else {
+          const float2 q2 = __ldg(reinterpret_cast<const float2 *>(xp));
+          xv[0] = q2.x;
+          xv[1] = q2.y;
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const long long qv = __float2ll_rn(xv[u] * qscale);
+          atomicAdd(&tk.gsum[(size_t)jn * D + lane * PER + u], (unsigned long long)qv);
+          if (jo >= 0) atomicAdd(&tk.gsum[(size_t)jo * D + lane * PER + u], (unsigned long long)(-qv));
+        }
+        if (lane == 0) {
+          atomicAdd(&tk.gcount[jn], 1u);
+          if (jo >= 0) atomicSub(&tk.gcount[jo], 1u);
+        }
+      }
+      if (ok && tk.labels && tk.labels != tk.plab) tk.labels[row] = j;
+    });
+    gbase += (uint32_t)R.ntiles;
+    __syncthreads();
+    if (s_abort) break;
+    // the objective partial on the grid 2^-Fo, summed over the block in integers
+    const unsigned long long bq = hpc_block_sum_u64(
+        (unsigned long long)(__float2ll_rn(fs_hi * oscale) + __float2ll_rn(fs_lo * oscale)),
+        reinterpret_cast<unsigned long long *>(s_dsum));
+    const int buf = it % 3;
+    if (threadIdx.x == 0 && bq != 0ull) atomicAdd(tk.gobj + buf, bq);
+    if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) break;
+    // Phase B: objective, stop test, new centroids (every CTA, identical)
+    if (threadIdx.x == 0) {
+      const double fo = (double)(long long)__ldcg(tk.gobj + buf) * oinv;
+      s_f = fo;
+      s_done = (it > 0 && (f_prev == 0.0 || (f_prev - fo) < a.tol * f_prev)) || it == a.max_iter;
+      s_nmax = 0u;
+      s_live = 0u;
+    }
+    __syncthreads();
+    const double f = s_f;
+    if (s_done) {
+      if (lb == 0) {
+        if (threadIdx.x == 0) {
+          *tk.f_out = f;
+          if (tk.iters_out) *tk.iters_out = it;
+        }
+        if (tk.fhat) hpc_incumbent_block(tk, D, f, it);
+      }
+      break;
+    }
+    tb_build_b<D, NP>(m, k, tk.gcent, lb == 0, &s_nmax, &s_live,
+                      [&](int j, int t0, float(&c)[PER]) {
+      const unsigned cnt = __ldcg(tk.gcount + j);
+      if (cnt == 0u) {  // emptied: degenerate for the rest of the run
+        __syncwarp();
+        if (lane == 0) {
+          m.dead[j] = 1;
+          if (lb == 0) tk.deg[j] = 1;
+        }
+        return false;
+      }
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const long long q = (long long)__ldcg(tk.gsum + (size_t)j * D + t0 + u);
+        c[u] = hpc_mean_f32(q, cnt, Fs);
+        if (lb == 0) tk.C[(int64_t)j * D + t0 + u] = c[u];
+      }
+      return true;
+    });
+    if (lb == 0 && threadIdx.x == 0) tk.gobj[(it + 2) % 3] = 0ull;
+    __syncthreads();
+    cmax = sqrtf(__uint_as_float(s_nmax));
+    live = (int)s_live;
+    f_prev = f;
+    if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) break;
+  }
+  // drain: no MMA may still target this CTA's TMEM or shared memory
+  __syncthreads();
+  if (warp == TB_MMAW && lane == 0) tb_drain(m, drains++, a.status);
+  hpc_tc_fence_before();
+  __syncthreads();
+  if (warp == TB_MMAW) {
+    hpc_tc_fence_after();
+    hpc_tmem_dealloc(m.tmem, Cfg::TCOLS);
+  }
+}
+
+// ---- full-data objective ----------------------------------------------------------
+struct TcbArgs {
+  const float *X;
+  int64_t n;
+  int k;
+  const float *C;
+  const uint8_t *deg;
+  float *gcent;
+  const float *gmeta;  // [0] max ||c||, [1] live count (int bits)
+  double *f_out;
+  int32_t *labels;
+  int *status;
+  double *part;
+  unsigned *done_count;
+};
+
+// One block: the exact centroid block and its max norm / live count.
+template <int D>
+__global__ void tcb_prep_kernel(const float *__restrict__ C, const uint8_t *__restrict__ deg, int k,
+                                float *gcent, float *gmeta) {
+  __shared__ float s_red[2];
+  hpc_cent_smem cs;
+  hpc_cent_bind(cs, reinterpret_cast<unsigned char *>(gcent), D, k);
+  hpc_load_centroids<D>(cs, C, deg, k, D, s_red);
+  if (threadIdx.x == 0) {
+    gmeta[0] = cs.cmax;
+    gmeta[1] = __int_as_float(cs.live);
+  }
+}
+
+template <int D, int NP>
+__global__ void __launch_bounds__(TB_THREADS, 1) tcb_objective_kernel(TcbArgs a) {
+  using Cfg = TbCfg<D, NP>;
+  constexpr int PER = D / 32;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ double s_dsum[32];
+  __shared__ bool s_last;
+  __shared__ int s_abort;
+  __shared__ unsigned s_nmax, s_live;
+  __shared__ uint32_t s_tmem;
+  const int warp = threadIdx.x >> 5;
+  unsigned char *base =
+      reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  TbSm m = tb_bind<D, NP>(base, &s_abort);
+  const int k = a.k, kp = (k + 1) & ~1;
+  if (threadIdx.x == 0) {
+    tb_init_barriers<D, NP>(m);
+    s_abort = 0;
+    s_nmax = s_live = 0u;
+  }
+  if (warp == TB_MMAW) hpc_tmem_alloc(&s_tmem, Cfg::TCOLS);
+  for (int j = threadIdx.x; j < 512; j += TB_THREADS)
+    m.dead[j] = (j >= k) || (a.deg != nullptr && a.deg[j] != 0);
+  hpc_tc_fence_before();
+  __syncthreads();
+  hpc_tc_fence_after();
+  m.tmem = s_tmem;
+  tb_build_b<D, NP>(m, k, a.gcent, false, &s_nmax, &s_live, [&](int j, int t0, float(&c)[PER]) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) c[u] = a.C[(int64_t)j * D + t0 + u];
+    return true;
+  });
+  __syncthreads();
+  const hpc_cent_smem gcs = tb_gcs<D>(a.gcent, k, a.gmeta[0], __float_as_int(a.gmeta[1]));
+  const bool run = gcs.live > 0;
+  if (!run && a.n > 0 && threadIdx.x == 0) hpc_status_set(a.status, HPC_ERR_DEGENERATE_ALL);
+  const int64_t ntiles = (a.n + TB_M - 1) / TB_M;
+  TbRows R;
+  R.rows = a.X;
+  R.nrows = a.n;
+  R.tile0 = blockIdx.x;
+  R.tstep = gridDim.x;
+  R.ntiles = run && (int64_t)blockIdx.x < ntiles
+                 ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  float fs_hi = 0.0f, fs_lo = 0.0f;
+  tb_pass<D, NP>(m, R, 0u, kp, a.status,
+                 [&](int64_t row0w, int64_t row, bool valid, int j1, int j2, float d1, float d2) {
+    int j = 0;
+    float dd = 0.0f;
+    if (tb_exact<D, Cfg::IB>(a.X, row0w, row, valid, j1, j2, d1, d2, gcs, a.status, &j, &dd)) {
+      hpc_sum2_add(fs_hi, fs_lo, dd);
+      if (a.labels) a.labels[row] = j;
+    }
+  });
+  __syncthreads();
+  if (warp == TB_MMAW && (threadIdx.x & 31) == 0 && R.ntiles > 0) tb_drain(m, 0u, a.status);
+  const double bsum = hpc_block_sum((double)fs_hi + (double)fs_lo, s_dsum);
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x] = bsum;
+    __threadfence();
+    const unsigned prev = atomicAdd(a.done_count, 1u);
+    s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    const double f = hpc_block_sum_array(a.part, (int)gridDim.x, s_dsum);
+    if (threadIdx.x == 0) {
+      *a.f_out = (!run && a.n > 0) ? __longlong_as_double(0x7ff8000000000000ll) : f;
+      *a.done_count = 0u;
+    }
+  }
+  hpc_tc_fence_before();
+  __syncthreads();
+  if (warp == TB_MMAW) {
+    hpc_tc_fence_after();
+    hpc_tmem_dealloc(m.tmem, Cfg::TCOLS);
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------
+int tb_np(int k) { return k <= 128 ? 128 : k <= 256 ? 256 : 512; }
+
+template <int D, int NP>
+int tcl_plan_t(const hpc_launch &L, LloydLaunch &h) {
+  using Cfg = TbCfg<D, NP>;
+  auto kern = tcl_lloyd_kernel<D, NP>;
+  const size_t smem = Cfg::TOTAL;
+  if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return HPC_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TB_THREADS, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return HPC_ERR_UNSUPPORTED;
+  // one CTA per SM: it holds the tensor memory its pipeline needs
+  int64_t total = L.num_sms;
+  if (total > h.max_blocks) total = h.max_blocks;
+  int64_t want = 0;
+  for (int w = 0; w < h.W; ++w) want += (h.tasks[w].s + TB_M - 1) / TB_M;
+  if (total > want) total = want;
+  if (h.W > total || h.W > HPC_MAX_TASKS) return HPC_ERR_UNSUPPORTED;
+  std::vector<int64_t> rows(h.W), work(h.W);
+  std::vector<int> b0(h.W), nb(h.W);
+  for (int w = 0; w < h.W; ++w) {
+    rows[w] = h.tasks[w].s;
+    work[w] = h.tasks[w].s * (int64_t)h.tasks[w].k;
+  }
+  hpc_split_blocks(h.W, rows.data(), work.data(), (int64_t)TB_M, total, b0.data(), nb.data());
+  int64_t grid = 0;
+  for (int w = 0; w < h.W; ++w) {
+    if (nb[w] > h.task_blocks) nb[w] = (int)h.task_blocks;
+    h.tasks[w].block0 = (int)grid;
+    h.tasks[w].nblocks = nb[w];
+    if (h.W > 1)
+      for (int b = 0; b < nb[w]; ++b) h.block_task_host[grid + b] = w;
+    grid += nb[w];
+  }
+  h.grid = grid;
+  h.smem = smem;
+  h.smem_sums = 0;
+  h.xstage = 0;
+  h.form = HPC_SEARCH_SPLIT_BF16;
+  return HPC_OK;
+}
+
+template <int D, int NP>
+int tcl_run_t(const hpc_launch &L, const LloydLaunch &h) {
+  auto kern = tcl_lloyd_kernel<D, NP>;
+  TclArgs a;
+  a.W = h.W;
+  a.single = h.tasks[0];
+  a.tasks = h.tasks_dev;
+  a.block_task = h.block_task_dev;
+  a.max_iter = h.max_iter;
+  a.tol = h.tol;
+  a.status = h.status;
+  a.round_advance = h.round_advance;
+  void *args[] = {&a};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)h.grid),
+                                                    dim3(TB_THREADS), args, h.smem, L.stream);
+  return e == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
+}
+
+template <int D, int NP>
+int tcb_objective_t(const hpc_launch &L, const ObjArgsHost &h) {
+  using Cfg = TbCfg<D, NP>;
+  auto kern = tcb_objective_kernel<D, NP>;
+  const size_t smem = Cfg::TOTAL;
+  if (smem > (size_t)L.smem_optin) return HPC_ERR_UNSUPPORTED;
+  const size_t gbytes = hpc_tcl_gcent_bytes(D, h.k);
+  if (!h.cent_scratch || h.cent_scratch_bytes < (int64_t)(gbytes + 256)) return HPC_ERR_UNSUPPORTED;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return HPC_ERR_CUDA;
+  float *gcent = reinterpret_cast<float *>(h.cent_scratch);
+  float *gmeta = reinterpret_cast<float *>(h.cent_scratch + gbytes);
+  tcb_prep_kernel<D><<<1, 256, 0, L.stream>>>(h.C, h.deg, h.k, gcent, gmeta);
+  if (cudaGetLastError() != cudaSuccess) return HPC_ERR_CUDA;
+  const int64_t ntiles = (h.n + TB_M - 1) / TB_M;
+  int64_t G = L.num_sms;
+  if (G > ntiles) G = ntiles;
+  if (G < 1) G = 1;
+  if (G > h.max_blocks) G = h.max_blocks;
+  TcbArgs a;
+  a.X = h.X;
+  a.n = h.n;
+  a.k = h.k;
+  a.C = h.C;
+  a.deg = h.deg;
+  a.gcent = gcent;
+  a.gmeta = gmeta;
+  a.f_out = h.f_out;
+  a.labels = h.labels;
+  a.status = h.status;
+  a.part = h.part;
+  a.done_count = h.done_count;
+  kern<<<(unsigned)G, TB_THREADS, smem, L.stream>>>(a);
+  return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
+}
+
+}  // namespace
+
+bool hpc_tcl_supported(int d, int kmax) {
+  return (d == 64 && kmax >= 1 && kmax <= 512) || (d == 128 && kmax >= 1 && kmax <= 256);
+}
+
+size_t hpc_tcl_gcent_bytes(int d, int k) {
+  const int kp = (k + 1) & ~1;
+  const int D = d <= 64 ? 64 : 128;
+  return (((size_t)kp * hpc_cstride(D) * 4 + (size_t)kp * 8) + 255) & ~(size_t)255;
+}
+
+int hpc_tcl_plan(const hpc_launch &L, LloydLaunch &h) {
+  if (!hpc_tcl_supported(h.d, h.kmax)) return HPC_ERR_UNSUPPORTED;
+  const int np = tb_np(h.kmax);
+  if (h.d == 64) {
+    if (np == 128) return tcl_plan_t<64, 128>(L, h);
+    if (np == 256) return tcl_plan_t<64, 256>(L, h);
+    return tcl_plan_t<64, 512>(L, h);
+  }
+  if (np == 128) return tcl_plan_t<128, 128>(L, h);
+  return tcl_plan_t<128, 256>(L, h);
+}
+
+int hpc_tcl_run(const hpc_launch &L, const LloydLaunch &h) {
+  const int np = tb_np(h.kmax);
+  if (h.d == 64) {
+    if (np == 128) return tcl_run_t<64, 128>(L, h);
+    if (np == 256) return tcl_run_t<64, 256>(L, h);
+    return tcl_run_t<64, 512>(L, h);
+  }
+  if (np == 128) return tcl_run_t<128, 128>(L, h);
+  return tcl_run_t<128, 256>(L, h);
+}
+
+int hpc_tcb_objective_launch(const hpc_launch &L, const ObjArgsHost &h) {
+  if (!hpc_tcl_supported(h.d, h.k) || h.n < 1) return HPC_ERR_UNSUPPORTED;
+  const int np = tb_np(h.k);
+  if (h.d == 64) {
+    if (np == 128) return tcb_objective_t<64, 128>(L, h);
+    if (np == 256) return tcb_objective_t<64, 256>(L, h);
+    return tcb_objective_t<64, 512>(L, h);
+  }
+  if (np == 128) return tcb_objective_t<128, 128>(L, h);
+  return tcb_objective_t<128, 256>(L, h);
+}

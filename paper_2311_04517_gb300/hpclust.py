@@ -26,9 +26,10 @@ HPC_ERR_DEGENERATE_ALL = -6
 HPC_ERR_UNSUPPORTED = -7
 HPC_FP32, HPC_BF16, HPC_FP8 = 0, 1, 2
 HPC_COMPETITIVE, HPC_COOPERATIVE, HPC_HYBRID = 0, 1, 2
-HPC_SEARCH_SIMT, HPC_SEARCH_SPLIT_TF32, HPC_SEARCH_TF32 = 0, 1, 2
+HPC_SEARCH_SIMT, HPC_SEARCH_SPLIT_TF32, HPC_SEARCH_TF32, HPC_SEARCH_SPLIT_BF16 = 0, 1, 2, 3
 SEARCH_NAMES = {HPC_SEARCH_SIMT: "simt", HPC_SEARCH_SPLIT_TF32: "split_tf32",
-                HPC_SEARCH_TF32: "tf32"}
+                HPC_SEARCH_TF32: "tf32", HPC_SEARCH_SPLIT_BF16: "split_bf16"}
+NFORMS = 4
 (HPC_PROBE_FFMA, HPC_PROBE_FFMA2, HPC_PROBE_DFMA, HPC_PROBE_FMIN, HPC_PROBE_L2_READ,
  HPC_PROBE_HBM_READ) = range(6)
 PROBES = {HPC_PROBE_FFMA: ("fp32 fma", "FMA/s"), HPC_PROBE_FFMA2: ("fp32x2 fma", "FMA/s"),
@@ -242,11 +243,12 @@ class Context:
         _need(C, torch.float32, "C", self.device)
         _need(degenerate, torch.uint8, "degenerate", self.device)
         form = ctypes.c_int32(-1)
-        ms = (ctypes.c_float * 3)()
+        ms = (ctypes.c_float * NFORMS)()
         self._check(self.lib.hpc_autotune_objective(self.h, _ptr(X), n, d, _ptr(C), k,
                                                     _ptr(degenerate), int(reps),
                                                     ctypes.byref(form), ms))
-        return int(form.value), {SEARCH_NAMES[i]: float(ms[i]) for i in range(3) if ms[i] >= 0}
+        return int(form.value), {SEARCH_NAMES[i]: float(ms[i]) for i in range(NFORMS)
+                                 if ms[i] >= 0}
 
     def autotune_objective_guided(self, X, C, params, degenerate=None, reps: int = 5,
                                   margin: float = 0.25):
@@ -260,11 +262,12 @@ class Context:
         _need(degenerate, torch.uint8, "degenerate", self.device)
         form = ctypes.c_int32(-1)
         timed = ctypes.c_int32(0)
-        ms = (ctypes.c_float * 3)()
+        ms = (ctypes.c_float * NFORMS)()
         self._check(self.lib.hpc_autotune_objective_guided(
             self.h, _ptr(X), n, d, _ptr(C), k, _ptr(degenerate), int(reps), _ptr(params),
             float(margin), ctypes.byref(form), ms, ctypes.byref(timed)))
-        return (int(form.value), {SEARCH_NAMES[i]: float(ms[i]) for i in range(3) if ms[i] >= 0},
+        return (int(form.value),
+                {SEARCH_NAMES[i]: float(ms[i]) for i in range(NFORMS) if ms[i] >= 0},
                 int(timed.value))
 
     def selftest_wait_timeout(self, limit_ns: int):

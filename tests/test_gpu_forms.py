@@ -1,5 +1,5 @@
 """Search-form control of the full-data objective: every form the library
-builds for a shape (CUDA cores, split TF32, TF32) against the CPU oracle,
+builds for a shape (CUDA cores, split TF32, TF32, split BF16) against the CPU oracle,
 the per-shape form table (hpc_set_objective_form) and the measured choice
 (hpc_autotune_objective).
 
@@ -16,7 +16,7 @@ from paper_2311_04517_gb300 import hpclust as H
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-6
-FORMS = (H.HPC_SEARCH_SIMT, H.HPC_SEARCH_SPLIT_TF32, H.HPC_SEARCH_TF32)
+FORMS = (H.HPC_SEARCH_SIMT, H.HPC_SEARCH_SPLIT_TF32, H.HPC_SEARCH_TF32, H.HPC_SEARCH_SPLIT_BF16)
 
 
 @pytest.fixture()
@@ -39,6 +39,8 @@ def built(d, k):
         ok.append(H.HPC_SEARCH_SPLIT_TF32)
     if (d in (16, 32, 64) and k <= 512) or (d == 128 and k <= 256):
         ok.append(H.HPC_SEARCH_TF32)
+    if (d == 64 and k <= 512) or (d == 128 and k <= 256):
+        ok.append(H.HPC_SEARCH_SPLIT_BF16)
     return ok
 
 

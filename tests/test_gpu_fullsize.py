@@ -110,7 +110,7 @@ def test_batching_workload_objective(ctx, k):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("form", [H.HPC_SEARCH_SIMT, H.HPC_SEARCH_TF32])
+@pytest.mark.parametrize("form", [H.HPC_SEARCH_SIMT, H.HPC_SEARCH_TF32, H.HPC_SEARCH_SPLIT_BF16])
 def test_large_workload_objective(ctx, form):
     # k = 500: the CUDA-core search (built-in choice) and the wide TF32 search
     # (four warpgroups over a tile's 512 accumulator columns)
@@ -133,10 +133,10 @@ def assert_centroids(Cg, Co, what=""):
     assert not bad.any(), f"{what}: {int(bad.sum())} centroid coordinates off"
 
 
-def replay_worker(ctx, X, wl, ws, batch, w, seed, rnd, f_new, iters, host_X=None):
+def oracle_worker(X, wl, ws, w, seed, rnd, host_X=None):
     """The oracle's replay of worker w's round from the all-degenerate start:
     its sample (indices from the oracle's Philox stream, rows gathered from
-    X), K-means++ and Lloyd; compared with the GPU round's results."""
+    X), K-means++ and Lloyd."""
     s, k = int(ws.s[w]), int(ws.k[w])
     if host_X is not None:
         S, _ = orc.draw_sample(host_X, seed, w, rnd, s)
@@ -144,12 +144,20 @@ def replay_worker(ctx, X, wl, ws, batch, w, seed, rnd, f_new, iters, host_X=None
         idx = orc.sample_indices(X.shape[0], seed, w, rnd, s)
         S = X[torch.from_numpy(idx).cuda()].cpu().numpy()
     kp = orc.kmeanspp(S, np.zeros((k, wl.d), np.float32), np.ones(k, np.uint8), 3, seed, w, rnd)
-    lo = orc.lloyd(S, kp["C"], kp["degenerate"])
+    return orc.lloyd(S, kp["C"], kp["degenerate"])
+
+
+def check_worker(lo, batch, w, f_new, iters):
     assert f_new[w] == pytest.approx(lo["f"], rel=RTOL), f"worker {w}"
     if int(iters[w]) == lo["iters"]:
         C, deg = batch.centroids(w)
         np.testing.assert_array_equal(deg.cpu().numpy(), lo["degenerate"])
         assert_centroids(C.cpu().numpy(), lo["C"], f"worker {w}")
+
+
+def replay_worker(ctx, X, wl, ws, batch, w, seed, rnd, f_new, iters, host_X=None):
+    lo = oracle_worker(X, wl, ws, w, seed, rnd, host_X)
+    check_worker(lo, batch, w, f_new, iters)
     return lo
 
 
@@ -162,19 +170,30 @@ def test_large_workload_round_sampled_workers(ctx):
     # same all-degenerate start.
     wl = synth.WORKLOADS["large"]
     ws = synth.worker_setup(wl)
-    assert not ctx.lloyd_schedule(int(ws.s.max()), wl.d, 500)["smem_sums"]
     X = synth.make_data(wl, "cuda")               # 2e8 x 64 float32, 51 GB
-    batch = H.Batch(wl.d, ws.s, ws.k, ws.group)
     seed, rnd = wl.seed, 0
-    H.hpc_round(ctx, X, batch, H.HPC_COMPETITIVE, seed, rnd)
-    ctx.check_status()
-    f_new = batch.f_new.cpu().numpy()
-    iters = batch.iters.cpu().numpy()
-    assert np.isfinite(f_new).all() and (iters >= 1).all()
-    # every worker's incumbent was replaced (the start is +inf)
-    assert batch.accepted.cpu().numpy().all()
-    for w in (int(np.argmin(ws.s)), int(np.argmax(ws.s))):
-        replay_worker(ctx, X, wl, ws, batch, w, seed, rnd, f_new, iters)
+    picks = (int(np.argmin(ws.s)), int(np.argmax(ws.s)))
+    replays = {w: oracle_worker(X, wl, ws, w, seed, rnd) for w in picks}
+    # both Lloyd searches: the CUDA cores (global fixed-point sums) and the
+    # split-BF16 tensor cores (incremental sums of the rows that moved)
+    for mode, form in ((0, "simt"), (2, "split_bf16")):
+        ctx.set_tensor_cores(mode)
+        try:
+            sched = ctx.lloyd_schedule(int(ws.s.max()), wl.d, 500)
+            assert not sched["smem_sums"] and sched["form"] == form, sched
+            batch = H.Batch(wl.d, ws.s, ws.k, ws.group)
+            H.hpc_round(ctx, X, batch, H.HPC_COMPETITIVE, seed, rnd)
+            ctx.check_status()
+        finally:
+            ctx.set_tensor_cores(2)
+        f_new = batch.f_new.cpu().numpy()
+        iters = batch.iters.cpu().numpy()
+        assert np.isfinite(f_new).all() and (iters >= 1).all()
+        # every worker's incumbent was replaced (the start is +inf)
+        assert batch.accepted.cpu().numpy().all()
+        for w in picks:
+            check_worker(replays[w], batch, w, f_new, iters)
+        del batch
     del X
     torch.cuda.empty_cache()
 

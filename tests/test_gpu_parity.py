@@ -310,24 +310,138 @@ def test_lloyd_parity(ctx, s, d, k, seed):
     lloyd_case(ctx, S, k, seed)
 
 
-@pytest.mark.parametrize("s,d,k,seed", [(20000, 64, 500, 11), (5000, 128, 256, 12),
-                                        (65536, 64, 500, 13)])
-def test_lloyd_parity_global_sums(ctx, s, d, k, seed):
-    # k x d x 8 bytes of per-block sums above what a block's shared memory
-    # holds (the large workload's k = 500 at d = 64): every block adds its
-    # rows' fixed-point coordinates straight into the global sums
-    sched = ctx.lloyd_schedule(s, d, k)
-    assert not sched["smem_sums"], sched
-    # a Zipf-weighted mixture like the large workload's (several centroids
-    # share the heavy components, light ones get few rows)
+def zipf_mixture(s, d, comps, seed):
+    """A Zipf-weighted mixture like the large workload's (several centroids
+    share the heavy components, light ones get few rows)."""
     rng = np.random.default_rng(seed)
-    comps = k
     mu = 4.0 * rng.standard_normal((comps, d))
     w = np.arange(1, comps + 1, dtype=np.float64) ** -1.1
     z = rng.choice(comps, s, p=w / w.sum())
     sd = rng.uniform(0.5, 2.0, comps)
-    S = (mu[z] + sd[z, None] * rng.standard_normal((s, d))).astype(np.float32)
-    lloyd_case(ctx, S, k, seed)
+    return (mu[z] + sd[z, None] * rng.standard_normal((s, d))).astype(np.float32)
+
+
+@pytest.mark.parametrize("s,d,k,seed", [(20000, 64, 500, 11), (5000, 128, 256, 12),
+                                        (65536, 64, 500, 13)])
+def test_lloyd_parity_global_sums(ctx, s, d, k, seed):
+    # CUDA-core Lloyd with k x d x 8 bytes of per-block sums above what a
+    # block's shared memory holds (the large workload's k = 500 at d = 64):
+    # every block adds its rows' fixed-point coordinates straight into the
+    # global sums
+    ctx.set_tensor_cores(0)
+    try:
+        sched = ctx.lloyd_schedule(s, d, k)
+        assert not sched["smem_sums"] and sched["form"] == "simt", sched
+        lloyd_case(ctx, zipf_mixture(s, d, k, seed), k, seed)
+    finally:
+        ctx.set_tensor_cores(2)
+
+
+# ---------------------------------------------------------------------------
+# Lloyd with the x.c contraction on the tensor cores (split BF16, d = 64 /
+# 128): incremental fixed-point sums of the rows whose label changed
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("s,d,k,seed", [(20000, 64, 500, 21), (65613, 64, 500, 22),
+                                        (5000, 128, 256, 23), (30011, 128, 100, 24),
+                                        (9001, 64, 130, 25), (3001, 64, 64, 26),
+                                        (129, 64, 60, 27), (1000, 128, 200, 28),
+                                        (40000, 64, 256, 29), (7000, 64, 33, 30)])
+def test_lloyd_parity_tensor_cores(ctx, s, d, k, seed):
+    ctx.set_tensor_cores(1)
+    try:
+        assert ctx.lloyd_schedule(s, d, k)["form"] == "split_bf16"
+        S = zipf_mixture(s, d, k, seed) if k >= 256 else mixture(s, d, k, seed, sd=1.5)
+        lloyd_case(ctx, S, k, seed)
+    finally:
+        ctx.set_tensor_cores(2)
+
+
+@pytest.mark.parametrize("d,k", [(64, 500), (128, 100)])
+def test_lloyd_tensor_cores_match_cuda_cores(ctx, d, k):
+    # the same run on both searches: the same labels away from near ties,
+    # centroids and objective within the contract, the same iteration count
+    S = zipf_mixture(30000, d, k, 31)
+    init = orc.kmeanspp(S, np.zeros((k, d), np.float32), np.ones(k, np.uint8), seed=31)
+    out = {}
+    for mode in (0, 1):
+        ctx.set_tensor_cores(mode)
+        out[mode] = gpu_lloyd(ctx, S, init["C"], init["degenerate"])
+    ctx.set_tensor_cores(2)
+    a, b = out[0], out[1]
+    if a["iters"] == b["iters"]:
+        assert_centroids(b["C"], a["C"], "tensor vs CUDA cores")
+        np.testing.assert_array_equal(a["degenerate"], b["degenerate"])
+        assert b["f"] == pytest.approx(a["f"], rel=RTOL)
+        assert_labels(b["labels"], S, a["C"], a["degenerate"], "tensor cores")
+    else:   # only a near tie may part the runs
+        lockstep_divergence(ctx, S, init["C"], init["degenerate"], max(a["iters"], b["iters"]))
+
+
+def test_lloyd_tensor_cores_edge_cases(ctx):
+    ctx.set_tensor_cores(1)
+    try:
+        d = 64
+        # one row, and fewer rows than a tile
+        S = mixture(77, d, 5, 41)
+        C0 = S[:5].copy()
+        o = orc.lloyd(S, C0, np.zeros(5, np.uint8))
+        g = gpu_lloyd(ctx, S, C0, np.zeros(5, np.uint8))
+        assert g["iters"] == o["iters"]
+        assert_centroids(g["C"], o["C"], "77 rows")
+        assert g["f"] == pytest.approx(o["f"], rel=RTOL)
+        g = gpu_lloyd(ctx, S[:1], C0[:1], np.zeros(1, np.uint8))
+        assert g["f"] == 0.0 and g["iters"] == 1
+        # centroids that lose every row become degenerate and keep their values
+        S2 = np.concatenate([np.zeros((100, d)), np.full((100, d), 5.0)]).astype(np.float32)
+        C2 = np.stack([np.zeros(d), np.full(d, 5.0), np.full(d, 100.0),
+                       np.full(d, 2.4)]).astype(np.float32)
+        o = orc.lloyd(S2, C2, np.zeros(4, np.uint8))
+        g = gpu_lloyd(ctx, S2, C2, np.zeros(4, np.uint8))
+        np.testing.assert_array_equal(g["degenerate"], o["degenerate"])
+        assert_centroids(g["C"], o["C"], "emptied clusters")
+        # zero iterations: only the assignment
+        g = gpu_lloyd(ctx, S, C0, np.zeros(5, np.uint8), max_iter=0)
+        assert g["iters"] == 0
+        np.testing.assert_array_equal(g["C"], C0)
+        # every centroid degenerate; a non-finite row
+        Cg, dg = dev(C0), dev(np.ones(5, np.uint8))
+        H.hpc_lloyd(ctx, dev(S), Cg, dg)
+        assert ctx.sync_status() == H.HPC_ERR_DEGENERATE_ALL
+        Sn = S.copy()
+        Sn[30, 7] = np.nan
+        H.hpc_lloyd(ctx, dev(Sn), dev(C0), dev(np.zeros(5, np.uint8)))
+        assert ctx.sync_status() == H.HPC_ERR_NONFINITE
+        # the context stays usable, and runs are deterministic
+        S3 = zipf_mixture(20000, d, 300, 42)
+        a = gpu_lloyd(ctx, S3, S3[:300].copy(), np.zeros(300, np.uint8))
+        b = gpu_lloyd(ctx, S3, S3[:300].copy(), np.zeros(300, np.uint8))
+        np.testing.assert_array_equal(a["C"], b["C"])
+        np.testing.assert_array_equal(a["labels"], b["labels"])
+        assert a["f"] == b["f"] and a["iters"] == b["iters"]
+    finally:
+        ctx.set_tensor_cores(2)
+
+
+def test_lloyd_tensor_cores_near_ties(ctx):
+    # rows on the bisector of two far centroids: the split-BF16 values
+    # cannot separate them; the exact stages must give the oracle's labels
+    rng = np.random.default_rng(43)
+    d = 64
+    c0 = rng.uniform(50, 60, d)
+    c1 = c0 + rng.uniform(-1, 1, d) * 0.5
+    mid = (c0 + c1) / 2
+    n = 4096
+    S = (mid + rng.standard_normal((n, d)) * 1e-3 +
+         np.outer(rng.uniform(-1e-2, 1e-2, n), c1 - c0)).astype(np.float32)
+    C = np.stack([c0, c1] + [c0 + 30 * rng.standard_normal(d) for _ in range(126)]).astype(np.float32)
+    ctx.set_tensor_cores(1)
+    try:
+        g = gpu_lloyd(ctx, S, C, np.zeros(128, np.uint8), max_iter=0)
+    finally:
+        ctx.set_tensor_cores(2)
+    lab_o, d1, d2, _ = orc.assign(S, C)
+    strict = (d2 - d1) > 1e-12 * d1
+    np.testing.assert_array_equal(g["labels"][strict], lab_o[strict])
 
 
 def test_lloyd_edge_cases(ctx):
@@ -435,6 +549,22 @@ def test_round_mixed_k_batch(ctx, strategy):
     batch = H.Batch(32, s, k, [0] * W)
     for rnd in range(3):
         check_round(ctx, X, Xd, batch, strategy, 17, rnd)
+
+
+@pytest.mark.parametrize("strategy", [0, 1])
+def test_round_tensor_core_lloyd(ctx, strategy):
+    # d = 64 workers with k up to 500 (the large workload's shape at test
+    # size): the split-BF16 tensor-core Lloyd inside the batched round
+    X = zipf_mixture(80000, 64, 300, 45)
+    Xd = dev(X)
+    rng = np.random.default_rng(46)
+    W = 8
+    s = rng.integers(3000, 12000, W).tolist()
+    k = [(100, 300, 500)[w % 3] for w in range(W)]
+    batch = H.Batch(64, s, k, [0] * W)
+    assert ctx.lloyd_schedule(max(s), 64, 500)["form"] == "split_bf16"
+    for rnd in range(3):
+        check_round(ctx, X, Xd, batch, strategy, 19, rnd)
 
 
 def test_round_hybrid_switches_phase(ctx):
