@@ -14,8 +14,9 @@ k = 500 and samples of 65,536 to 1,048,576 rows).
 Prints one JSON line (rank 0).  Arms:
   --impl mine       the CUDA library (default)
   --impl reference  the CPU oracle as the reference arm (host cores)
-Multi-GPU (torchrun): independent replicas per rank (weak scaling), barrier
-and max-over-ranks timing.
+Multi-GPU (torchrun): one job over the ranks -- workers split into contiguous
+ranges, the objective's rows into blocks (paper_2311_04517_gb300/multirank.py);
+barrier and max-over-ranks timing, the work summed over the ranks.
 """
 from __future__ import annotations
 
@@ -275,20 +276,18 @@ def group_members(ws):
     return [np.flatnonzero(ws.group == g) for g in sorted(set(int(v) for v in ws.group))]
 
 
-def workload_config(wl, strategy, args):
+def workload_config(wl, strategy, args, world: int = 1):
     st = strategy if strategy != "hybrid" else f"hybrid (competitive for {n_comp(args)} rounds)"
+    par = ("one GPU" if world == 1 else
+           f"one job on {world} GPUs: workers in contiguous ranges per rank, the objective's "
+           f"rows in blocks per rank (all-reduce), the cooperative share as an all-gather of "
+           f"(f-hat, index) and a broadcast of the best incumbent")
     return {"workload": f"{wl.name}: {wl.notes}", "n": wl.n, "d": wl.d, "k": list(wl.k),
-            "workers": wl.W, "s": list(wl.s), "strategy": st,
+            "workers": wl.W, "s": list(wl.s), "strategy": st, "parallelism": par,
             "step": "one HPClust round for every worker + full-data objective of the best "
                     "incumbent of each sharing group (workers with equal k)",
             "l2": "inputs larger than L2 (X is %.0f MB)" % (wl.n * wl.d * 4 / 1e6),
             "lloyd_max_iter": 300, "lloyd_rel_tol": 1e-4, "kmeanspp_candidates": 3}
-
-
-def replica_seed(wl, rank: int) -> int:
-    """Ranks run independent replicas of the workload (weak scaling): each
-    draws its own data and samples from its own seed."""
-    return wl.seed + rank
 
 
 def job_totals(ms: float, dist_total: float, device):
@@ -569,21 +568,36 @@ def run_mine(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    from paper_2311_04517_gb300 import multirank as MR
     wl = bench_workload(args)
     ws = synth.worker_setup(wl)
-    seed = replica_seed(wl, rank)
+    # one job on every rank: the same data, the workers split into
+    # contiguous ranges (each with its global random streams), the full-data
+    # objective split into row blocks
+    seed = wl.seed
     X = load_data(wl, dev, seed)
     strategy = {"cooperative": H.HPC_COOPERATIVE, "hybrid": H.HPC_HYBRID}.get(
         args.strategy, H.HPC_COMPETITIVE)
     ctx = H.Context(local)
     ctx.set_tensor_cores(args.tensor_cores)
-    batch = H.Batch(wl.d, ws.s, ws.k, ws.group, device=dev, n_competitive=n_comp(args))
+    ranges = MR.worker_ranges(ws.s, ws.k, world)
+    w0, w1 = ranges[rank]
+    if w1 <= w0:
+        raise SystemExit(f"rank {rank}: more ranks than workers ({wl.W})")
+    lw = slice(w0, w1)
+    Wl = w1 - w0
+    batch = H.Batch(wl.d, ws.s[lw], ws.k[lw], ws.group[lw], device=dev,
+                    n_competitive=n_comp(args), worker0=w0)
+    job = MR.RankedRun(MR.LibraryBackend(ctx, X, batch), ws.s, ws.k, ws.group, wl.d, w0, w1,
+                       device=dev)
+    ra, rb = MR.row_range(wl.n, world, rank) if world > 1 else (0, wl.n)
+    Xo = X[ra:rb]          # this rank's rows of the full-data objective
     groups = group_members(ws)
     f_sse = torch.zeros(len(groups), dtype=torch.float64, device=dev)
     K, Wm = args.steps, args.warmup
-    iters_log = torch.zeros((K, wl.W), dtype=torch.int32, device=dev)
+    iters_log = torch.zeros((K, Wl), dtype=torch.int32, device=dev)
     best_log = []
-    fhat_host = torch.empty(wl.W, dtype=torch.float64).pin_memory()
+    fhat_host = torch.empty(Wl, dtype=torch.float64).pin_memory()
 
     def bests():
         # the incumbent with the smallest objective per sample point in each
@@ -594,12 +608,25 @@ def run_mine(args):
         fh = fhat_host.numpy()
         return [int(g[np.argmin(fh[g])]) for g in groups]
 
+    def best_centroids():
+        """(k, C, flags) of each sharing group's best incumbent: on one rank
+        from the batch, across ranks by the all-gather and broadcast of the
+        cooperative share (which synchronises with the round)."""
+        if world == 1:
+            return [(int(ws.k[b]),) + tuple(batch.centroids(b)) for b in bests()]
+        out = []
+        for key in range(len(job.keys)):
+            _, _, C, deg = job.best(ranges, key)
+            kb = job.keys[key][1]
+            out.append((kb, C.view(kb, wl.d), deg))
+        return out
+
     graph = None
     graph_launches = 0
     # CUDA events around every launch of a round (graph nodes when recorded
     # in the graph): per-phase device times of each step
     ctx.set_phase_timing(True)
-    if args.graph:
+    if args.graph and not (world > 1 and strategy != H.HPC_COMPETITIVE):
         # one round recorded once; its round index lives on the device and
         # advances with every replay (rounds 0, 1, 2, ... as below)
         H.hpc_round_prepare(ctx, X, batch, strategy, seed, 0)
@@ -612,8 +639,13 @@ def run_mine(args):
         ctx.set_stream(torch.cuda.current_stream(dev))
         graph_launches = ctx.launch_count() - l0
 
+    # across ranks the cooperative share is an exchange between rounds
+    shared = world > 1 and strategy != H.HPC_COMPETITIVE
+
     def run_round(r):
-        if graph is not None:
+        if shared:
+            job.round(strategy, seed, r, ranges, n_competitive=n_comp(args))
+        elif graph is not None:
             graph.replay()
         else:
             H.hpc_round(ctx, X, batch, strategy, seed, r)
@@ -624,18 +656,19 @@ def run_mine(args):
         run_round(r)
         if log_row is not None:
             iters_log[log_row].copy_(batch.iters, non_blocking=True)
-        bs = bests()
+        cb = best_centroids()
         if log_row is not None:
-            best_log.append(bs)
+            best_log.append([kb for kb, _, _ in cb])
             if wl.W > 1:
-                # bests() has synchronised with the round: its phase times
-                # are ready (read before the next replay re-records them)
+                # best_centroids() has synchronised with the round: its phase
+                # times are ready (read before the next replay re-records them)
                 phase_log.append(ctx.phase_times())
         if ev is not None:
             ev[0].record()
-        for gi, b in enumerate(bs):
-            C, deg = batch.centroids(b)
-            H.hpc_objective(ctx, X, C, deg, f_out=f_sse[gi:gi + 1])
+        for gi, (kb, C, deg) in enumerate(cb):
+            H.hpc_objective(ctx, Xo, C, deg, f_out=f_sse[gi:gi + 1])
+        if world > 1:
+            dist.all_reduce(f_sse)     # Eq. 1 is a sum over the ranks' rows
         if ev is not None:
             ev[1].record()
 
@@ -653,11 +686,9 @@ def run_mine(args):
         if CM.OUT.exists():
             cm_params = torch.tensor(json.loads(CM.OUT.read_text())["params"],
                                      dtype=torch.float32, device=dev)
-        for b in bests():
-            kb = int(ws.k[b])
+        for kb, C, deg in best_centroids():
             if kb in forms:
                 continue
-            C, deg = batch.centroids(b)
             form, tms = ctx.autotune_objective(X[:rows], C, deg, reps=3)
             forms[kb] = {"form": H.SEARCH_NAMES[form], "ms_per_call": tms, "rows": rows}
             if cm_params is not None:
@@ -703,7 +734,7 @@ def run_mine(args):
     ms = start.elapsed_time(end)
     obj_ms = [a.elapsed_time(b) for a, b in evs]
     iters = iters_log.cpu().numpy()
-    dist_total = sum(dist_count(iters[i], ws.s, ws.k, wl.n, [int(ws.k[b]) for b in best_log[i]])
+    dist_total = sum(dist_count(iters[i], ws.s[lw], ws.k[lw], rb - ra, best_log[i])
                      for i in range(K))
     ms, dist_total = job_totals(ms, dist_total, dev)
     value = dist_total / (ms / 1e3)
@@ -717,9 +748,9 @@ def run_mine(args):
     if E > 0:
         X_host = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
         X_host.copy_(X)
-        res_host = torch.empty(len(groups) * 8 + wl.W, dtype=torch.float64).pin_memory()
+        res_host = torch.empty(len(groups) * 8 + Wl, dtype=torch.float64).pin_memory()
         C_host = torch.empty_like(batch.C, device="cpu").pin_memory()
-        e_iters = torch.zeros((E, wl.W), dtype=torch.int32, device=dev)
+        e_iters = torch.zeros((E, Wl), dtype=torch.int32, device=dev)
         e_best = []
         r0 = Wm + K + Wm_extra
         torch.cuda.synchronize()
@@ -737,8 +768,9 @@ def run_mine(args):
         copy_stream = torch.cuda.Stream(dev)
         arrived = [torch.cuda.Event() for _ in range(nck)]
         for i in range(E):
-            bs = bests()
-            e_best.append(bs)
+            cb = best_centroids()
+            e_best.append([kb for kb, _, _ in cb])
+            f_chunks.zero_()
             copy_stream.wait_stream(main)               # X is free once the last step is done
             with torch.cuda.stream(copy_stream):
                 for c in range(nck):
@@ -747,12 +779,12 @@ def run_mine(args):
                         X[a:b_].copy_(X_host[a:b_], non_blocking=True)
                     arrived[c].record(copy_stream)
             for c in range(nck):
-                a, b_ = c * rows, min(wl.n, (c + 1) * rows)
+                # the chunk's rows within this rank's block of the objective
+                a, b_ = max(ra, c * rows), min(rb, (c + 1) * rows)
                 main.wait_event(arrived[c])
                 if a >= b_:
                     continue
-                for gi, b in enumerate(bs):
-                    C, deg = batch.centroids(b)
+                for gi, (kb, C, deg) in enumerate(cb):
                     H.hpc_objective(ctx, X[a:b_], C, deg, f_out=f_chunks[gi, c:c + 1])
             run_round(r0 + i)
             e_iters[i].copy_(batch.iters, non_blocking=True)
@@ -764,26 +796,25 @@ def run_mine(args):
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1)
         ei = e_iters.cpu().numpy()
-        e_dist = sum(dist_count(ei[i], ws.s, ws.k, wl.n, [int(ws.k[b]) for b in e_best[i]])
-                     for i in range(E))
+        e_dist = sum(dist_count(ei[i], ws.s[lw], ws.k[lw], rb - ra, e_best[i]) for i in range(E))
         e_ms, e_dist = job_totals(e_ms, e_dist, dev)
         e_value = e_dist / (e_ms / 1e3)
         e2e = {"value": e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(X_host.numel() * 4),
                "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4 +
-                                         (wl.W * 8 if wl.W > 1 else 0))}
+                                         (Wl * 8 if wl.W > 1 else 0))}
         del X_host
 
     hbm, src = peaks()
     obj_avg_ms = float(np.mean(obj_ms)) / len(groups)  # one launch per group per step
-    kb0 = int(ws.k[best_log[0][0]]) if best_log else int(ws.k[0])
-    k_mean = (float(np.mean([int(ws.k[b]) for b in best_log[0]])) if best_log else float(kb0))
+    kb0 = int(best_log[0][0]) if best_log else int(ws.k[0])
+    k_mean = float(np.mean(best_log[0])) if best_log else float(kb0)
     form0 = ctx.objective_form(wl.n, wl.d, kb0)
     obj_kernel = {H.HPC_SEARCH_SIMT: "objective_kernel",
                   H.HPC_SEARCH_SPLIT_TF32: "tcs_objective_kernel",
                   H.HPC_SEARCH_TF32: "tc_objective_kernel" if kb0 <= 128
                   else "tw_objective_kernel"}[form0]
-    obj_entry = roofline_entry(obj_kernel, form0 == H.HPC_SEARCH_SIMT, wl.n, wl.d, k_mean,
+    obj_entry = roofline_entry(obj_kernel, form0 == H.HPC_SEARCH_SIMT, rb - ra, wl.d, k_mean,
                                obj_avg_ms, hbm, src,
                                profiled_traffic("objective", wl.name, obj_kernel))
     # the Lloyd launches of the timed steps (their phase times: one launch
@@ -793,11 +824,11 @@ def run_mine(args):
     lsched = ctx.lloyd_schedule(int(max(ws.s)), wl.d, int(max(ws.k)))
     lloyd_kernel_name = "lloyd_kernel" if lsched["form"] == "simt" else "tcl_lloyd_kernel"
     if Wm_extra:
-        it_rows = [(int(it[w]) + 1, int(ws.s[w]), int(ws.k[w]))
-                   for it in extra_iters for w in range(wl.W)]
+        it_rows = [(int(it[w]) + 1, int(ws.s[w0 + w]), int(ws.k[w0 + w]))
+                   for it in extra_iters for w in range(Wl)]
     else:
-        it_rows = [(int(iters[i][w]) + 1, int(ws.s[w]), int(ws.k[w]))
-                   for i in range(K) for w in range(wl.W)]
+        it_rows = [(int(iters[i][w]) + 1, int(ws.s[w0 + w]), int(ws.k[w0 + w]))
+                   for i in range(K) for w in range(Wl)]
     lloyd_entry = lloyd_roofline(lloyd_kernel_name, lsched["form"] == "simt", it_rows, wl.d,
                                  len(lloyd_ms) * chunks,
                                  float(np.sum(lloyd_ms)) / (len(lloyd_ms) * chunks), hbm, src,
@@ -813,9 +844,9 @@ def run_mine(args):
     if R > 0 and world == 1:
         tto = time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-            "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(wl, args.strategy, args),
+            "config": workload_config(wl, args.strategy, args, world),
             "round_issue": ("one round recorded in a CUDA graph, replayed every step" if args.graph
                             else "calls issued one by one"),
             "roofline": dominant,

@@ -272,6 +272,10 @@ typedef struct hpc_batch {
   uint8_t *accepted;    /* device [W] (nullable): 1 if the incumbent was replaced */
   int32_t n_competitive; /* HPC_HYBRID: rounds 0 .. n_competitive - 1 form the
                             competitive phase (Algorithm 5's N1); ignored otherwise */
+  int32_t worker0;       /* global index of worker 0: worker w draws its sample and its
+                            K-means++ candidates from stream (seed, worker0 + w), so a run
+                            split over several batches (processes, GPUs) draws what one
+                            batch of all workers would; 0 for a batch of all workers */
 } hpc_batch;
 
 /* One HPClust round for every worker of `batch` (one pass of the loop body

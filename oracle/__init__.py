@@ -83,7 +83,7 @@ def lib() -> ctypes.CDLL:
         L.orc_objective.argtypes = [P, i64, i32, P, i32, P, P]
         L.orc_objective.restype = f64
         L.orc_round.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P, P, i32, u64, u32,
-                                i32, f64, i32, P, P, P, i32]
+                                i32, f64, i32, P, P, P, i32, i32]
         L.orc_round.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -255,11 +255,13 @@ class RoundState:
 
 
 def round_(X, state: RoundState, strategy: int, seed: int, round_idx: int,
-           max_iter: int = 300, rel_tol: float = 1e-4, L: int = 3, n_competitive: int = 0):
+           max_iter: int = 300, rel_tol: float = 1e-4, L: int = 3, n_competitive: int = 0,
+           worker0: int = 0):
     """Runs one round in place on ``state``; returns dict(f_new, iters, accepted).
 
     strategy HYBRID (Algorithm 5): round_idx < n_competitive runs the
-    competitive phase, later rounds the cooperative one."""
+    competitive phase, later rounds the cooperative one.  worker0: the
+    global index of the state's first worker (its random streams)."""
     X = _f32(X)
     n, d = X.shape
     W = len(state.s)
@@ -269,7 +271,8 @@ def round_(X, state: RoundState, strategy: int, seed: int, round_idx: int,
     rc = lib().orc_round(_p(X), n, d, W, _p(state.s), _p(state.k), _p(state.group),
                          _p(state.C_pool), _p(state.C_off), _p(state.deg_pool),
                          _p(state.K_off), _p(state.fhat), strategy, seed, round_idx,
-                         max_iter, rel_tol, L, _p(f_new), _p(iters), _p(acc), n_competitive)
+                         max_iter, rel_tol, L, _p(f_new), _p(iters), _p(acc), n_competitive,
+                         int(worker0))
     if rc:
         raise ValueError(f"orc_round failed: {rc}")
     return dict(f_new=f_new, iters=iters, accepted=acc.astype(bool))

@@ -460,8 +460,13 @@ int orc_round(const float *X, int64_t n, int32_t d, int32_t W, const int64_t *s,
               const int64_t *C_off, uint8_t *deg_pool, const int64_t *K_off,
               double *fhat, int32_t strategy, uint64_t seed, uint32_t round,
               int32_t max_iter, double rel_tol, int32_t L, double *f_new_out,
-              int32_t *iters_out, uint8_t *accepted_out, int32_t n_competitive) {
-  if (W < 1 || d < 1 || n < 1) return ORC_ERR_ARG;
+              int32_t *iters_out, uint8_t *accepted_out, int32_t n_competitive,
+              int32_t worker0) {
+  /* worker0: the index of this set's first worker among all the workers of
+   * the run, so that worker w draws from its own stream (seed, worker0 + w)
+   * however the workers are split between processes (Section 5.3: one
+   * independent random stream per worker). */
+  if (W < 1 || d < 1 || n < 1 || worker0 < 0) return ORC_ERR_ARG;
   /* Algorithm 5 runs its phases in order over the round counter t_w (the
    * same for every worker here): the competitive phase while
    * t_w < n_competitive, the cooperative phase after it. */
@@ -488,7 +493,7 @@ int orc_round(const float *X, int64_t n, int32_t d, int32_t W, const int64_t *s,
     float *Cn = (float *)malloc(sizeof(float) * (size_t)kw * (size_t)d);
     uint8_t *dn = (uint8_t *)malloc((size_t)kw);
     int32_t *lab = (int32_t *)malloc(sizeof(int32_t) * (size_t)s[w]);
-    orc_draw_sample(X, n, d, seed, (uint32_t)w, round, s[w], Sw, NULL);
+    orc_draw_sample(X, n, d, seed, (uint32_t)(worker0 + w), round, s[w], Sw, NULL);
     int32_t b = w;
     if (strategy == ORC_STRAT_COOPERATIVE) {
       for (int32_t v = 0; v < W; ++v) {
@@ -500,7 +505,8 @@ int orc_round(const float *X, int64_t n, int32_t d, int32_t W, const int64_t *s,
     memcpy(dn, deg_snap + K_off[b], (size_t)kw);
     double f = 0.0;
     int32_t iters = 0;
-    rc = orc_kmeanspp(Sw, s[w], d, kw, Cn, dn, L, seed, (uint32_t)w, round, NULL, NULL);
+    rc = orc_kmeanspp(Sw, s[w], d, kw, Cn, dn, L, seed, (uint32_t)(worker0 + w), round, NULL,
+                      NULL);
     if (rc == ORC_OK)
       rc = orc_lloyd(Sw, s[w], d, kw, Cn, dn, max_iter, rel_tol, lab, &f, &iters, NULL);
     if (rc == ORC_OK) {

@@ -423,7 +423,7 @@ static int round_check(hpc_ctx *c, const float *X, int64_t n, int32_t d, const h
                        int32_t strategy, int32_t max_iter, int32_t n_candidates, int32_t prec) {
   if (int rc = check_dims(c, d)) return rc;
   if (n < 1 || !X || b->W < 1 || b->W > HPC_MAX_WORKERS || !b->s || !b->k || !b->C_off ||
-      !b->K_off || !b->C || !b->degenerate || !b->fhat)
+      !b->K_off || !b->C || !b->degenerate || !b->fhat || b->worker0 < 0)
     return fail(c, HPC_ERR_ARG, "malformed batch");
   if (strategy != HPC_COMPETITIVE && strategy != HPC_COOPERATIVE && strategy != HPC_HYBRID)
     return fail(c, HPC_ERR_ARG, "unknown strategy");
@@ -486,7 +486,7 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     float *S = cv.take<float>((size_t)s * d);
     float *Cn = cv.take<float>((size_t)k * d);
     uint8_t *dn = cv.take<uint8_t>((size_t)k);
-    st_h[w] = hpc_sample_task{S, nullptr, s, (uint32_t)w};
+    st_h[w] = hpc_sample_task{S, nullptr, s, (uint32_t)(b->worker0 + w)};
     rw_h[w] = hpc_round_worker{s, b->C_off[w], b->K_off[w], k, b->group ? b->group[w] : 0, Cn, dn,
                           fw + w, itw + w};
     hpc_kpp_task &kt = kt_h[w];
@@ -494,7 +494,7 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     kt.S = S;
     kt.s = s;
     kt.k = k;
-    kt.worker = (uint32_t)w;
+    kt.worker = (uint32_t)(b->worker0 + w);
     kt.C = Cn;
     kt.deg = dn;
     kpp_task_scratch(c, cv, hdr + w, s, L, kt);

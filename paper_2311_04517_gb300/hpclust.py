@@ -63,7 +63,8 @@ class hpc_batch(ctypes.Structure):
                 ("K_off", ctypes.c_void_p), ("C", ctypes.c_void_p),
                 ("degenerate", ctypes.c_void_p), ("fhat", ctypes.c_void_p),
                 ("f_new", ctypes.c_void_p), ("iters", ctypes.c_void_p),
-                ("accepted", ctypes.c_void_p), ("n_competitive", ctypes.c_int32)]
+                ("accepted", ctypes.c_void_p), ("n_competitive", ctypes.c_int32),
+                ("worker0", ctypes.c_int32)]
 
 
 _lib = None
@@ -338,10 +339,12 @@ def hpc_objective(ctx: Context, X, C, degenerate=None, prec: int = HPC_FP32, f_o
 class Batch:
     """Worker set for hpc_round: host descriptors plus device state."""
 
-    def __init__(self, d: int, s, k, group=None, device=None, n_competitive: int = 0):
+    def __init__(self, d: int, s, k, group=None, device=None, n_competitive: int = 0,
+                 worker0: int = 0):
         import numpy as np
         self.d = d
         self.n_competitive = int(n_competitive)  # HPC_HYBRID: rounds of the competitive phase
+        self.worker0 = int(worker0)  # global index of worker 0 (its random streams)
         self.device = device or torch.device("cuda", 0)
         self.s = np.ascontiguousarray(s, dtype=np.int64)
         self.k = np.ascontiguousarray(k, dtype=np.int32)
@@ -368,7 +371,8 @@ class Batch:
         return hpc_batch(self.W, self.s.ctypes.data, self.k.ctypes.data, self.group.ctypes.data,
                          self.C_off.ctypes.data, self.K_off.ctypes.data, self.C.data_ptr(),
                          self.degenerate.data_ptr(), self.fhat.data_ptr(), self.f_new.data_ptr(),
-                         self.iters.data_ptr(), self.accepted.data_ptr(), self.n_competitive)
+                         self.iters.data_ptr(), self.accepted.data_ptr(), self.n_competitive,
+                         self.worker0)
 
     def save(self, ctx: "Context", path, next_round: int, seed: int, strategy: int):
         """Writes the checkpoint of hpc_batch_save to the file `path`."""
