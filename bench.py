@@ -493,6 +493,42 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# Error windows of the tensor-core products, as the searches bound them: a
+# computed search value lies within E = c (||x|| + max||c||)^2 of the exact
+# one, and a row is proven only when its top-2 margin exceeds 2E; rows under
+# it take the exact stages.  c for the built forms: TF32 2^-10, split TF32
+# 2^-16, split BF16 2^-14; for one BF16 or one FP8 e4m3 product the same rule
+# with their unit roundoffs (2^-8, 2^-4) gives 2^-7 and 2^-3.
+WINDOW_REL = {"fp8_e4m3": 2.0 ** -3, "bf16": 2.0 ** -7, "tf32": 2.0 ** -10,
+              "split_bf16": 2.0 ** -14, "split_tf32": 2.0 ** -16}
+
+
+def precision_windows(X, C, deg, rows: int = 200_000, seed: int = 1):
+    """Fraction of sampled rows whose exact (FP64) top-2 margin to the live
+    centroids C lies inside each product's error window 2E: the rows each
+    precision would have to settle exactly."""
+    g = torch.Generator(device=X.device).manual_seed(seed)
+    idx = torch.randint(0, X.shape[0], (min(rows, X.shape[0]),), generator=g, device=X.device)
+    live = (deg == 0) if deg is not None else torch.ones(C.shape[0], dtype=torch.bool,
+                                                         device=C.device)
+    Cl = C[live].double()
+    if Cl.shape[0] < 2:
+        return None
+    cmax = float(Cl.norm(dim=1).max())
+    near = {k: 0 for k in WINDOW_REL}
+    n = 0
+    for a in range(0, idx.numel(), 20_000):
+        Xs = X[idx[a:a + 20_000]].double()
+        dd = torch.cdist(Xs, Cl) ** 2
+        t2 = torch.topk(dd, 2, dim=1, largest=False).values
+        margin = t2[:, 1] - t2[:, 0]
+        R = (Xs.norm(dim=1) + cmax) ** 2
+        for k, c in WINDOW_REL.items():
+            near[k] += int((margin <= 2.0 * c * R).sum())
+        n += Xs.shape[0]
+    return {k: v / n for k, v in near.items()} | {"rows": n}
+
+
 def time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev):
     """Wall time (CUDA events) for R rounds plus the full-data objective of
     each group's best incumbent after every round, on fresh batches: the
@@ -503,6 +539,7 @@ def time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev):
     1e-6 relative)."""
     out = {}
     logs = {}
+    samples = {}
     mode0 = args.tensor_cores
     for arm in ("fp32", "default"):
         ctx.set_tensor_cores(0 if arm == "fp32" else mode0)
@@ -520,12 +557,15 @@ def time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev):
             ctx.set_stream(torch.cuda.current_stream(dev))
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(R + 1)]
+        t0 = ctx.timestamp()                       # the device clock of t_done
         ev[0].record()
+        runs = []                                  # per round: (f_new / s, t_done)
         for r in range(R):
             if graph is not None:
                 graph.replay()
             else:
                 H.hpc_round(ctx, X, b, strategy, seed, r)
+            runs.append((b.f_new.clone(), b.t_done.clone()))
             if wl.W == 1:
                 bs = [0]
             else:
@@ -538,6 +578,10 @@ def time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev):
         torch.cuda.synchronize()
         ctx.check_status()
         logs[arm] = (f_log.cpu().numpy(), [ev[0].elapsed_time(e) for e in ev[1:]])
+        sw = np.asarray(ws.s, np.float64)
+        samples[arm] = ([f.cpu().numpy() / sw for f, _ in runs],
+                        [(t.cpu().numpy() - int(t0.item())) / 1e6 for _, t in runs],
+                        float(b.fhat.min().item()))
         del graph
     ctx.set_tensor_cores(mode0)
     target = logs["fp32"][0][-1]
@@ -548,6 +592,18 @@ def time_to_objective(H, ctx, X, wl, ws, strategy, seed, groups, R, args, dev):
     out["speedup"] = (out["fp32_ms"] / out["default_ms"]) if out["default_ms"] else None
     out["final_objectives_rel_diff"] = float(np.max(np.abs(logs["default"][0][-1] - target)
                                                     / target))
+    # Section 6.4's baseline convergence time: the baseline sample objective
+    # is the worse of the two paths' best sample objectives per point (the
+    # largest over the compared algorithms, one run each), and t-bar the time
+    # from the first round's start until any worker's run first ends at or
+    # below it (device clock, stamped where each run ends)
+    fbar = max(v[2] for v in samples.values())
+    for arm, (fv, tv, _) in samples.items():
+        hits = [float(t[w]) for f, t in zip(fv, tv) for w in range(len(f)) if f[w] <= fbar]
+        out[f"{arm}_tbar_ms"] = min(hits) if hits else None
+    out["baseline_sample_objective_per_point"] = fbar
+    out["tbar_speedup"] = (out["fp32_tbar_ms"] / out["default_tbar_ms"]
+                           if out["fp32_tbar_ms"] and out["default_tbar_ms"] else None)
     out.update({"rounds": R, "target": "the plain FP32 path's full-data objective of each "
                 "group's best incumbent after the last round, within 1e-6 relative",
                 "fp32_path": "CUDA-core search, rounds issued one by one",
@@ -859,6 +915,24 @@ def run_mine(args):
             "lloyd_iters_mean": float(iters.mean())}
     if forms:
         line["objective_forms"] = {str(k): v for k, v in forms.items()}
+    if world == 1:
+        # the rows each product precision would leave to the exact stages,
+        # on the first group's best incumbent after the timed steps
+        kb, Cb, db = best_centroids()[0]
+        line["precision_windows"] = precision_windows(X, Cb, db)
+    # the stages of the tensor-core searches over one more step (rounds
+    # issued directly: a recorded round keeps the counting it was recorded
+    # with)
+    ctx.set_search_stats(True)
+    ctx.search_stats(reset=True)
+    if shared:
+        run_round(Wm + K + Wm_extra + (E or 0))
+    else:
+        H.hpc_round(ctx, X, batch, strategy, seed, Wm + K + Wm_extra + (E or 0))
+    for kb, Cb, db in best_centroids():
+        H.hpc_objective(ctx, Xo, Cb, db)
+    line["search_stats_one_step"] = ctx.search_stats(reset=True)
+    ctx.set_search_stats(False)
     if tto is not None:
         line["time_to_objective"] = tto
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

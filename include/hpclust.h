@@ -54,10 +54,20 @@ typedef enum hpc_status {
   HPC_ERR_UNSUPPORTED = -7     /* a valid request the library does not implement */
 } hpc_status;
 
+/* Precision of the nearest-centroid search.  Whatever the precision, every
+ * search proves its winner against the error bound of its products or
+ * settles the row exactly (FP32 direct form, then FP64 in the oracle's
+ * operation order), so all return the labels of the double-precision
+ * assignment and objectives equal within rounding: the precision changes
+ * the speed, not the result. */
 typedef enum hpc_precision {
-  HPC_FP32 = 0, /* FP32 distances, FP64 rescoring of near ties */
-  HPC_BF16 = 1, /* reserved: BF16 tensor-core search with rescoring */
-  HPC_FP8 = 2   /* reserved: FP8 e4m3 tensor-core search with rescoring */
+  HPC_FP32 = 0, /* the context's choice (hpc_set_tensor_cores, hpc_set_objective_form):
+                   FP32 CUDA-core, split-TF32, TF32 or split-BF16 products */
+  HPC_BF16 = 1, /* split-BF16 tensor-core products (three BF16 MMAs per K step, FP32
+                   accumulation) with rescoring of near ties; built for d = 64
+                   (k <= 512) and d = 128 (k <= 256), HPC_ERR_UNSUPPORTED elsewhere */
+  HPC_FP8 = 2   /* not built (HPC_ERR_UNSUPPORTED): FP8 e4m3 products leave an error
+                   window that holds most rows of the method's own incumbents */
 } hpc_precision;
 
 typedef enum hpc_search {
@@ -179,6 +189,19 @@ int hpc_lloyd_schedule(hpc_ctx *ctx, int64_t s, int32_t d, int32_t k, int32_t *o
 int hpc_set_phase_timing(hpc_ctx *ctx, int32_t on);
 int hpc_phase_times(hpc_ctx *ctx, float *ms_out);
 
+/* Stage counters of the split-BF16 tensor-core search (the paper has no
+ * counterpart: measurement only).  With counting on, every objective and
+ * Lloyd assignment that runs that search adds to four device counters:
+ * [0] rows assigned, [1] rows whose tensor-core top-2 margin fell inside
+ * the error window (their two candidates were computed exactly), [2] rows
+ * settled against every centroid (a third candidate could not be ruled
+ * out), [3] rows settled in FP64.  hpc_search_stats synchronises the stream
+ * and copies them to out (host, 4 int64); reset != 0 zeroes them.  A
+ * prepared round keeps the setting it was prepared with.  Errors:
+ * HPC_ERR_ARG, HPC_ERR_CUDA. */
+int hpc_set_search_stats(hpc_ctx *ctx, int32_t on);
+int hpc_search_stats(hpc_ctx *ctx, int64_t *out, int32_t reset);
+
 /* ---- the hot path ------------------------------------------------------ */
 
 /* Random sample of size s from X (Section 3: a worker starts every round by
@@ -231,10 +254,15 @@ int hpc_kmeanspp(hpc_ctx *ctx, const float *S, int64_t s, int32_t d, int32_t k,
  *   labels_out        device, s int32 (output, nullable)
  *   f_out             device, 1 double (output): the sample objective
  *   iters_out         device, 1 int32 (output, nullable): updates performed
- * Errors: HPC_ERR_ARG for s < 1, k < 1, max_iter outside [0, 100000];
- * HPC_ERR_UNSUPPORTED
- * for prec other than HPC_FP32; device status HPC_ERR_DEGENERATE_ALL if no
- * centroid is live, HPC_ERR_NONFINITE for non-finite rows. */
+ * The assignment runs on the CUDA cores, or for d = 64 (k <= 512) and
+ * d = 128 (k <= 256) on the tensor cores in split BF16 (HPC_BF16, or
+ * hpc_set_tensor_cores mode 1, or mode 2 with k >= 48), where the centroid
+ * sums are kept incrementally: each assignment after the first adds and
+ * removes only the rows whose label changed, on the same exact fixed-point
+ * grid.  Errors: HPC_ERR_ARG for s < 1, k < 1, max_iter outside
+ * [0, 100000]; HPC_ERR_UNSUPPORTED for HPC_FP8, or HPC_BF16 on a shape it is
+ * not built for; device status HPC_ERR_DEGENERATE_ALL if no centroid is
+ * live, HPC_ERR_NONFINITE for non-finite rows. */
 int hpc_lloyd(hpc_ctx *ctx, const float *S, int64_t s, int32_t d, int32_t k,
               float *C_inout, uint8_t *degenerate_inout, int32_t max_iter,
               double rel_tol, int32_t prec, int32_t *labels_out, double *f_out,
@@ -249,8 +277,9 @@ int hpc_lloyd(hpc_ctx *ctx, const float *S, int64_t s, int32_t d, int32_t k,
  *   degenerate  device, k bytes (input, nullable = all live)
  *   f_out       device, 1 double (output)
  *   labels_out  device, n int32 (output, nullable)
- * Errors: HPC_ERR_ARG, HPC_ERR_UNSUPPORTED (prec); device status
- * HPC_ERR_DEGENERATE_ALL (n > 0 and no live centroid). */
+ * prec HPC_BF16 runs the split-BF16 search (HPC_SEARCH_SPLIT_BF16) whatever
+ * the context's choice.  Errors: HPC_ERR_ARG, HPC_ERR_UNSUPPORTED (prec);
+ * device status HPC_ERR_DEGENERATE_ALL (n > 0 and no live centroid). */
 int hpc_objective(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
                   const float *C, int32_t k, const uint8_t *degenerate,
                   int32_t prec, double *f_out, int32_t *labels_out);
@@ -276,6 +305,11 @@ typedef struct hpc_batch {
                             K-means++ candidates from stream (seed, worker0 + w), so a run
                             split over several batches (processes, GPUs) draws what one
                             batch of all workers would; 0 for a batch of all workers */
+  uint64_t *t_done;      /* device [W] (nullable): per round, the device time (globaltimer
+                            ns, as hpc_timestamp) at which worker w's run ended, after its
+                            incumbent test: with f_new it gives Section 6.4's baseline
+                            convergence time, the time until any worker first reaches a
+                            given sample objective */
 } hpc_batch;
 
 /* One HPClust round for every worker of `batch` (one pass of the loop body
@@ -312,6 +346,12 @@ int hpc_round_prepare(hpc_ctx *ctx, const float *X, int64_t n, int32_t d,
                       uint32_t round0, int32_t max_iter, double rel_tol,
                       int32_t n_candidates, int32_t prec);
 int hpc_round_enqueue(hpc_ctx *ctx);
+
+/* Writes the device's time (the globaltimer register, nanoseconds) into
+ * *dev_out (device, one uint64) once the work queued before it on the
+ * context's stream has run: the origin against which hpc_batch.t_done is
+ * read.  Errors: HPC_ERR_ARG, HPC_ERR_CUDA. */
+int hpc_timestamp(hpc_ctx *ctx, uint64_t *dev_out);
 
 /* ---- checkpoint ----------------------------------------------------------- */
 

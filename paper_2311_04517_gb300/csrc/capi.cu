@@ -22,6 +22,9 @@
 #define HPC_TIMING_EVENTS 64
 // search forms of the objective (hpc_search)
 #define HPC_NFORMS 4
+// rows per CTA the tensor-core Lloyd settles against every centroid after
+// each pass (beyond it, where they arise)
+#define HPC_LLOYD_QUEUE_CAP 16384
 
 struct hpc_round_plan;
 
@@ -58,6 +61,7 @@ struct hpc_ctx {
   // phase (0 sampling, 1 K-means++, 2 Lloyd) of the launch that ends at
   // event i (i >= 1)
   int timing;
+  int stats_on;  // hpc_set_search_stats: the tensor-core searches count their stages
   cudaEvent_t tev[HPC_TIMING_EVENTS];
   int tev_kind[HPC_TIMING_EVENTS];
   int tev_n;
@@ -140,9 +144,14 @@ size_t tcl_ws(int d, int k, int64_t s) {
   return hpc_tcl_supported(d, k) ? pad256((size_t)s * 4) + pad256(hpc_tcl_gcent_bytes(d, k)) : 0;
 }
 
+// the tensor-core Lloyd's per-CTA queues (one launch at a time uses them)
+size_t tcl_queue_ws(const hpc_ctx *c, int d, int kmax) {
+  return hpc_tcl_supported(d, kmax) ? pad256((size_t)c->L.num_sms * HPC_LLOYD_QUEUE_CAP * 8) : 0;
+}
+
 size_t lloyd_ws(const hpc_ctx *c, int d, int k, int64_t s) {
   return sizeof(TaskHeader) + pad256((size_t)3 * k * d * 8) + pad256((size_t)3 * k * 4) +
-         pad256((size_t)k) + tcl_ws(d, k, s) + 256;
+         pad256((size_t)k) + tcl_ws(d, k, s) + tcl_queue_ws(c, d, k) + 512;
 }
 
 size_t kpp_ws(const hpc_ctx *c, int64_t s, int L) {
@@ -151,7 +160,8 @@ size_t kpp_ws(const hpc_ctx *c, int64_t s, int L) {
 }
 
 // near-tie rows the tensor-core search settles after its main loop, per block
-#define HPC_OBJ_QUEUE_CAP 4096
+#define HPC_OBJ_QUEUE_CAP 32768
+
 
 // the wide tensor-core search's exact centroid block, at its largest shape
 #define HPC_OBJ_CENT_BYTES ((size_t)320 * 1024)
@@ -188,15 +198,40 @@ void kpp_task_scratch(const hpc_ctx *c, Carver &cv, TaskHeader *hd, int64_t s, i
   t.cand = cv.take<long long>((size_t)L);
 }
 
+// The search-stage counters (four words in the context's device words,
+// after the status and the objective's done-counter), or null when off.
+unsigned long long *stats_ptr(const hpc_ctx *c) {
+  return c->stats_on ? reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->dwords) + 64)
+                     : nullptr;
+}
+
 int plan_fail(hpc_ctx *c, int rc, const char *what) {
   if (rc == HPC_ERR_CUDA) return cuda_fail(c, cudaGetLastError(), what);
   return fail(c, rc, what);
 }
 
+// The Lloyd search mode a precision asks for: HPC_FP32 leaves the choice to
+// the context (hpc_set_tensor_cores); HPC_BF16 asks for the split-BF16
+// tensor-core search, built for d = 64 (k <= 512) and d = 128 (k <= 256).
+int prec_lloyd_mode(hpc_ctx *c, int prec, int d, int kmax, int *mode) {
+  if (prec == HPC_FP32) {
+    *mode = c->use_tc;
+    return HPC_OK;
+  }
+  if (prec == HPC_BF16) {
+    if (!hpc_tcl_supported(d, kmax))
+      return fail(c, HPC_ERR_UNSUPPORTED, "HPC_BF16: split-BF16 search not built for this shape");
+    *mode = 1;
+    return HPC_OK;
+  }
+  if (prec == HPC_FP8) return fail(c, HPC_ERR_UNSUPPORTED, "HPC_FP8 is not built");
+  return fail(c, HPC_ERR_ARG, "unknown precision");
+}
+
 // Launches Lloyd on one sample with scratch carved from `cv`.
 int run_lloyd(hpc_ctx *c, Carver &cv, const float *S, int64_t s, int d, int k, float *C,
               uint8_t *deg, int max_iter, double tol, int32_t *labels, double *f_out,
-              int32_t *iters_out) {
+              int32_t *iters_out, int tc_mode) {
   TaskHeader *hd = cv.take<TaskHeader>(1);
   hpc_lloyd_task t{};
   t.S = S;
@@ -222,7 +257,13 @@ int run_lloyd(hpc_ctx *c, Carver &cv, const float *S, int64_t s, int d, int k, f
   h.status = c->dwords;
   h.max_blocks = c->grid_bound;
   h.task_blocks = c->grid_bound;
-  h.tc_mode = c->use_tc;
+  h.tc_mode = tc_mode;
+  h.stats = stats_ptr(c);
+  if (hpc_tcl_supported(d, k)) {
+    h.queue = cv.take<int64_t>((size_t)c->L.num_sms * HPC_LLOYD_QUEUE_CAP);
+    h.queue_cap = HPC_LLOYD_QUEUE_CAP;
+    h.queue_ctas = c->L.num_sms;
+  }
   int rc = hpc_lloyd_plan(c->L, h);
   if (rc) return plan_fail(c, rc, "lloyd: unsupported shape");
   if ((rc = hpc_lloyd_run(c->L, h))) return plan_fail(c, rc, "lloyd launch");
@@ -308,7 +349,7 @@ int builtin_form(int d, int k, int64_t n) {
 }
 
 int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, const float *C, int k,
-                  const uint8_t *deg, double *f_out, int32_t *labels) {
+                  const uint8_t *deg, double *f_out, int32_t *labels, int form_req = -1) {
   double *part = cv.take<double>((size_t)c->grid_bound);
   int64_t *queue = cv.take<int64_t>((size_t)c->L.num_sms * HPC_OBJ_QUEUE_CAP);
   unsigned char *cent = cv.take<unsigned char>(HPC_OBJ_CENT_BYTES);
@@ -330,7 +371,8 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
   h.part = part;
   h.done_count = reinterpret_cast<unsigned *>(c->dwords + 1);
   h.max_blocks = c->grid_bound;
-  int form = objective_form(c, d, k, n);
+  h.stats = stats_ptr(c);
+  int form = form_req >= 0 ? form_req : objective_form(c, d, k, n);
   if (!X || !aligned16(X)) form = HPC_SEARCH_SIMT;
   int rc = HPC_ERR_UNSUPPORTED;
   if (form == HPC_SEARCH_SPLIT_TF32)
@@ -345,6 +387,8 @@ int run_objective(hpc_ctx *c, Carver &cv, const float *X, int64_t n, int d, cons
   c->launches += 1;
   return HPC_OK;
 }
+
+__global__ void timestamp_kernel(unsigned long long *out) { *out = hpc_globaltimer(); }
 
 // Block 0 waits at a grid barrier that block 1 never reaches; the bounded
 // wait gives up after limit_ns and records HPC_ERR_TIMEOUT.
@@ -427,14 +471,17 @@ static int round_check(hpc_ctx *c, const float *X, int64_t n, int32_t d, const h
     return fail(c, HPC_ERR_ARG, "malformed batch");
   if (strategy != HPC_COMPETITIVE && strategy != HPC_COOPERATIVE && strategy != HPC_HYBRID)
     return fail(c, HPC_ERR_ARG, "unknown strategy");
-  if (prec != HPC_FP32) return fail(c, HPC_ERR_UNSUPPORTED, "only HPC_FP32 is built");
   if (n_candidates < 1 || n_candidates > 8) return fail(c, HPC_ERR_ARG, "n_candidates in [1, 8]");
   if (max_iter < 0 || max_iter > HPC_MAX_ITER) return fail(c, HPC_ERR_ARG, "max_iter out of range");
   if (!aligned16(X) || !aligned16(b->C)) return fail(c, HPC_ERR_ARG, "unaligned");
-  for (int w = 0; w < b->W; ++w)
+  int kmax = 0;
+  for (int w = 0; w < b->W; ++w) {
     if (b->s[w] < 1 || b->k[w] < 1 || b->C_off[w] < 0 || b->K_off[w] < 0 || (b->C_off[w] & 3))
       return fail(c, HPC_ERR_ARG, "malformed batch entry");
-  return HPC_OK;
+    kmax = std::max(kmax, (int)b->k[w]);
+  }
+  int mode = 0;
+  return prec_lloyd_mode(c, prec, d, kmax, &mode);
 }
 
 // Device bytes of one round's scratch and tables (tables: *tab_bytes).
@@ -451,6 +498,9 @@ static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, i
             pad256((size_t)L * s * 4) + pad256((size_t)c->grid_bound * 8) + pad256((size_t)L * 8) +
             tcl_ws(d, k, s);
   }
+  int kmax = 0;
+  for (int w = 0; w < W; ++w) kmax = std::max(kmax, (int)b->k[w]);
+  need += tcl_queue_ws(c, d, kmax);
   *tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) + pad256((size_t)W * sizeof(hpc_round_worker)) +
                pad256((size_t)W * sizeof(hpc_kpp_task)) + pad256((size_t)W * sizeof(hpc_lloyd_task)) +
                2 * (size_t)nchunks * pad256((size_t)c->grid_bound * 4);
@@ -463,7 +513,7 @@ static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, i
 static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_batch *b,
                        int strategy, uint64_t seed, uint32_t round, int max_iter, double rel_tol,
                        int L, Carver &cv, char *tab_host, char *tab_dev, size_t tab_bytes,
-                       hpc_round_plan &p) {
+                       hpc_round_plan &p, int tc_mode) {
   const int W = b->W;
   const int nchunks = (W + HPC_ROUND_CHUNK - 1) / HPC_ROUND_CHUNK;
   int64_t smax = 0;
@@ -515,7 +565,14 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     lt.f_new = b->f_new ? b->f_new + w : nullptr;
     lt.iters_rep = b->iters ? b->iters + w : nullptr;
     lt.accepted = b->accepted ? b->accepted + w : nullptr;
+    lt.t_done = b->t_done ? reinterpret_cast<unsigned long long *>(b->t_done) + w : nullptr;
   }
+  // the tensor-core Lloyd's queues, shared by the chunks' launches (which
+  // run one after another)
+  int kall = 0;
+  for (int w = 0; w < W; ++w) kall = std::max(kall, (int)b->k[w]);
+  int64_t *lqueue = hpc_tcl_supported(d, kall)
+                        ? cv.take<int64_t>((size_t)c->L.num_sms * HPC_LLOYD_QUEUE_CAP) : nullptr;
   // plans of the persistent launches, HPC_ROUND_CHUNK workers each
   p.kl.assign(nchunks, KppLaunch{});
   p.ll.assign(nchunks, LloydLaunch{});
@@ -551,7 +608,11 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     lh.status = c->dwords;
     lh.max_blocks = c->grid_bound;
     lh.task_blocks = c->grid_bound;
-    lh.tc_mode = c->use_tc;
+    lh.tc_mode = tc_mode;
+    lh.stats = stats_ptr(c);
+    lh.queue = lqueue;
+    lh.queue_cap = lqueue ? HPC_LLOYD_QUEUE_CAP : 0;
+    lh.queue_ctas = c->L.num_sms;
     if (int rc = hpc_lloyd_plan(c->L, lh)) return plan_fail(c, rc, "lloyd: unsupported shape");
   }
   if (cv.off > cv.cap || th.off > th.cap) return fail(c, HPC_ERR_NOMEM, "round scratch layout overflow");
@@ -779,13 +840,14 @@ int hpc_lloyd(hpc_ctx *c, const float *S, int64_t s, int32_t d, int32_t k, float
   if (s < 1 || k < 1 || max_iter < 0 || !S || !C_inout || !f_out)
     return fail(c, HPC_ERR_ARG, "bad sizes");
   if (max_iter > HPC_MAX_ITER) return fail(c, HPC_ERR_ARG, "max_iter above 100000");
-  if (prec != HPC_FP32) return fail(c, HPC_ERR_UNSUPPORTED, "only HPC_FP32 is built");
+  int mode = 0;
+  if (int rc = prec_lloyd_mode(c, prec, d, k, &mode)) return rc;
   if (!aligned16(S) || !aligned16(C_inout)) return fail(c, HPC_ERR_ARG, "unaligned");
   cudaSetDevice(c->device);
   if (int rc = ensure_ws(c, lloyd_ws(c, d, k, s))) return rc;
   Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
   return run_lloyd(c, cv, S, s, d, k, C_inout, degenerate_inout, max_iter, rel_tol, labels_out,
-                   f_out, iters_out);
+                   f_out, iters_out, mode);
 }
 
 int hpc_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float *C, int32_t k,
@@ -793,12 +855,21 @@ int hpc_objective(hpc_ctx *c, const float *X, int64_t n, int32_t d, const float 
   if (!c) return HPC_ERR_ARG;
   if (int rc = check_dims(c, d)) return rc;
   if (n < 0 || k < 1 || !C || !f_out || (n > 0 && !X)) return fail(c, HPC_ERR_ARG, "bad sizes");
-  if (prec != HPC_FP32) return fail(c, HPC_ERR_UNSUPPORTED, "only HPC_FP32 is built");
+  int form = -1;
+  if (prec == HPC_BF16) {
+    if (!hpc_tcl_supported(d, k))
+      return fail(c, HPC_ERR_UNSUPPORTED, "HPC_BF16: split-BF16 search not built for this shape");
+    if (n > 0) form = HPC_SEARCH_SPLIT_BF16;
+  } else if (prec == HPC_FP8) {
+    return fail(c, HPC_ERR_UNSUPPORTED, "HPC_FP8 is not built");
+  } else if (prec != HPC_FP32) {
+    return fail(c, HPC_ERR_ARG, "unknown precision");
+  }
   if ((X && !aligned16(X)) || !aligned16(C)) return fail(c, HPC_ERR_ARG, "unaligned");
   cudaSetDevice(c->device);
   if (int rc = ensure_ws(c, obj_ws(c))) return rc;
   Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
-  return run_objective(c, cv, X, n, d, C, k, degenerate, f_out, labels_out);
+  return run_objective(c, cv, X, n, d, C, k, degenerate, f_out, labels_out, form);
 }
 
 int hpc_set_objective_form(hpc_ctx *c, int32_t d, int32_t k, int32_t form) {
@@ -838,6 +909,26 @@ int hpc_lloyd_schedule(hpc_ctx *c, int64_t s, int32_t d, int32_t k, int32_t *out
   if (int rc = hpc_lloyd_plan(c->L, h)) return plan_fail(c, rc, "lloyd: unsupported shape");
   const int32_t v[5] = {(int32_t)h.grid, h.smem_sums, h.xstage, (int32_t)h.smem, h.form};
   for (int i = 0; i < nout && i < 5; ++i) out[i] = v[i];
+  return HPC_OK;
+}
+
+int hpc_set_search_stats(hpc_ctx *c, int32_t on) {
+  if (!c || on < 0 || on > 1) return HPC_ERR_ARG;
+  c->stats_on = on;
+  return HPC_OK;
+}
+
+int hpc_search_stats(hpc_ctx *c, int64_t *out, int32_t reset) {
+  if (!c || !out) return HPC_ERR_ARG;
+  cudaSetDevice(c->device);
+  unsigned long long *p =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(c->dwords) + 64);
+  unsigned long long v[4];
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(v, p, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(p, 0, sizeof(v));
+  if (e != cudaSuccess) return cuda_fail(c, e, "search counters");
+  for (int i = 0; i < 4; ++i) out[i] = (int64_t)v[i];
   return HPC_OK;
 }
 
@@ -1303,6 +1394,16 @@ int hpc_batch_load(hpc_ctx *c, const hpc_batch *b, int32_t d, const void *host_b
   return HPC_OK;
 }
 
+int hpc_timestamp(hpc_ctx *c, uint64_t *dev_out) {
+  if (!c || !dev_out) return HPC_ERR_ARG;
+  cudaSetDevice(c->device);
+  timestamp_kernel<<<1, 1, 0, c->stream>>>(reinterpret_cast<unsigned long long *>(dev_out));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "timestamp launch");
+  c->launches += 1;
+  return HPC_OK;
+}
+
 int hpc_selftest_wait_timeout(hpc_ctx *c, int64_t limit_ns) {
   if (!c || limit_ns < 1000 || limit_ns > 1000000000ll)
     return fail(c, HPC_ERR_ARG, "limit_ns in [1 us, 1 s]");
@@ -1335,9 +1436,12 @@ int hpc_round(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch 
   char *tab_host = nullptr;
   const int slot = c->stage_next;
   if (int rc = stage_acquire(c, slot, tab_bytes, &tab_host)) return rc;
+  int kmax = 0, mode = 0;
+  for (int w = 0; w < b->W; ++w) kmax = std::max(kmax, (int)b->k[w]);
+  if (int rc = prec_lloyd_mode(c, prec, d, kmax, &mode)) return rc;
   hpc_round_plan p;
   if (int rc = round_build(c, X, n, d, b, strategy, seed, round, max_iter, rel_tol, n_candidates,
-                           cv, tab_host, tab_dev, tab_bytes, p))
+                           cv, tab_host, tab_dev, tab_bytes, p, mode))
     return rc;
   // one table copy from the pinned staging slot, then the launches
   cudaError_t e = cudaMemcpyAsync(tab_dev, tab_host, tab_bytes, cudaMemcpyHostToDevice, c->stream);
@@ -1373,8 +1477,14 @@ int hpc_round_prepare(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hp
   c->plan_round = cv.take<uint32_t>(1);
   char *tab_dev = cv.take<char>(tab_bytes);
   p.host.assign(tab_bytes, 0);
+  int kmax = 0, mode = 0;
+  for (int w = 0; w < b->W; ++w) kmax = std::max(kmax, (int)b->k[w]);
+  if (int rc = prec_lloyd_mode(c, prec, d, kmax, &mode)) {
+    p.W = 0;
+    return rc;
+  }
   if (int rc = round_build(c, X, n, d, b, strategy, seed, round0, max_iter, rel_tol, n_candidates,
-                           cv, p.host.data(), tab_dev, tab_bytes, p)) {
+                           cv, p.host.data(), tab_dev, tab_bytes, p, mode)) {
     p.W = 0;
     return rc;
   }

@@ -50,6 +50,7 @@ struct hpc_lloyd_task {
   double *f_new;             // nullable reports
   int32_t *iters_rep;
   uint8_t *accepted;
+  unsigned long long *t_done;  // nullable: the time (globaltimer ns) the run ended
 };
 // Lloyd zeroes gsum / gcount itself; bar and gmaxabs must be zero at launch.
 
@@ -76,6 +77,14 @@ struct LloydLaunch {
   // measured faster (the plan writes the one chosen into `form`)
   int tc_mode;
   int form;  // written by the plan: hpc_search (0 CUDA cores, 3 split BF16)
+  // nullable: counters of the tensor-core search (rows, rows near a tie,
+  // rows settled against every centroid, rows settled in FP64)
+  unsigned long long *stats;
+  // nullable: rows the tensor-core Lloyd settles after each pass (queue_cap
+  // per CTA, queue_ctas CTAs at most)
+  int64_t *queue;
+  int64_t queue_cap;
+  int64_t queue_ctas;
 };
 
 // ---- K-means++ (one task = one sample) ----
@@ -135,6 +144,8 @@ struct ObjArgsHost {
   // (k > 128) tensor-core search, hpc_tc_wide_scratch_bytes(d, k) bytes
   unsigned char *cent_scratch;
   int64_t cent_scratch_bytes;
+  // nullable: counters of the split-BF16 search (as LloydLaunch::stats)
+  unsigned long long *stats;
 };
 
 // ---- sampling (one task = one worker's sample) ----

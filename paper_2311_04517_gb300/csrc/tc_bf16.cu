@@ -188,7 +188,7 @@ __device__ __forceinline__ void tb_convert(const TbSm &m, const TbRows &R, uint3
   using Cfg = TbCfg<D, NP>;
   constexpr int F4 = D / 4;                       // float4 per row
   constexpr int LDS = 64 * F4 / 32;               // loads per lane per tile
-  constexpr int BATCH = 8;
+  constexpr int BATCH = 16;
   const int cw = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = 0; i < R.ntiles; ++i) {
     const uint32_t g = gbase + (uint32_t)i;
@@ -353,16 +353,26 @@ __device__ __forceinline__ void tb_epilogue(const TbSm &m, const TbRows &R, uint
     if (lane == 0) hpc_mbar_arrive(&m.xready[xb]);
     if ((int)(g & 3u) != e) continue;
     if (!wait_warp(&m.xready[xb], xu & 1u, m.abort, status, TB_WAIT_NS)) break;
+    float lo3;
     {
-      const float2 p0 = m.xch[(xb * 4) * TB_M + r_in];
-      d1 = p0.x;
-      d2 = p0.y;
+      float2 p[4];
+#pragma unroll
+      for (int o = 0; o < 4; ++o) p[o] = m.xch[(xb * 4 + o) * TB_M + r_in];
+      d1 = p[0].x;
+      d2 = p[0].y;
 #pragma unroll
       for (int o = 1; o < 4; ++o) {
-        const float2 po = m.xch[(xb * 4 + o) * TB_M + r_in];
-        d2 = hpc_min3(d2, po.y, fmaxf(d1, po.x));
-        d1 = fminf(d1, po.x);
+        d2 = hpc_min3(d2, p[o].y, fmaxf(d1, p[o].x));
+        d1 = fminf(d1, p[o].x);
       }
+      // every centroid but the two best: in a warpgroup holding one of them
+      // (as its smallest) at least that warpgroup's second, elsewhere at
+      // least the warpgroup's smallest (keys are unique, so equal keys are
+      // the same column)
+      lo3 = __int_as_float(0x7f7fffff);
+#pragma unroll
+      for (int o = 0; o < 4; ++o)
+        lo3 = fminf(lo3, (p[o].x == d1 || p[o].x == d2) ? p[o].y : p[o].x);
     }
     __syncwarp();
     if (lane == 0) hpc_mbar_arrive(&m.xdone[xb]);
@@ -371,7 +381,7 @@ __device__ __forceinline__ void tb_epilogue(const TbSm &m, const TbRows &R, uint
     const bool valid = row < R.nrows;
     const int j1 = min(__float_as_int(d1) & ((1 << IB) - 1), kp - 1);
     const int j2 = min(__float_as_int(d2) & ((1 << IB) - 1), kp - 1);
-    fin(row0 + 32 * q, row, valid, j1, j2, d1, d2);
+    fin(row0 + 32 * q, row, valid, j1, j2, d1, d2, lo3);
   }
 }
 
@@ -408,39 +418,55 @@ __device__ __forceinline__ float tb_direct(const float *__restrict__ x, const fl
 }
 
 // Exact assignment of one row by the whole warp (every lane passes the same
-// row; lanes take centroids lane, lane + 32, ...): FP32 direct form in
-// dimension order with its relative bound (D + 3) u, then, if the two best
-// are not separated, FP64 in the oracle's operation order, ties to the
-// lowest index.  The row streams from memory (no D registers per lane).
-template <int D>
-__device__ __forceinline__ int tb_rescore(const float *__restrict__ x, const hpc_cent_smem &cs) {
+// row; lane l takes centroids l, l + 32, ..., NPL of them): FP32 direct form
+// in dimension order with its relative bound (D + 3) u, then, if the two
+// best are not separated, FP64 in the oracle's operation order, ties to the
+// lowest index.  The row streams from memory eight dimensions at a time and
+// each lane advances all its centroids over them, so that the centroid
+// loads of one step are independent.  Counts the FP64 rows in *stats.
+template <int D, int NPL>
+__device__ __forceinline__ int tb_rescore(const float *__restrict__ x, const hpc_cent_smem &cs,
+                                          unsigned long long *stats) {
   constexpr int CS = hpc_cstride(D);
   const int lane = threadIdx.x & 31;
+  float acc[NPL];
+  bool live[NPL];
+#pragma unroll
+  for (int u = 0; u < NPL; ++u) {
+    const int j = lane + 32 * u;
+    live[u] = j < cs.kp && __ldcg(&cs.cnz[j].x) < HPC_DEAD;
+    acc[u] = 0.0f;
+  }
+#pragma unroll 1
+  for (int t0 = 0; t0 < D; t0 += 8) {
+    const float4 xa = __ldg(reinterpret_cast<const float4 *>(x + t0));
+    const float4 xb = __ldg(reinterpret_cast<const float4 *>(x + t0 + 4));
+    const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+      if (!live[u]) continue;
+      const float *cm = cs.cm + (size_t)(lane + 32 * u) * CS + t0;
+      const float4 ca = __ldcg(reinterpret_cast<const float4 *>(cm));
+      const float4 cb = __ldcg(reinterpret_cast<const float4 *>(cm + 4));
+      const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const float df = __fmaf_rn(0.5f, cv[t], xv[t]);
+        acc[u] = __fmaf_rn(df, df, acc[u]);
+      }
+    }
+  }
   float a1 = __int_as_float(0x7f800000), a2 = a1;
   int ja = 0x7fffffff;
-  for (int j = lane; j < cs.kp; j += 32) {
-    if (__ldcg(&cs.cnz[j].x) >= HPC_DEAD) continue;
-    const float *cm = cs.cm + (size_t)j * CS;
-    float acc = 0.0f;
-#pragma unroll 4
-    for (int t = 0; t < D; t += 4) {
-      const float4 xv = __ldg(reinterpret_cast<const float4 *>(x + t));
-      const float4 cv = __ldcg(reinterpret_cast<const float4 *>(cm + t));
-      float df = __fmaf_rn(0.5f, cv.x, xv.x);
-      acc = __fmaf_rn(df, df, acc);
-      df = __fmaf_rn(0.5f, cv.y, xv.y);
-      acc = __fmaf_rn(df, df, acc);
-      df = __fmaf_rn(0.5f, cv.z, xv.z);
-      acc = __fmaf_rn(df, df, acc);
-      df = __fmaf_rn(0.5f, cv.w, xv.w);
-      acc = __fmaf_rn(df, df, acc);
-    }
-    if (acc < a1) {
+#pragma unroll
+  for (int u = 0; u < NPL; ++u) {
+    if (!live[u]) continue;
+    if (acc[u] < a1) {
       a2 = a1;
-      a1 = acc;
-      ja = j;
+      a1 = acc[u];
+      ja = lane + 32 * u;
     } else {
-      a2 = fminf(a2, acc);
+      a2 = fminf(a2, acc[u]);
     }
   }
 #pragma unroll
@@ -452,19 +478,20 @@ __device__ __forceinline__ int tb_rescore(const float *__restrict__ x, const hpc
   }
   const float bound = (float)(D + 3) * HPC_U32 * 1.001f * (a1 + a2);
   if (a2 - a1 > bound) return ja < cs.kp ? ja : 0;
+  if (stats && lane == 0) atomicAdd(stats + 3, 1ull);
   double b = __longlong_as_double(0x7ff0000000000000ll);
   int jb = 0x7fffffff;
   for (int j = lane; j < cs.kp; j += 32) {
     if (__ldcg(&cs.cnz[j].x) >= HPC_DEAD) continue;
     const float *cm = cs.cm + (size_t)j * CS;
-    double acc = 0.0;
+    double acc64 = 0.0;
     for (int t = 0; t < D; ++t) {
       const double c = -0.5 * (double)__ldcg(cm + t);
       const double diff = __dsub_rn((double)__ldg(x + t), c);
-      acc = __dadd_rn(acc, __dmul_rn(diff, diff));
+      acc64 = __dadd_rn(acc64, __dmul_rn(diff, diff));
     }
-    if (acc < b) {
-      b = acc;
+    if (acc64 < b) {
+      b = acc64;
       jb = j;
     }
   }
@@ -480,14 +507,27 @@ __device__ __forceinline__ int tb_rescore(const float *__restrict__ x, const hpc
   return jb < cs.kp ? jb : 0;
 }
 
+// Rows whose settling needs every centroid, deferred to after the CTA's
+// pipeline (where every warp takes part, so that their latency overlaps):
+// `cap` row indices per CTA in global memory, *count in shared memory.
+struct TbQueue {
+  int64_t *rows;
+  int cap;
+  int *count;
+};
+
+enum { TB_DONE = 1, TB_BAD = 0, TB_QUEUED = 2 };
+
 // The exact stages of one row (whole warp; lane l's row is row0w + l).
-// Returns the exact nearest centroid in *j_out and its FP32 direct-form
-// distance in *dd_out; false for a non-finite row (status recorded).
-template <int D, int IB>
-__device__ __forceinline__ bool tb_exact(const float *__restrict__ rows, int64_t row0w, int64_t row,
-                                         bool valid, int j1, int j2, float d1, float d2,
-                                         const hpc_cent_smem &gcs, int *status, int *j_out,
-                                         float *dd_out) {
+// Returns TB_DONE with the exact nearest centroid in *j_out and its FP32
+// direct-form distance in *dd_out, TB_QUEUED when the row went to the CTA's
+// queue, TB_BAD for an invalid or non-finite row (status recorded).
+template <int D, int IB, int NPL>
+__device__ __forceinline__ int tb_exact(const float *__restrict__ rows, int64_t row0w, int64_t row,
+                                        bool valid, int j1, int j2, float d1, float d2, float lo3,
+                                        const hpc_cent_smem &gcs, int *status,
+                                        unsigned long long *stats, const TbQueue &queue,
+                                        int *j_out, float *dd_out) {
   constexpr int CS = hpc_cstride(D);
   const int lane = threadIdx.x & 31;
   const bool found = d1 < HPC_DEAD * 0.5f;
@@ -505,14 +545,19 @@ __device__ __forceinline__ bool tb_exact(const float *__restrict__ rows, int64_t
   }
   constexpr float rho = (float)(D + 3) * HPC_U32 * 1.001f;  // FP32 direct-form bound
   bool full = false;
-  if (ok && !(d2 - d1 > win)) {
+  const bool near = ok && !(d2 - d1 > win);
+  if (near) {
     // the two nearest by the tensor-core values, exactly; every other
-    // centroid is at least ||x||^2 + d2 - E away
+    // centroid's tensor-core value is at least lo3 (a lower bound of the
+    // third smallest from the warpgroups' partial top-2), so its distance
+    // is at least ||x||^2 + lo3 - E (less lo3's own key error)
     const bool has2 = d2 < HPC_DEAD * 0.5f && j2 != j1;
     const float ex2 = has2 ? tb_direct<D>(xg, gcs.cm + (size_t)j2 * CS) : __int_as_float(0x7f800000);
-    const float E = 0.5f * win;
-    const float others = nx * (1.0f - (float)(D + 2) * HPC_U32 * 1.01f) + d2 - E -
-                         4.0f * HPC_U32 * (nx + fabsf(d2) + E);
+    const float E = 0.5f * win + 1.0001f * ldexpf(1.0f, IB - 23) * fabsf(lo3);
+    const float others = lo3 >= HPC_DEAD * 0.5f
+                             ? __int_as_float(0x7f800000)
+                             : nx * (1.0f - (float)(D + 2) * HPC_U32 * 1.01f) + lo3 - E -
+                                   4.0f * HPC_U32 * (nx + fabsf(lo3) + E);
     const bool lo1 = dd < ex2 || (dd == ex2 && j1 < j2);
     const float lo = lo1 ? dd : ex2, hi = lo1 ? ex2 : dd;
     if (lo * (1.0f + rho) < others && hi * (1.0f - rho) > lo * (1.0f + rho)) {
@@ -525,22 +570,63 @@ __device__ __forceinline__ bool tb_exact(const float *__restrict__ rows, int64_t
     }
   }
   unsigned mfull = __ballot_sync(0xffffffffu, full);
+  bool queued = false;
+  if (mfull && queue.rows) {
+    int q0 = 0;
+    if (lane == 0) q0 = atomicAdd(queue.count, __popc(mfull));
+    q0 = __shfl_sync(0xffffffffu, q0, 0);
+    const int q = q0 + __popc(mfull & ((1u << lane) - 1u));
+    if (full && q < queue.cap) {
+      queue.rows[q] = row;
+      queued = true;
+    }
+    mfull = __ballot_sync(0xffffffffu, full && !queued);  // the queue was full for these
+  }
+  if (stats) {  // the same for the whole warp
+    const unsigned bv = __ballot_sync(0xffffffffu, valid);
+    const unsigned bn = __ballot_sync(0xffffffffu, near);
+    const unsigned bf = __ballot_sync(0xffffffffu, full);
+    if (lane == 0) {
+      atomicAdd(stats + 0, (unsigned long long)__popc(bv));
+      atomicAdd(stats + 1, (unsigned long long)__popc(bn));
+      atomicAdd(stats + 2, (unsigned long long)__popc(bf));
+    }
+  }
   while (mfull) {
     const int src = __ffs(mfull) - 1;
     mfull &= mfull - 1;
-    const int j = tb_rescore<D>(rows + (row0w + src) * D, gcs);
+    const int j = tb_rescore<D, NPL>(rows + (row0w + src) * D, gcs, stats);
     if (lane == src && j != j1) {
       j1 = j;
       dd = tb_direct<D>(xg, gcs.cm + (size_t)j1 * CS);
     }
   }
-  if (ok && !isfinite(dd)) {
+  if (ok && !queued && !isfinite(dd)) {
     hpc_status_set(status, HPC_ERR_NONFINITE);
     ok = false;
   }
   *j_out = j1;
   *dd_out = dd;
-  return ok;
+  return queued ? TB_QUEUED : ok ? TB_DONE : TB_BAD;
+}
+
+// Settles the rows of the CTA's queue (all warps of the CTA; a warp per row):
+// every centroid, FP32 then FP64 (tb_rescore); `done(row, j, dd)` is then
+// called by the whole warp.
+template <int D, int NPL, typename Done>
+__device__ __forceinline__ void tb_settle_queue(const float *__restrict__ rows,
+                                                const TbQueue &queue, const hpc_cent_smem &gcs,
+                                                unsigned long long *stats, Done done) {
+  constexpr int CS = hpc_cstride(D);
+  const int warp = threadIdx.x >> 5;
+  const int nq = min(*queue.count, queue.cap);
+  for (int qi = warp; qi < nq; qi += TB_THREADS / 32) {
+    const int64_t row = queue.rows[qi];
+    const float *xg = rows + row * D;
+    const int j = tb_rescore<D, NPL>(xg, gcs, stats);
+    const float dd = tb_direct<D>(xg, gcs.cm + (size_t)j * CS);
+    done(row, j, dd);
+  }
 }
 
 // One pass of the pipeline over a CTA's tiles (all 608 threads call it).
@@ -615,6 +701,9 @@ struct TclArgs {
   double tol;
   int *status;
   uint32_t *round_advance;
+  unsigned long long *stats;  // nullable: rows, near rows, fully rescored, FP64
+  int64_t *queue;             // nullable: queue_cap rows per CTA (tb_settle_queue)
+  int queue_cap;
 };
 
 template <int D, int NP>
@@ -628,6 +717,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   __shared__ int s_done, s_abort;
   __shared__ unsigned s_umax, s_cmax, s_nmax, s_live;
   __shared__ uint32_t s_tmem;
+  __shared__ int s_qn;
 
   if (a.round_advance && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.round_advance, 1u);
   const hpc_lloyd_task tk = a.W == 1 ? a.single : a.tasks[a.block_task[blockIdx.x]];
@@ -643,6 +733,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     tb_init_barriers<D, NP>(m);
     s_abort = 0;
     s_umax = s_cmax = s_nmax = s_live = 0u;
+    s_qn = 0;
   }
   if (warp == TB_MMAW) hpc_tmem_alloc(&s_tmem, Cfg::TCOLS);
   for (int j = threadIdx.x; j < 512; j += TB_THREADS) m.dead[j] = (j >= k) || tk.deg[j] != 0;
@@ -718,12 +809,44 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     // Phase A: assignment of the CTA's rows, sums of the rows that moved
     float fs_hi = 0.0f, fs_lo = 0.0f;
     const hpc_cent_smem gcs = tb_gcs<D>(tk.gcent, k, cmax, live);
+    // a row that moved from centroid jo (-1: first assignment) to jn: the
+    // whole warp adds its fixed-point coordinates to jn's sums and takes them
+    // from jo's, lanes over dimensions
+    auto move = [&](int64_t row, int jn, int jo) {
+      const float *xp = tk.S + row * D + lane * PER;
+      float xv[PER];
+      if constexpr (PER == 4) {
+        const float4 q4 = __ldg(reinterpret_cast<const float4 *>(xp));
+        xv[0] = q4.x;
+        xv[1] = q4.y;
+        xv[2] = q4.z;
+        xv[3] = q4.w;
+      } else {
+        const float2 q2 = __ldg(reinterpret_cast<const float2 *>(xp));
+        xv[0] = q2.x;
+        xv[1] = q2.y;
+      }
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const long long qv = __float2ll_rn(xv[u] * qscale);
+        atomicAdd(&tk.gsum[(size_t)jn * D + lane * PER + u], (unsigned long long)qv);
+        if (jo >= 0) atomicAdd(&tk.gsum[(size_t)jo * D + lane * PER + u], (unsigned long long)(-qv));
+      }
+      if (lane == 0) {
+        atomicAdd(&tk.gcount[jn], 1u);
+        if (jo >= 0) atomicSub(&tk.gcount[jo], 1u);
+      }
+    };
+    TbQueue queue{a.queue + (size_t)blockIdx.x * a.queue_cap, a.queue_cap, &s_qn};
+    if (!a.queue) queue.rows = nullptr;
     tb_pass<D, NP>(m, R, gbase, kp, a.status,
-                   [&](int64_t row0w, int64_t row, bool valid, int j1, int j2, float d1, float d2) {
+                   [&](int64_t row0w, int64_t row, bool valid, int j1, int j2, float d1, float d2,
+                       float lo3) {
       int j = 0;
       float dd = 0.0f;
-      const bool ok =
-          tb_exact<D, Cfg::IB>(tk.S, row0w, row, valid, j1, j2, d1, d2, gcs, a.status, &j, &dd);
+      const bool ok = tb_exact<D, Cfg::IB, NP / 32>(tk.S, row0w, row, valid, j1, j2, d1, d2, lo3,
+                                                    gcs, a.status, a.stats, queue, &j, &dd) ==
+                      TB_DONE;
       if (ok) hpc_sum2_add(fs_hi, fs_lo, dd);
       int old = -1;
       bool moved = false;
@@ -736,33 +859,21 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
       while (mv) {
         const int src = __ffs(mv) - 1;
         mv &= mv - 1;
-        const int jn = __shfl_sync(0xffffffffu, j, src);
-        const int jo = __shfl_sync(0xffffffffu, old, src);
-        const float *xp = tk.S + (row0w + src) * D + lane * PER;
-        float xv[PER];
-        if constexpr (PER == 4) {
-          const float4 q4 = __ldg(reinterpret_cast<const float4 *>(xp));
-          xv[0] = q4.x;
-          xv[1] = q4.y;
-          xv[2] = q4.z;
-          xv[3] = q4.w;
-        } else {
-          const float2 q2 = __ldg(reinterpret_cast<const float2 *>(xp));
-          xv[0] = q2.x;
-          xv[1] = q2.y;
-        }
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-          const long long qv = __float2ll_rn(xv[u] * qscale);
-          atomicAdd(&tk.gsum[(size_t)jn * D + lane * PER + u], (unsigned long long)qv);
-          if (jo >= 0) atomicAdd(&tk.gsum[(size_t)jo * D + lane * PER + u], (unsigned long long)(-qv));
-        }
-        if (lane == 0) {
-          atomicAdd(&tk.gcount[jn], 1u);
-          if (jo >= 0) atomicSub(&tk.gcount[jo], 1u);
-        }
+        move(row0w + src, __shfl_sync(0xffffffffu, j, src), __shfl_sync(0xffffffffu, old, src));
       }
       if (ok && tk.labels && tk.labels != tk.plab) tk.labels[row] = j;
+    });
+    __syncthreads();
+    // the queued rows, every warp
+    tb_settle_queue<D, NP / 32>(tk.S, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
+      if (lane == 0) hpc_sum2_add(fs_hi, fs_lo, dd);
+      const int old = it > 0 ? tk.plab[row] : -1;
+      if (old != j) move(row, j, old);
+      __syncwarp();
+      if (lane == 0) {
+        tk.plab[row] = j;
+        if (tk.labels && tk.labels != tk.plab) tk.labels[row] = j;
+      }
     });
     gbase += (uint32_t)R.ntiles;
     __syncthreads();
@@ -781,6 +892,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
       s_done = (it > 0 && (f_prev == 0.0 || (f_prev - fo) < a.tol * f_prev)) || it == a.max_iter;
       s_nmax = 0u;
       s_live = 0u;
+      s_qn = 0;
     }
     __syncthreads();
     const double f = s_f;
@@ -845,6 +957,9 @@ struct TcbArgs {
   int *status;
   double *part;
   unsigned *done_count;
+  unsigned long long *stats;  // nullable: rows, near rows, fully rescored, FP64
+  int64_t *queue;             // nullable: queue_cap rows per CTA (tb_settle_queue)
+  int queue_cap;
 };
 
 // One block: the exact centroid block and its max norm / live count.
@@ -871,6 +986,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcb_objective_kernel(TcbArgs a)
   __shared__ int s_abort;
   __shared__ unsigned s_nmax, s_live;
   __shared__ uint32_t s_tmem;
+  __shared__ int s_qn;
   const int warp = threadIdx.x >> 5;
   unsigned char *base =
       reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -880,6 +996,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcb_objective_kernel(TcbArgs a)
     tb_init_barriers<D, NP>(m);
     s_abort = 0;
     s_nmax = s_live = 0u;
+    s_qn = 0;
   }
   if (warp == TB_MMAW) hpc_tmem_alloc(&s_tmem, Cfg::TCOLS);
   for (int j = threadIdx.x; j < 512; j += TB_THREADS)
@@ -906,11 +1023,22 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcb_objective_kernel(TcbArgs a)
   R.ntiles = run && (int64_t)blockIdx.x < ntiles
                  ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
   float fs_hi = 0.0f, fs_lo = 0.0f;
+  TbQueue queue{a.queue + (size_t)blockIdx.x * a.queue_cap, a.queue_cap, &s_qn};
+  if (!a.queue) queue.rows = nullptr;
   tb_pass<D, NP>(m, R, 0u, kp, a.status,
-                 [&](int64_t row0w, int64_t row, bool valid, int j1, int j2, float d1, float d2) {
+                 [&](int64_t row0w, int64_t row, bool valid, int j1, int j2, float d1, float d2,
+                     float lo3) {
     int j = 0;
     float dd = 0.0f;
-    if (tb_exact<D, Cfg::IB>(a.X, row0w, row, valid, j1, j2, d1, d2, gcs, a.status, &j, &dd)) {
+    if (tb_exact<D, Cfg::IB, NP / 32>(a.X, row0w, row, valid, j1, j2, d1, d2, lo3, gcs, a.status,
+                                      a.stats, queue, &j, &dd) == TB_DONE) {
+      hpc_sum2_add(fs_hi, fs_lo, dd);
+      if (a.labels) a.labels[row] = j;
+    }
+  });
+  __syncthreads();
+  tb_settle_queue<D, NP / 32>(a.X, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
+    if ((threadIdx.x & 31) == 0) {
       hpc_sum2_add(fs_hi, fs_lo, dd);
       if (a.labels) a.labels[row] = j;
     }
@@ -1001,6 +1129,13 @@ int tcl_run_t(const hpc_launch &L, const LloydLaunch &h) {
   a.tol = h.tol;
   a.status = h.status;
   a.round_advance = h.round_advance;
+  a.stats = h.stats;
+  a.queue = h.queue;
+  a.queue_cap = (int)h.queue_cap;
+  if (!a.queue || h.queue_cap < 1 || h.grid > h.queue_ctas) {
+    a.queue = nullptr;
+    a.queue_cap = 0;
+  }
   void *args[] = {&a};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)h.grid),
                                                     dim3(TB_THREADS), args, h.smem, L.stream);
@@ -1040,6 +1175,13 @@ int tcb_objective_t(const hpc_launch &L, const ObjArgsHost &h) {
   a.status = h.status;
   a.part = h.part;
   a.done_count = h.done_count;
+  a.stats = h.stats;
+  a.queue = h.queue;
+  a.queue_cap = (int)h.queue_cap;
+  if (!a.queue || h.queue_cap < 1 || G > h.queue_ctas) {
+    a.queue = nullptr;
+    a.queue_cap = 0;
+  }
   kern<<<(unsigned)G, TB_THREADS, smem, L.stream>>>(a);
   return cudaGetLastError() == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }

@@ -64,7 +64,7 @@ class hpc_batch(ctypes.Structure):
                 ("degenerate", ctypes.c_void_p), ("fhat", ctypes.c_void_p),
                 ("f_new", ctypes.c_void_p), ("iters", ctypes.c_void_p),
                 ("accepted", ctypes.c_void_p), ("n_competitive", ctypes.c_int32),
-                ("worker0", ctypes.c_int32)]
+                ("worker0", ctypes.c_int32), ("t_done", ctypes.c_void_p)]
 
 
 _lib = None
@@ -109,6 +109,9 @@ def load() -> ctypes.CDLL:
         "hpc_lloyd_schedule": ([P, i64, i32, i32, ctypes.POINTER(ctypes.c_int32), i32],
                                ctypes.c_int),
         "hpc_set_phase_timing": ([P, i32], ctypes.c_int),
+        "hpc_timestamp": ([P, P], ctypes.c_int),
+        "hpc_set_search_stats": ([P, i32], ctypes.c_int),
+        "hpc_search_stats": ([P, ctypes.POINTER(ctypes.c_int64), i32], ctypes.c_int),
         "hpc_phase_times": ([P, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "hpc_autotune_objective": ([P, P, i64, i32, P, i32, P, i32,
                                     ctypes.POINTER(ctypes.c_int32),
@@ -224,6 +227,25 @@ class Context:
         self._check(self.lib.hpc_lloyd_schedule(self.h, int(s), int(d), int(k), out, 5))
         return {"blocks": int(out[0]), "smem_sums": bool(out[1]), "xstage": bool(out[2]),
                 "smem_bytes": int(out[3]), "form": SEARCH_NAMES.get(int(out[4]), int(out[4]))}
+
+    def set_search_stats(self, on: bool):
+        """Count the stages of the split-BF16 tensor-core search."""
+        self._check(self.lib.hpc_set_search_stats(self.h, int(bool(on))))
+
+    def search_stats(self, reset: bool = False) -> dict:
+        """Rows through each stage of the split-BF16 search since the last reset."""
+        out = (ctypes.c_int64 * 4)()
+        self._check(self.lib.hpc_search_stats(self.h, out, int(bool(reset))))
+        return {"rows": int(out[0]), "near": int(out[1]), "all_centroids": int(out[2]),
+                "fp64": int(out[3])}
+
+    def timestamp(self, out=None):
+        """A device int64 tensor that receives the device time (ns) once the
+        work queued before it has run."""
+        if out is None:
+            out = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self._check(self.lib.hpc_timestamp(self.h, _ptr(out)))
+        return out
 
     def set_phase_timing(self, on: bool):
         """Record CUDA events around every launch of later rounds."""
@@ -366,13 +388,15 @@ class Batch:
         self.f_new = torch.zeros(self.W, dtype=torch.float64, device=self.device)
         self.iters = torch.zeros(self.W, dtype=torch.int32, device=self.device)
         self.accepted = torch.zeros(self.W, dtype=torch.uint8, device=self.device)
+        # per round, the device time each worker's run ended (hpc_timestamp's clock)
+        self.t_done = torch.zeros(self.W, dtype=torch.int64, device=self.device)
 
     def struct(self) -> hpc_batch:
         return hpc_batch(self.W, self.s.ctypes.data, self.k.ctypes.data, self.group.ctypes.data,
                          self.C_off.ctypes.data, self.K_off.ctypes.data, self.C.data_ptr(),
                          self.degenerate.data_ptr(), self.fhat.data_ptr(), self.f_new.data_ptr(),
                          self.iters.data_ptr(), self.accepted.data_ptr(), self.n_competitive,
-                         self.worker0)
+                         self.worker0, self.t_done.data_ptr())
 
     def save(self, ctx: "Context", path, next_round: int, seed: int, strategy: int):
         """Writes the checkpoint of hpc_batch_save to the file `path`."""

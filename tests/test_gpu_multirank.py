@@ -94,5 +94,7 @@ def test_row_block_objective(ctx, data):
         a, b = MR.row_range(X.shape[0], 3, r)
         parts += float(H.hpc_objective(ctx, X[a:b], C).item())
     ctx.check_status()
-    assert parts == pytest.approx(whole, rel=1e-12)
+    # row blocks regroup the rows each thread adds (FP32 sums of a few rows
+    # before the pair), about 1e-9 of the total; the contract is 1e-6
+    assert parts == pytest.approx(whole, rel=1e-8)
     assert whole == pytest.approx(orc.objective(Xh, Xh[:12]), rel=1e-6)
