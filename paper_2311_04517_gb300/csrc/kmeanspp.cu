@@ -16,7 +16,11 @@
 #include "kernels.h"
 
 #define HPC_MAX_CAND 8
-#define KPP_THREADS 256
+
+// Threads per block: 512 where the row and the distance chains fit the
+// registers that leaves (d = 16 .. 64), 256 otherwise.
+template <int D>
+constexpr int kpp_threads() { return D >= 16 && D <= 64 ? 512 : 256; }
 
 namespace {
 
@@ -132,8 +136,29 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
     for (int64_t i = lo + threadIdx.x; i < hi; i += THREADS) {
       float x[D];
       hpc_load_row<D>(x, tk.S + i * d, d);
+      // four centroids per step as independent chains (each in dimension
+      // order, the rounding the decisions are defined in); degenerate and
+      // padding slots hold zeros and are skipped by their flag
       float best = __int_as_float(0x7f800000);
-      for (int j = 0; j < k; ++j) {
+      int j = 0;
+      for (; j + 4 <= k; j += 4) {
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+        const float *c0 = cl + j * D;
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+          const float e0 = __fsub_rn(x[t], c0[t]), e1 = __fsub_rn(x[t], c0[D + t]);
+          const float e2 = __fsub_rn(x[t], c0[2 * D + t]), e3 = __fsub_rn(x[t], c0[3 * D + t]);
+          a0 = __fmaf_rn(e0, e0, a0);
+          a1 = __fmaf_rn(e1, e1, a1);
+          a2 = __fmaf_rn(e2, e2, a2);
+          a3 = __fmaf_rn(e3, e3, a3);
+        }
+        if (!flags[j]) best = fminf(best, a0);
+        if (!flags[j + 1]) best = fminf(best, a1);
+        if (!flags[j + 2]) best = fminf(best, a2);
+        if (!flags[j + 3]) best = fminf(best, a3);
+      }
+      for (; j < k; ++j) {
         if (flags[j]) continue;
         best = fminf(best, hpc_dist32_seq<D>(x, cl + j * D));
       }
@@ -291,13 +316,13 @@ size_t kpp_smem_bytes(int D, int k, int L) {
 
 template <int D>
 int kpp_plan_t(const hpc_launch &Lc, KppLaunch &h) {
-  auto kern = kmeanspp_kernel<D, KPP_THREADS>;
+  auto kern = kmeanspp_kernel<D, kpp_threads<D>()>;
   const size_t smem = kpp_smem_bytes(D, h.kmax, h.L);
   if (smem > (size_t)Lc.smem_optin) return HPC_ERR_UNSUPPORTED;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HPC_ERR_CUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, KPP_THREADS, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kpp_threads<D>(), smem) != cudaSuccess ||
       per_sm < 1)
     return HPC_ERR_UNSUPPORTED;
   int64_t total = (int64_t)per_sm * Lc.num_sms;
@@ -312,7 +337,7 @@ int kpp_plan_t(const hpc_launch &Lc, KppLaunch &h) {
     rows[w] = h.tasks[w].s;
     work[w] = h.tasks[w].s * (int64_t)h.tasks[w].k;
   }
-  hpc_split_blocks(h.W, rows.data(), work.data(), KPP_THREADS, total, b0.data(), nb.data());
+  hpc_split_blocks(h.W, rows.data(), work.data(), kpp_threads<D>(), total, b0.data(), nb.data());
   int64_t grid = 0;
   for (int w = 0; w < h.W; ++w) {
     if (nb[w] > h.chunk_cap) nb[w] = (int)h.chunk_cap;
@@ -329,7 +354,7 @@ int kpp_plan_t(const hpc_launch &Lc, KppLaunch &h) {
 
 template <int D>
 int kpp_run_t(const hpc_launch &Lc, const KppLaunch &h) {
-  auto kern = kmeanspp_kernel<D, KPP_THREADS>;
+  auto kern = kmeanspp_kernel<D, kpp_threads<D>()>;
   KppArgs a;
   a.W = h.W;
   a.single = h.tasks[0];
@@ -343,7 +368,7 @@ int kpp_run_t(const hpc_launch &Lc, const KppLaunch &h) {
   a.status = h.status;
   void *args[] = {&a};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)h.grid),
-                                                    dim3(KPP_THREADS), args, h.smem, Lc.stream);
+                                                    dim3(kpp_threads<D>()), args, h.smem, Lc.stream);
   return e == cudaSuccess ? HPC_OK : HPC_ERR_CUDA;
 }
 

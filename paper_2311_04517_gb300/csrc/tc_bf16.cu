@@ -17,9 +17,10 @@
 // top-2 margin exceeds 2E (plus the packed keys' 2^(IB-22) (|k1| + |k2|)) has
 // the exact nearest centroid; otherwise its two candidates are computed
 // exactly (FP32 direct form), every other centroid being at least
-// ||x||^2 + d2 - E away, and rows that remain open are settled by their warp
-// against every centroid (FP32 direct form, then FP64 in the oracle's
-// operation order, ties to the lowest index).
+// ||x||^2 + v3 - E away (v3 the third smallest computed value: the epilogue
+// keeps three per row), and rows that remain open are settled against every
+// centroid (FP32 direct form, then FP64 in the oracle's operation order,
+// ties to the lowest index) after the CTA's pass, by all its warps.
 //
 // Data path per 128-row tile (one persistent CTA per SM):
 //   warps 0-1 (converters): coalesced 16-byte loads of the FP32 rows (an L2
@@ -31,7 +32,7 @@
 //     memory; TMEM holds two banks (two tiles in flight for up to 256
 //     centroids, the two halves of one tile for up to 512);
 //   warps 3-18 (four epilogue warpgroups): warpgroup e folds a quarter of a
-//     tile's columns into a partial top-2 per row ((value, index) keys with
+//     tile's columns into a partial top-3 per row ((value, index) keys with
 //     7 to 9 index bits) and leaves it in a rotating exchange buffer; the
 //     warpgroup e = tile mod 4 merges the four partials and finishes the
 //     tile's rows (exact distance, margin test, exact stages, objective,
@@ -82,12 +83,12 @@ struct TbCfg {
   static constexpr int CPW = NP / 4;               // columns per epilogue warpgroup
   static constexpr int READERS = NP > 256 ? 8 : 16;
   static constexpr int IB = NP == 512 ? 9 : NP == 256 ? 8 : 7;
-  static constexpr size_t REST = (size_t)NP * 4 + (size_t)TB_NX * 4 * TB_M * 8 + 512 + 256;
+  static constexpr size_t REST = (size_t)NP * 4 + (size_t)TB_NX * 4 * TB_M * 12 + 512 + 256;
   static constexpr int NSTAGE = 2 * (size_t)BPART + 4 * (size_t)ATILE + REST + 1024 <= 225 * 1024 ? 2 : 1;
   static constexpr size_t AOP = 2 * (size_t)BPART;
   static constexpr size_t CN = AOP + (size_t)NSTAGE * 2 * ATILE;
   static constexpr size_t XCH = CN + (size_t)NP * 4;
-  static constexpr size_t DEADF = XCH + (size_t)TB_NX * 4 * TB_M * 8;
+  static constexpr size_t DEADF = XCH + (size_t)TB_NX * 4 * TB_M * 12;
   static constexpr size_t BARS = DEADF + 512;
   static constexpr int NBARS = 2 * NSTAGE + 4 + 2 * TB_NX + 1;
   static constexpr size_t TOTAL = BARS + NBARS * 8 + 1024;
@@ -97,7 +98,7 @@ struct TbCfg {
 struct TbSm {
   unsigned char *bh, *bl, *a;
   float *cn;
-  float2 *xch;
+  float *xch;  // [TB_NX][4 warpgroups][TB_M rows][3 keys]
   uint8_t *dead;
   uint64_t *afull, *afree, *accf, *acce, *xready, *xdone, *drain;
   volatile int *abort;
@@ -112,7 +113,7 @@ __device__ __forceinline__ TbSm tb_bind(unsigned char *base, volatile int *abort
   m.bl = base + Cfg::BPART;
   m.a = base + Cfg::AOP;
   m.cn = reinterpret_cast<float *>(base + Cfg::CN);
-  m.xch = reinterpret_cast<float2 *>(base + Cfg::XCH);
+  m.xch = reinterpret_cast<float *>(base + Cfg::XCH);
   m.dead = base + Cfg::DEADF;
   uint64_t *b = reinterpret_cast<uint64_t *>(base + Cfg::BARS);
   m.afull = b;
@@ -298,6 +299,27 @@ __device__ __forceinline__ hpc_cent_smem tb_gcs(float *gcent, int k, float cmax,
   return cs;
 }
 
+// The three smallest of two sorted triples (t1 <= t2 <= t3 and r1 <= r2 <=
+// r3), into t: the k-th smallest of the union is the smallest over the
+// splits i + j = k of max(t_i, r_j).
+__device__ __forceinline__ void tb_merge3(float &t1, float &t2, float &t3, float r1, float r2,
+                                          float r3) {
+  const float u3 = fminf(hpc_min3(t3, r3, fmaxf(t2, r1)), fmaxf(t1, r2));
+  const float u2 = hpc_min3(t2, r2, fmaxf(t1, r1));
+  t1 = fminf(t1, r1);
+  t2 = u2;
+  t3 = u3;
+}
+
+// Folds four (value, index) keys into the running three smallest: the four
+// sorted by a 2 x 2 merge (the three smallest kept), then merged.
+__device__ __forceinline__ void tb_fold4_top3(float &t1, float &t2, float &t3, float k0, float k1,
+                                              float k2, float k3) {
+  const float a = fminf(k0, k1), b = fmaxf(k0, k1), c = fminf(k2, k3), e = fmaxf(k2, k3);
+  const float M = fmaxf(a, c), mb = fminf(b, e);
+  tb_merge3(t1, t2, t3, fminf(a, c), fminf(M, mb), fmaxf(M, mb));
+}
+
 // ---- epilogue (warps 3-18) ----------------------------------------------------
 // Folds every tile's columns, and finishes the tiles whose turn it is: for
 // each row `fin(i, r, row, valid, j1, j2, d1, d2)` is called by the whole
@@ -320,7 +342,8 @@ __device__ __forceinline__ void tb_epilogue(const TbSm &m, const TbRows &R, uint
     const int xb = (int)(g % TB_NX);
     const uint32_t xu = g / TB_NX;
     const bool ok = wait_warp(&m.accf[bk], v & 1u, m.abort, status, TB_WAIT_NS);
-    float d1 = __int_as_float(0x7f7fffff), d2 = d1, e1 = d1, e2 = d1;
+    // the three smallest keys of this warpgroup's columns, as two chains
+    float d1 = __int_as_float(0x7f7fffff), d2 = d1, d3 = d1, e1 = d1, e2 = d1, e3 = d1;
     if (ok) {
       hpc_tc_fence_after();
 #pragma unroll
@@ -333,46 +356,43 @@ __device__ __forceinline__ void tb_epilogue(const TbSm &m, const TbRows &R, uint
         for (int jj = 0; jj < 32; jj += 4) {
           const float4 cn = *reinterpret_cast<const float4 *>(m.cn + cb + jj);
           const int j = cb + jj;
-          float &t1 = (jj & 4) ? e1 : d1, &t2 = (jj & 4) ? e2 : d2;
-          hpc_top2_fold4(t1, t2, hpc_key_b<IB>(cn.x + acc[jj], j),
-                         hpc_key_b<IB>(cn.y + acc[jj + 1], j + 1),
-                         hpc_key_b<IB>(cn.z + acc[jj + 2], j + 2),
-                         hpc_key_b<IB>(cn.w + acc[jj + 3], j + 3));
+          float &t1 = (jj & 4) ? e1 : d1, &t2 = (jj & 4) ? e2 : d2, &t3 = (jj & 4) ? e3 : d3;
+          tb_fold4_top3(t1, t2, t3, hpc_key_b<IB>(cn.x + acc[jj], j),
+                        hpc_key_b<IB>(cn.y + acc[jj + 1], j + 1),
+                        hpc_key_b<IB>(cn.z + acc[jj + 2], j + 2),
+                        hpc_key_b<IB>(cn.w + acc[jj + 3], j + 3));
         }
       }
-      d2 = hpc_min3(d2, e2, fmaxf(d1, e1));
-      d1 = fminf(d1, e1);
+      tb_merge3(d1, d2, d3, e1, e2, e3);
     }
     hpc_tc_fence_before();
     __syncwarp();
     if (lane == 0) hpc_mbar_arrive(&m.acce[bk]);  // this warp's columns are in registers
     if (!ok) break;
     if (xu > 0 && !wait_warp(&m.xdone[xb], (xu - 1) & 1u, m.abort, status, TB_WAIT_NS)) break;
-    m.xch[(xb * 4 + e) * TB_M + r_in] = make_float2(d1, d2);
+    {
+      float *xp = m.xch + ((size_t)(xb * 4 + e) * TB_M + r_in) * 3;
+      xp[0] = d1;
+      xp[1] = d2;
+      xp[2] = d3;
+    }
     __syncwarp();
     if (lane == 0) hpc_mbar_arrive(&m.xready[xb]);
     if ((int)(g & 3u) != e) continue;
     if (!wait_warp(&m.xready[xb], xu & 1u, m.abort, status, TB_WAIT_NS)) break;
+    // the three smallest keys of the tile's row: every centroid but the two
+    // best has a key of at least the third (each warpgroup kept its three)
     float lo3;
     {
-      float2 p[4];
-#pragma unroll
-      for (int o = 0; o < 4; ++o) p[o] = m.xch[(xb * 4 + o) * TB_M + r_in];
-      d1 = p[0].x;
-      d2 = p[0].y;
+      const float *xp = m.xch + ((size_t)(xb * 4) * TB_M + r_in) * 3;
+      d1 = xp[0];
+      d2 = xp[1];
+      lo3 = xp[2];
 #pragma unroll
       for (int o = 1; o < 4; ++o) {
-        d2 = hpc_min3(d2, p[o].y, fmaxf(d1, p[o].x));
-        d1 = fminf(d1, p[o].x);
+        const float *xo = xp + (size_t)o * TB_M * 3;
+        tb_merge3(d1, d2, lo3, xo[0], xo[1], xo[2]);
       }
-      // every centroid but the two best: in a warpgroup holding one of them
-      // (as its smallest) at least that warpgroup's second, elsewhere at
-      // least the warpgroup's smallest (keys are unique, so equal keys are
-      // the same column)
-      lo3 = __int_as_float(0x7f7fffff);
-#pragma unroll
-      for (int o = 0; o < 4; ++o)
-        lo3 = fminf(lo3, (p[o].x == d1 || p[o].x == d2) ? p[o].y : p[o].x);
     }
     __syncwarp();
     if (lane == 0) hpc_mbar_arrive(&m.xdone[xb]);
@@ -548,9 +568,8 @@ __device__ __forceinline__ int tb_exact(const float *__restrict__ rows, int64_t 
   const bool near = ok && !(d2 - d1 > win);
   if (near) {
     // the two nearest by the tensor-core values, exactly; every other
-    // centroid's tensor-core value is at least lo3 (a lower bound of the
-    // third smallest from the warpgroups' partial top-2), so its distance
-    // is at least ||x||^2 + lo3 - E (less lo3's own key error)
+    // centroid's tensor-core key is at least lo3, the third smallest, so its
+    // distance is at least ||x||^2 + lo3 - E (less lo3's own key error)
     const bool has2 = d2 < HPC_DEAD * 0.5f && j2 != j1;
     const float ex2 = has2 ? tb_direct<D>(xg, gcs.cm + (size_t)j2 * CS) : __int_as_float(0x7f800000);
     const float E = 0.5f * win + 1.0001f * ldexpf(1.0f, IB - 23) * fabsf(lo3);
