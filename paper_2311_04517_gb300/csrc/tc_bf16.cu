@@ -31,12 +31,14 @@
 //     MMAs per 256-column bank against B = (c_h | c_l) resident in shared
 //     memory; TMEM holds two banks (two tiles in flight for up to 256
 //     centroids, the two halves of one tile for up to 512);
-//   warps 3-18 (four epilogue warpgroups): warpgroup e folds a quarter of a
-//     tile's columns into a partial top-3 per row ((value, index) keys with
-//     7 to 9 index bits) and leaves it in a rotating exchange buffer; the
-//     warpgroup e = tile mod 4 merges the four partials and finishes the
-//     tile's rows (exact distance, margin test, exact stages, objective,
-//     labels, and in Lloyd the centroid sums).
+//   warps 3-18 (four fold warpgroups): warpgroup e folds a quarter of a
+//     tile's columns into the three smallest (value, index) keys per row
+//     (7 to 9 index bits) and leaves them in a rotating exchange buffer;
+//   warps 19-26 (two finisher warpgroups): warpgroup f takes every second
+//     tile, merges the four partial top-3 of each row and finishes the row
+//     (exact distance, margin test, exact stages, objective, labels, and in
+//     Lloyd the centroid sums), so that the fold warps, which release the
+//     TMEM banks, never wait on a row's global loads.
 //
 // Lloyd's centroid sums are kept incrementally: every coordinate goes on the
 // exact 64-bit fixed-point grid 2^-Fs of the CUDA-core kernel, the first
@@ -64,8 +66,10 @@ namespace {
 constexpr int TB_M = 128;
 constexpr int TB_CONV = 2;                       // converter warps 0, 1
 constexpr int TB_MMAW = 2;                       // TMEM owner and MMA issuer
-constexpr int TB_EPI0 = 3;                       // first epilogue warp
-constexpr int TB_THREADS = (TB_EPI0 + 16) * 32;  // 608
+constexpr int TB_EPI0 = 3;                       // first fold warp (four warpgroups)
+constexpr int TB_FIN0 = TB_EPI0 + 16;            // first finisher warp (two warpgroups)
+constexpr int TB_NFIN = 2;                       // finisher warpgroups
+constexpr int TB_THREADS = (TB_FIN0 + 4 * TB_NFIN) * 32;  // 864
 constexpr int TB_NX = 4;                         // exchange buffers
 constexpr uint64_t TB_WAIT_NS = 2000000000ull;
 constexpr uint64_t TB_DRAIN_NS = 500000000ull;
@@ -140,8 +144,8 @@ __device__ __forceinline__ void tb_init_barriers(const TbSm &m) {
     hpc_mbar_init(&m.acce[b], Cfg::READERS);
   }
   for (int b = 0; b < TB_NX; ++b) {
-    hpc_mbar_init(&m.xready[b], 16);
-    hpc_mbar_init(&m.xdone[b], 4);
+    hpc_mbar_init(&m.xready[b], 16);  // the fold warps
+    hpc_mbar_init(&m.xdone[b], 4);    // the finisher warpgroup's warps
   }
   hpc_mbar_init(m.drain, 1);
   hpc_fence_barrier_init();
@@ -320,13 +324,13 @@ __device__ __forceinline__ void tb_fold4_top3(float &t1, float &t2, float &t3, f
   tb_merge3(t1, t2, t3, fminf(a, c), fminf(M, mb), fmaxf(M, mb));
 }
 
-// ---- epilogue (warps 3-18) ----------------------------------------------------
-// Folds every tile's columns, and finishes the tiles whose turn it is: for
-// each row `fin(i, r, row, valid, j1, j2, d1, d2)` is called by the whole
-// warp (lane l holds row 32 q + l of the tile).
-template <int D, int NP, typename Fin>
-__device__ __forceinline__ void tb_epilogue(const TbSm &m, const TbRows &R, uint32_t gbase, int kp, int *status,
-                            Fin fin) {
+// ---- fold warps (warps 3-18) -------------------------------------------------
+// Warpgroup e folds columns [e NP/4, (e+1) NP/4) of every tile into the
+// three smallest (value, index) keys per row and leaves them in the tile's
+// exchange buffer (the finishers merge the four).
+template <int D, int NP>
+__device__ __forceinline__ void tb_fold(const TbSm &m, const TbRows &R, uint32_t gbase, int kp,
+                                        int *status) {
   using Cfg = TbCfg<D, NP>;
   constexpr int IB = Cfg::IB;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -378,11 +382,31 @@ __device__ __forceinline__ void tb_epilogue(const TbSm &m, const TbRows &R, uint
     }
     __syncwarp();
     if (lane == 0) hpc_mbar_arrive(&m.xready[xb]);
-    if ((int)(g & 3u) != e) continue;
+  }
+}
+
+// ---- finishers (warps 19-26) ----------------------------------------------------
+// Finisher warpgroup f takes the tiles g with g mod TB_NFIN == f: merges the
+// four partial top-3 of each row, frees the exchange buffer, and calls
+// `fin(row0w, row, valid, j1, j2, d1, d2, v3)` with the whole warp (lane l
+// holds row 32 q + l of the tile).
+template <int D, int NP, typename Fin>
+__device__ __forceinline__ void tb_finish(const TbSm &m, const TbRows &R, uint32_t gbase, int kp,
+                                          int *status, Fin fin) {
+  using Cfg = TbCfg<D, NP>;
+  constexpr int IB = Cfg::IB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = (warp - TB_FIN0) >> 2, q = warp & 3;
+  const int r_in = 32 * q + lane;
+  for (int i = 0; i < R.ntiles; ++i) {
+    const uint32_t g = gbase + (uint32_t)i;
+    if ((int)(g % TB_NFIN) != f) continue;
+    const int xb = (int)(g % TB_NX);
+    const uint32_t xu = g / TB_NX;
     if (!wait_warp(&m.xready[xb], xu & 1u, m.abort, status, TB_WAIT_NS)) break;
     // the three smallest keys of the tile's row: every centroid but the two
     // best has a key of at least the third (each warpgroup kept its three)
-    float lo3;
+    float d1, d2, lo3;
     {
       const float *xp = m.xch + ((size_t)(xb * 4) * TB_M + r_in) * 3;
       d1 = xp[0];
@@ -658,8 +682,10 @@ __device__ __forceinline__ void tb_pass(const TbSm &m, const TbRows &R, uint32_t
   } else if (warp == TB_MMAW) {
     if ((threadIdx.x & 31) == 0) tb_mma<D, NP>(m, R, gbase, status);
     __syncwarp();
+  } else if (warp < TB_FIN0) {
+    tb_fold<D, NP>(m, R, gbase, kp, status);
   } else {
-    tb_epilogue<D, NP>(m, R, gbase, kp, status, fin);
+    tb_finish<D, NP>(m, R, gbase, kp, status, fin);
   }
 }
 

@@ -119,15 +119,23 @@ def make_data(wl: Workload | str, device="cpu", seed: int | None = None, n: int 
     return X
 
 
+def scaling_params(seed: int = 0):
+    """The Section 6.8 blobs: means (10 x 10, uniform in (-40, 40)) and sds
+    (10, uniform in (0, 10)), float64 on the CPU."""
+    g = torch.Generator().manual_seed(seed)
+    mu = -40 + 80 * torch.rand(10, 10, generator=g, dtype=torch.float64)
+    sd = 10 * torch.rand(10, generator=g, dtype=torch.float64)
+    return mu, sd
+
+
 def scaling_data(i: int, device="cpu", seed: int = 0) -> torch.Tensor:
     """Section 6.8 scaling set: 10 blobs in (-40, 40)^10, sd ~ U(0, 10),
     m = 3^(i+7) points, plus 500 uniform noise points in (-50, 50)^10
     (the noise rows last)."""
     m = 3 ** (i + 7)
     device = torch.device(device)
-    g = torch.Generator().manual_seed(seed)
-    mu = (-40 + 80 * torch.rand(10, 10, generator=g, dtype=torch.float64)).to(device)
-    sd = (10 * torch.rand(10, generator=g, dtype=torch.float64)).to(device)
+    mu, sd = scaling_params(seed)
+    mu, sd = mu.to(device), sd.to(device)
     gd = torch.Generator(device=device).manual_seed(int(seed) * 7919 + 3)
     X = torch.empty((m + 500, 10), dtype=torch.float32, device=device)
     chunk = 4_000_000
