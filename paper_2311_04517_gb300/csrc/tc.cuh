@@ -175,6 +175,18 @@ __device__ __forceinline__ void hpc_prefetch_l2_bulk(const void *p, uint32_t byt
                : "memory");
 }
 
+// Copies `bytes` (a multiple of 16) from global memory at `src` to this CTA's
+// shared memory at `dst` (both 16-byte aligned) as one bulk copy, whose
+// bytes complete the transaction count of *bar.
+__device__ __forceinline__ void hpc_bulk_load(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          hpc_smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(hpc_smem_u32(bar))
+      : "memory");
+}
+
 // Arrives once on *bar when every MMA issued so far by this thread is done.
 __device__ __forceinline__ void hpc_mma_commit(uint64_t *bar) {
   asm volatile(

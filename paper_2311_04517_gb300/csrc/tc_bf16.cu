@@ -70,7 +70,8 @@ constexpr int TB_EPI0 = 3;                       // first fold warp (four warpgr
 constexpr int TB_FIN0 = TB_EPI0 + 16;            // first finisher warp (two warpgroups)
 constexpr int TB_NFIN = 2;                       // finisher warpgroups
 constexpr int TB_THREADS = (TB_FIN0 + 4 * TB_NFIN) * 32;  // 864
-constexpr int TB_NX = 4;                         // exchange buffers
+constexpr uint32_t TB_SLOT = 4096;               // bytes of one row-ring slot
+constexpr size_t TB_SMEM_MAX = 226 * 1024;       // dynamic shared memory of one CTA (static: < 1 KB)
 constexpr uint64_t TB_WAIT_NS = 2000000000ull;
 constexpr uint64_t TB_DRAIN_NS = 500000000ull;
 constexpr float TB_E_REL = 6.103515625e-05f;     // 2^-14
@@ -87,24 +88,40 @@ struct TbCfg {
   static constexpr int CPW = NP / 4;               // columns per epilogue warpgroup
   static constexpr int READERS = NP > 256 ? 8 : 16;
   static constexpr int IB = NP == 512 ? 9 : NP == 256 ? 8 : 7;
-  static constexpr size_t REST = (size_t)NP * 4 + (size_t)TB_NX * 4 * TB_M * 12 + 512 + 256;
-  static constexpr int NSTAGE = 2 * (size_t)BPART + 4 * (size_t)ATILE + REST + 1024 <= 225 * 1024 ? 2 : 1;
+  static constexpr int RS = TB_SLOT / (D * 4);    // rows per ring slot
+  static constexpr int CPT = TB_M / RS;            // ring slots per row tile
+  // what every layout holds besides the A stages, the exchange buffers and
+  // the ring: B, norms, flags, barriers (at most 64), alignment slack
+  static constexpr size_t FIXED = 2 * (size_t)BPART + (size_t)NP * 4 + 512 + 64 * 8 + 1024;
+  static constexpr size_t XBUF = 4 * (size_t)TB_M * 12;  // one exchange buffer
+  static constexpr int NSTAGE =
+      FIXED + 4 * (size_t)ATILE + 2 * XBUF + 4 * (size_t)TB_SLOT <= TB_SMEM_MAX ? 2 : 1;
+  static constexpr size_t AFTER_A = FIXED + (size_t)NSTAGE * 2 * ATILE;
+  // four exchange buffers where eight ring slots fit beside them, else two
+  static constexpr int NX = AFTER_A + 4 * XBUF + 8 * (size_t)TB_SLOT <= TB_SMEM_MAX ? 4 : 2;
+  static constexpr size_t RING_ROOM = TB_SMEM_MAX - AFTER_A - NX * XBUF;
+  static constexpr int NR = RING_ROOM / TB_SLOT >= 16 ? 16 : (int)(RING_ROOM / TB_SLOT);
+  static_assert(NR >= 4, "row ring of at least four slots");
   static constexpr size_t AOP = 2 * (size_t)BPART;
-  static constexpr size_t CN = AOP + (size_t)NSTAGE * 2 * ATILE;
+  static constexpr size_t RING = AOP + (size_t)NSTAGE * 2 * ATILE;
+  static constexpr size_t CN = RING + (size_t)NR * TB_SLOT;
   static constexpr size_t XCH = CN + (size_t)NP * 4;
-  static constexpr size_t DEADF = XCH + (size_t)TB_NX * 4 * TB_M * 12;
+  static constexpr size_t DEADF = XCH + (size_t)NX * XBUF;
   static constexpr size_t BARS = DEADF + 512;
-  static constexpr int NBARS = 2 * NSTAGE + 4 + 2 * TB_NX + 1;
+  static constexpr int NBARS = 2 * NSTAGE + 4 + 2 * NX + 1 + 2 * NR;
+  static_assert(NBARS <= 64, "barrier room");
   static constexpr size_t TOTAL = BARS + NBARS * 8 + 1024;
+  static_assert(TOTAL <= TB_SMEM_MAX, "shared memory of one CTA");
 };
 
 // Shared-memory views of one CTA.
 struct TbSm {
   unsigned char *bh, *bl, *a;
+  const float *ring;  // [NR slots][RS rows][D floats]
   float *cn;
-  float *xch;  // [TB_NX][4 warpgroups][TB_M rows][3 keys]
+  float *xch;  // [NX][4 warpgroups][TB_M rows][3 keys]
   uint8_t *dead;
-  uint64_t *afull, *afree, *accf, *acce, *xready, *xdone, *drain;
+  uint64_t *afull, *afree, *accf, *acce, *xready, *xdone, *drain, *rfull, *rfree;
   volatile int *abort;
   uint32_t tmem;
 };
@@ -116,6 +133,7 @@ __device__ __forceinline__ TbSm tb_bind(unsigned char *base, volatile int *abort
   m.bh = base;
   m.bl = base + Cfg::BPART;
   m.a = base + Cfg::AOP;
+  m.ring = reinterpret_cast<const float *>(base + Cfg::RING);
   m.cn = reinterpret_cast<float *>(base + Cfg::CN);
   m.xch = reinterpret_cast<float *>(base + Cfg::XCH);
   m.dead = base + Cfg::DEADF;
@@ -125,8 +143,10 @@ __device__ __forceinline__ TbSm tb_bind(unsigned char *base, volatile int *abort
   m.accf = m.afree + Cfg::NSTAGE;
   m.acce = m.accf + 2;
   m.xready = m.acce + 2;
-  m.xdone = m.xready + TB_NX;
-  m.drain = m.xdone + TB_NX;
+  m.xdone = m.xready + Cfg::NX;
+  m.drain = m.xdone + Cfg::NX;
+  m.rfull = m.drain + 1;
+  m.rfree = m.rfull + Cfg::NR;
   m.abort = abort;
   m.tmem = 0;
   return m;
@@ -143,7 +163,11 @@ __device__ __forceinline__ void tb_init_barriers(const TbSm &m) {
     hpc_mbar_init(&m.accf[b], 1);
     hpc_mbar_init(&m.acce[b], Cfg::READERS);
   }
-  for (int b = 0; b < TB_NX; ++b) {
+  for (int r = 0; r < Cfg::NR; ++r) {
+    hpc_mbar_init(&m.rfull[r], 1);        // the copy's issuer (+ its bytes)
+    hpc_mbar_init(&m.rfree[r], TB_CONV);  // the converter warps
+  }
+  for (int b = 0; b < Cfg::NX; ++b) {
     hpc_mbar_init(&m.xready[b], 16);  // the fold warps
     hpc_mbar_init(&m.xdone[b], 4);    // the finisher warpgroup's warps
   }
@@ -188,19 +212,52 @@ struct TbRows {
 };
 
 // ---- converters (warps 0, 1) ------------------------------------------------
+// Rows reach shared memory through a ring of NR slots of RS rows each, filled
+// by bulk copies that lane 0 of warp 0 issues NR - 1 slots ahead (and the L2
+// is asked for the rows two tiles ahead); each converter warp splits half of
+// every slot's rows into x_h | x_l (K-major, 128-byte swizzle) in the tile's A
+// stage.  Rows past the end are zeros.  Slot s of chunk q (q = tile sequence
+// number x CPT + chunk) is s = q mod NR, its use q / NR, so that the ring's
+// phases run on from one pass to the next.
 template <int D, int NP>
 __device__ __forceinline__ void tb_convert(const TbSm &m, const TbRows &R, uint32_t gbase, int *status) {
   using Cfg = TbCfg<D, NP>;
-  constexpr int F4 = D / 4;                       // float4 per row
-  constexpr int LDS = 64 * F4 / 32;               // loads per lane per tile
-  constexpr int BATCH = 16;
+  constexpr int RS = Cfg::RS, CPT = Cfg::CPT, NR = Cfg::NR;
+  constexpr int F4 = D / 4;        // float4 per row
+  constexpr int HR = RS / TB_CONV;  // rows of a slot per converter warp
+  constexpr int PER = HR * F4 / 32;  // float4 per lane per slot
+  static_assert(HR * F4 % 32 == 0 && PER >= 1, "whole warps");
   const int cw = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = 0; i < R.ntiles; ++i) {
+  const bool issuer = cw == 0 && lane == 0;
+  const int nch = R.ntiles * CPT;
+  int issued = 0, consumed = 0;
+  // chunk c of this pass into its slot (issuer only)
+  auto issue = [&](int c) -> bool {
+    const int i = c / CPT, cc = c % CPT;
+    const uint32_t q = (gbase + (uint32_t)i) * CPT + (uint32_t)cc;
+    const int sl = (int)(q % NR);
+    const uint32_t use = q / NR;
+    if (use > 0 && !hpc_mbar_wait(&m.rfree[sl], (use - 1) & 1u, m.abort, status, TB_WAIT_NS))
+      return false;
+    const int64_t row0 = (R.tile0 + (int64_t)i * R.tstep) * TB_M + (int64_t)cc * RS;
+    const int64_t nv = max((int64_t)0, min((int64_t)RS, R.nrows - row0));
+    const uint32_t bytes = (uint32_t)nv * D * 4;
+    hpc_mbar_arrive_expect_tx(&m.rfull[sl], bytes);
+    if (bytes) hpc_bulk_load((void *)(m.ring + (size_t)sl * RS * D), R.rows + row0 * D, bytes, &m.rfull[sl]);
+    return true;
+  };
+  bool ok = true;
+  while (issuer && ok && issued < min(NR - 1, nch)) {
+    ok = issue(issued);
+    issued += ok ? 1 : 0;
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  for (int i = 0; ok && i < R.ntiles; ++i) {
     const uint32_t g = gbase + (uint32_t)i;
     const int st = (int)(g % Cfg::NSTAGE);
     const uint32_t use = g / Cfg::NSTAGE;
     const int64_t row0 = (R.tile0 + (int64_t)i * R.tstep) * TB_M;
-    if (cw == 0 && lane == 0 && i + 2 < R.ntiles) {
+    if (issuer && i + 2 < R.ntiles) {
       const int64_t p0 = (R.tile0 + (int64_t)(i + 2) * R.tstep) * TB_M;
       const int64_t nr = min((int64_t)TB_M, R.nrows - p0);
       if (nr > 0) hpc_prefetch_l2_bulk(R.rows + p0 * D, (uint32_t)(nr * D * 4));
@@ -209,20 +266,35 @@ __device__ __forceinline__ void tb_convert(const TbSm &m, const TbRows &R, uint3
     unsigned char *ah = m.a + (size_t)st * 2 * Cfg::ATILE;
     unsigned char *al = ah + Cfg::ATILE;
 #pragma unroll 1
-    for (int b0 = 0; b0 < LDS; b0 += BATCH) {
-      float4 v[BATCH];
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int e = (b0 + u) * 32 + lane;
-        const int r = 64 * cw + e / F4;
-        const int64_t row = row0 + r;
-        v[u] = row < R.nrows ? __ldg(reinterpret_cast<const float4 *>(R.rows + row * D) + e % F4)
-                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int cc = 0; cc < CPT; ++cc) {
+      if (issuer && issued < nch) {
+        ok = issue(issued);
+        issued += ok ? 1 : 0;
       }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      const uint32_t q = g * CPT + (uint32_t)cc;
+      const int sl = (int)(q % NR);
+      if (!wait_warp(&m.rfull[sl], (q / NR) & 1u, m.abort, status, TB_WAIT_NS)) {
+        ok = false;
+        break;
+      }
+      const float *src = m.ring + ((size_t)sl * RS + (size_t)cw * HR) * D;
+      const int r0 = cc * RS + cw * HR;  // the slot's first row of this warp, in the tile
+      float4 v[PER];
 #pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int e = (b0 + u) * 32 + lane;
-        const int r = 64 * cw + e / F4;
+      for (int u = 0; u < PER; ++u) {
+        const int e = u * 32 + lane;
+        v[u] = row0 + r0 + e / F4 < R.nrows ? *reinterpret_cast<const float4 *>(src + 4 * e)
+                                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+      __syncwarp();
+      if (lane == 0) hpc_mbar_arrive(&m.rfree[sl]);  // the slot is in registers
+      ++consumed;
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = u * 32 + lane;
+        const int r = r0 + e / F4;
         const int t = 4 * (e % F4);
         const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[u].x, v[u].y);
         const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[u].z, v[u].w);
@@ -234,9 +306,20 @@ __device__ __forceinline__ void tb_convert(const TbSm &m, const TbRows &R, uint3
         *reinterpret_cast<uint2 *>(al + off) = make_uint2(tb_bits(l01), tb_bits(l23));
       }
     }
+    if (!ok) break;
     hpc_fence_proxy_async();  // the stage's generic writes, visible to the tensor core
     __syncwarp();
     if (lane == 0) hpc_mbar_arrive(&m.afull[st]);
+  }
+  // after an abort: copies still in flight land before the CTA goes on
+  if (issuer && consumed < issued) {
+    int no_abort = 0;
+    for (int c = consumed; c < issued; ++c) {
+      const uint32_t q = (gbase + (uint32_t)(c / CPT)) * CPT + (uint32_t)(c % CPT);
+      if (!hpc_mbar_wait(&m.rfull[q % NR], (q / NR) & 1u, (volatile int *)&no_abort, status,
+                         TB_DRAIN_NS))
+        break;
+    }
   }
 }
 
@@ -343,8 +426,8 @@ __device__ __forceinline__ void tb_fold(const TbSm &m, const TbRows &R, uint32_t
     const uint32_t g = gbase + (uint32_t)i;
     const int bk = Cfg::PARTS == 2 ? part : (int)(g & 1u);
     const uint32_t v = Cfg::PARTS == 2 ? g : (g >> 1);
-    const int xb = (int)(g % TB_NX);
-    const uint32_t xu = g / TB_NX;
+    const int xb = (int)(g % Cfg::NX);
+    const uint32_t xu = g / Cfg::NX;
     const bool ok = wait_warp(&m.accf[bk], v & 1u, m.abort, status, TB_WAIT_NS);
     // the three smallest keys of this warpgroup's columns, as two chains
     float d1 = __int_as_float(0x7f7fffff), d2 = d1, d3 = d1, e1 = d1, e2 = d1, e3 = d1;
@@ -401,8 +484,8 @@ __device__ __forceinline__ void tb_finish(const TbSm &m, const TbRows &R, uint32
   for (int i = 0; i < R.ntiles; ++i) {
     const uint32_t g = gbase + (uint32_t)i;
     if ((int)(g % TB_NFIN) != f) continue;
-    const int xb = (int)(g % TB_NX);
-    const uint32_t xu = g / TB_NX;
+    const int xb = (int)(g % Cfg::NX);
+    const uint32_t xu = g / Cfg::NX;
     if (!wait_warp(&m.xready[xb], xu & 1u, m.abort, status, TB_WAIT_NS)) break;
     // the three smallest keys of the tile's row: every centroid but the two
     // best has a key of at least the third (each warpgroup kept its three)
@@ -462,85 +545,114 @@ __device__ __forceinline__ float tb_direct(const float *__restrict__ x, const fl
 }
 
 // Exact assignment of one row by the whole warp (every lane passes the same
-// row; lane l takes centroids l, l + 32, ..., NPL of them): FP32 direct form
-// in dimension order with its relative bound (D + 3) u, then, if the two
-// best are not separated, FP64 in the oracle's operation order, ties to the
-// lowest index.  The row streams from memory eight dimensions at a time and
-// each lane advances all its centroids over them, so that the centroid
-// loads of one step are independent.  Counts the FP64 rows in *stats.
-template <int D, int NPL>
+// row).  FP32 direct form for every centroid: the warp's four 8-lane groups
+// take centroids 4i + g, and lane l of a group the dimensions 4l + 32v ..
+// 4l + 32v + 3, so that a group reads a centroid row in coalesced 128-byte
+// pieces; U centroids per group are loaded before any is used.  The group's
+// partial sums meet by shuffles (every lane of the group gets the same
+// value: the butterfly adds the same pairs); summed in any order, the D
+// nonnegative terms carry the relative bound (D + 3) u.  If the two best are
+// not separated by it, FP64 in the oracle's operation order for the
+// centroids whose FP32 value lies within the bound of the best (no other one
+// can win), ties to the lowest index.  Every lane returns the same index.
+// Counts the FP64 rows in *stats.
+template <int D>
+__device__ __forceinline__ float tb_group_dist(const float4 (&xv)[D / 32], const float4 (&cv)[D / 32]) {
+  float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+  for (int v = 0; v < D / 32; ++v) {
+    const float dx = __fmaf_rn(0.5f, cv[v].x, xv[v].x), dy = __fmaf_rn(0.5f, cv[v].y, xv[v].y);
+    const float dz = __fmaf_rn(0.5f, cv[v].z, xv[v].z), dw = __fmaf_rn(0.5f, cv[v].w, xv[v].w);
+    s0 = __fmaf_rn(dx, dx, s0);
+    s1 = __fmaf_rn(dy, dy, s1);
+    s0 = __fmaf_rn(dz, dz, s0);
+    s1 = __fmaf_rn(dw, dw, s1);
+  }
+  float s = s0 + s1;
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  return s;
+}
+
+template <int D>
 __device__ __forceinline__ int tb_rescore(const float *__restrict__ x, const hpc_cent_smem &cs,
                                           unsigned long long *stats) {
   constexpr int CS = hpc_cstride(D);
-  const int lane = threadIdx.x & 31;
-  float acc[NPL];
-  bool live[NPL];
+  constexpr int V = D / 32;           // float4 of a centroid row per lane
+  constexpr int U = D == 64 ? 4 : 2;  // centroids per group in flight
+  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
+  const int kp = cs.kp;
+  float4 xv[V];
 #pragma unroll
-  for (int u = 0; u < NPL; ++u) {
-    const int j = lane + 32 * u;
-    live[u] = j < cs.kp && __ldcg(&cs.cnz[j].x) < HPC_DEAD;
-    acc[u] = 0.0f;
-  }
+  for (int v = 0; v < V; ++v) xv[v] = __ldg(reinterpret_cast<const float4 *>(x + 4 * sl + 32 * v));
+  float a1 = __int_as_float(0x7f800000), a2 = a1;
+  int ja = 0x7fffffff;
 #pragma unroll 1
-  for (int t0 = 0; t0 < D; t0 += 8) {
-    const float4 xa = __ldg(reinterpret_cast<const float4 *>(x + t0));
-    const float4 xb = __ldg(reinterpret_cast<const float4 *>(x + t0 + 4));
-    const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+  for (int j0 = 0; j0 < kp; j0 += 4 * U) {
+    float4 cv[U][V];
+    float nz[U];
 #pragma unroll
-    for (int u = 0; u < NPL; ++u) {
-      if (!live[u]) continue;
-      const float *cm = cs.cm + (size_t)(lane + 32 * u) * CS + t0;
-      const float4 ca = __ldcg(reinterpret_cast<const float4 *>(cm));
-      const float4 cb = __ldcg(reinterpret_cast<const float4 *>(cm + 4));
-      const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    for (int u = 0; u < U; ++u) {
+      const int j = min(j0 + 4 * u + g, kp - 1);
+      const float *cm = cs.cm + (size_t)j * CS + 4 * sl;
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const float df = __fmaf_rn(0.5f, cv[t], xv[t]);
-        acc[u] = __fmaf_rn(df, df, acc[u]);
+      for (int v = 0; v < V; ++v) cv[u][v] = __ldcg(reinterpret_cast<const float4 *>(cm + 32 * v));
+      nz[u] = __ldcg(&cs.cnz[j].x);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float s = tb_group_dist<D>(xv, cv[u]);
+      const int j = j0 + 4 * u + g;
+      if (j < kp && nz[u] < HPC_DEAD) {
+        if (s < a1) {
+          a2 = a1;
+          a1 = s;
+          ja = j;
+        } else {
+          a2 = fminf(a2, s);
+        }
       }
     }
   }
-  float a1 = __int_as_float(0x7f800000), a2 = a1;
-  int ja = 0x7fffffff;
 #pragma unroll
-  for (int u = 0; u < NPL; ++u) {
-    if (!live[u]) continue;
-    if (acc[u] < a1) {
-      a2 = a1;
-      a1 = acc[u];
-      ja = lane + 32 * u;
-    } else {
-      a2 = fminf(a2, acc[u]);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = 8; o < 32; o <<= 1) {
     const float b1 = __shfl_xor_sync(0xffffffffu, a1, o);
     const int jb = __shfl_xor_sync(0xffffffffu, ja, o);
     const float b2 = __shfl_xor_sync(0xffffffffu, a2, o);
     hpc_merge_top2(a1, ja, a2, b1, jb, b2);
   }
-  const float bound = (float)(D + 3) * HPC_U32 * 1.001f * (a1 + a2);
-  if (a2 - a1 > bound) return ja < cs.kp ? ja : 0;
+  constexpr float rho = (float)(D + 3) * HPC_U32 * 1.001f;
+  if (a2 - a1 > rho * (a1 + a2)) return ja < kp ? ja : 0;
   if (stats && lane == 0) atomicAdd(stats + 3, 1ull);
+  // every centroid whose exact value may be at most the best's: FP32 value
+  // s_j with s_j / (1 + rho) <= a1 / (1 - rho)
+  const float thr = a1 * ((1.0f + rho) / (1.0f - rho)) * 1.0001f;
   double b = __longlong_as_double(0x7ff0000000000000ll);
   int jb = 0x7fffffff;
-  for (int j = lane; j < cs.kp; j += 32) {
-    if (__ldcg(&cs.cnz[j].x) >= HPC_DEAD) continue;
+#pragma unroll 1
+  for (int j0 = 0; j0 < kp; j0 += 4) {
+    const int j = min(j0 + g, kp - 1);
     const float *cm = cs.cm + (size_t)j * CS;
-    double acc64 = 0.0;
-    for (int t = 0; t < D; ++t) {
-      const double c = -0.5 * (double)__ldcg(cm + t);
-      const double diff = __dsub_rn((double)__ldg(x + t), c);
-      acc64 = __dadd_rn(acc64, __dmul_rn(diff, diff));
-    }
-    if (acc64 < b) {
-      b = acc64;
-      jb = j;
+    float4 cv[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) cv[v] = __ldcg(reinterpret_cast<const float4 *>(cm + 4 * sl + 32 * v));
+    const float s = tb_group_dist<D>(xv, cv);
+    if (j0 + g < kp && sl == 0 && __ldcg(&cs.cnz[j].x) < HPC_DEAD && s <= thr) {
+      double acc64 = 0.0;
+      for (int t = 0; t < D; ++t) {
+        const double c = -0.5 * (double)__ldcg(cm + t);
+        const double diff = __dsub_rn((double)__ldg(x + t), c);
+        acc64 = __dadd_rn(acc64, __dmul_rn(diff, diff));
+      }
+      if (acc64 < b) {  // j increases along a lane: ties keep the lower index
+        b = acc64;
+        jb = j;
+      }
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = 8; o < 32; o <<= 1) {
     const double ob = __shfl_xor_sync(0xffffffffu, b, o);
     const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
     if (ob < b || (ob == b && oj < jb)) {
@@ -548,7 +660,8 @@ __device__ __forceinline__ int tb_rescore(const float *__restrict__ x, const hpc
       jb = oj;
     }
   }
-  return jb < cs.kp ? jb : 0;
+  jb = __shfl_sync(0xffffffffu, jb, 0);  // the first lanes of the groups held the FP64 values
+  return jb < kp ? jb : ja < kp ? ja : 0;
 }
 
 // Rows whose settling needs every centroid, deferred to after the CTA's
@@ -566,7 +679,7 @@ enum { TB_DONE = 1, TB_BAD = 0, TB_QUEUED = 2 };
 // Returns TB_DONE with the exact nearest centroid in *j_out and its FP32
 // direct-form distance in *dd_out, TB_QUEUED when the row went to the CTA's
 // queue, TB_BAD for an invalid or non-finite row (status recorded).
-template <int D, int IB, int NPL>
+template <int D, int IB>
 __device__ __forceinline__ int tb_exact(const float *__restrict__ rows, int64_t row0w, int64_t row,
                                         bool valid, int j1, int j2, float d1, float d2, float lo3,
                                         const hpc_cent_smem &gcs, int *status,
@@ -638,7 +751,7 @@ __device__ __forceinline__ int tb_exact(const float *__restrict__ rows, int64_t 
   while (mfull) {
     const int src = __ffs(mfull) - 1;
     mfull &= mfull - 1;
-    const int j = tb_rescore<D, NPL>(rows + (row0w + src) * D, gcs, stats);
+    const int j = tb_rescore<D>(rows + (row0w + src) * D, gcs, stats);
     if (lane == src && j != j1) {
       j1 = j;
       dd = tb_direct<D>(xg, gcs.cm + (size_t)j1 * CS);
@@ -656,7 +769,7 @@ __device__ __forceinline__ int tb_exact(const float *__restrict__ rows, int64_t 
 // Settles the rows of the CTA's queue (all warps of the CTA; a warp per row):
 // every centroid, FP32 then FP64 (tb_rescore); `done(row, j, dd)` is then
 // called by the whole warp.
-template <int D, int NPL, typename Done>
+template <int D, typename Done>
 __device__ __forceinline__ void tb_settle_queue(const float *__restrict__ rows,
                                                 const TbQueue &queue, const hpc_cent_smem &gcs,
                                                 unsigned long long *stats, Done done) {
@@ -666,7 +779,7 @@ __device__ __forceinline__ void tb_settle_queue(const float *__restrict__ rows,
   for (int qi = warp; qi < nq; qi += TB_THREADS / 32) {
     const int64_t row = queue.rows[qi];
     const float *xg = rows + row * D;
-    const int j = tb_rescore<D, NPL>(xg, gcs, stats);
+    const int j = tb_rescore<D>(xg, gcs, stats);
     const float dd = tb_direct<D>(xg, gcs.cm + (size_t)j * CS);
     done(row, j, dd);
   }
@@ -889,7 +1002,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
                        float lo3) {
       int j = 0;
       float dd = 0.0f;
-      const bool ok = tb_exact<D, Cfg::IB, NP / 32>(tk.S, row0w, row, valid, j1, j2, d1, d2, lo3,
+      const bool ok = tb_exact<D, Cfg::IB>(tk.S, row0w, row, valid, j1, j2, d1, d2, lo3,
                                                     gcs, a.status, a.stats, queue, &j, &dd) ==
                       TB_DONE;
       if (ok) hpc_sum2_add(fs_hi, fs_lo, dd);
@@ -910,7 +1023,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     });
     __syncthreads();
     // the queued rows, every warp
-    tb_settle_queue<D, NP / 32>(tk.S, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
+    tb_settle_queue<D>(tk.S, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
       if (lane == 0) hpc_sum2_add(fs_hi, fs_lo, dd);
       const int old = it > 0 ? tk.plab[row] : -1;
       if (old != j) move(row, j, old);
@@ -1075,14 +1188,14 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcb_objective_kernel(TcbArgs a)
                      float lo3) {
     int j = 0;
     float dd = 0.0f;
-    if (tb_exact<D, Cfg::IB, NP / 32>(a.X, row0w, row, valid, j1, j2, d1, d2, lo3, gcs, a.status,
+    if (tb_exact<D, Cfg::IB>(a.X, row0w, row, valid, j1, j2, d1, d2, lo3, gcs, a.status,
                                       a.stats, queue, &j, &dd) == TB_DONE) {
       hpc_sum2_add(fs_hi, fs_lo, dd);
       if (a.labels) a.labels[row] = j;
     }
   });
   __syncthreads();
-  tb_settle_queue<D, NP / 32>(a.X, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
+  tb_settle_queue<D>(a.X, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
     if ((threadIdx.x & 31) == 0) {
       hpc_sum2_add(fs_hi, fs_lo, dd);
       if (a.labels) a.labels[row] = j;

@@ -20,11 +20,10 @@ import oracle as orc
 from paper_2311_04517_gb300 import hpclust as H
 from paper_2311_04517_gb300 import synth
 
-pytestmark = pytest.mark.gpu
+from lloyd_replay import (RTOL, TIE, assert_centroids, check_parted_run, dev, gpu_lloyd, host,
+                          lockstep_divergence)
 
-RTOL = 1e-6
-TIE = 1e-6
-ATOL_REL = 1e-9
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -32,17 +31,6 @@ def ctx():
     c = H.Context(0)
     yield c
     c.close()
-
-
-def dev(a, dtype=None):
-    t = torch.from_numpy(np.ascontiguousarray(a))
-    if dtype is not None:
-        t = t.to(dtype)
-    return t.cuda()
-
-
-def host(t):
-    return t.detach().cpu().numpy()
 
 
 def mixture(n, d, comps, seed, spread=10.0, sd=1.0):
@@ -63,19 +51,6 @@ def assert_labels(lab_g, S, C, deg, what=""):
         dg = ((S[diff].astype(np.float64) - Cd[lab_g[diff]]) ** 2).sum(1)
         assert np.all(dg <= d1[diff] * (1 + TIE))
     return diff.size
-
-
-def assert_centroids(Cg, Co, what=""):
-    """Per coordinate: |Cg - Co| <= 1e-6 |Co| + 1e-9 max(1, max |Co|)."""
-    Co64 = np.asarray(Co, np.float64)
-    Cg64 = np.asarray(Cg, np.float64)
-    scale = max(1.0, float(np.abs(Co64).max())) if Co64.size else 1.0
-    tol = RTOL * np.abs(Co64) + ATOL_REL * scale
-    bad = np.abs(Cg64 - Co64) > tol
-    if bad.any():
-        i = np.unravel_index(np.argmax(np.abs(Cg64 - Co64) - tol), Co64.shape)
-        raise AssertionError(f"{what}: {int(bad.sum())} centroid coordinates off, worst at {i}: "
-                             f"{Cg64[i]} vs {Co64[i]}")
 
 
 # ---------------------------------------------------------------------------
@@ -234,38 +209,6 @@ def test_kmeanspp_partial_reseed_and_exhaustion(ctx):
 # ---------------------------------------------------------------------------
 # Lloyd (Algorithm 1, Section 6.5 stop rule)
 # ---------------------------------------------------------------------------
-def gpu_lloyd(ctx, S, C0, deg0, **kw):
-    Cg, dg = dev(C0), dev(deg0)
-    lab = torch.empty(S.shape[0], dtype=torch.int32, device="cuda")
-    f, it = H.hpc_lloyd(ctx, dev(S), Cg, dg, labels_out=lab, **kw)
-    ctx.check_status()
-    return dict(C=host(Cg), degenerate=host(dg), labels=host(lab), f=float(host(f)[0]),
-                iters=int(host(it)[0]))
-
-
-def lockstep_divergence(ctx, S, C0, deg0, iters):
-    """Steps the oracle and the GPU one update at a time from the same state.
-    Returns the first step where the labels differ (only near ties allowed),
-    or None; any centroid difference beyond tolerance fails."""
-    C, deg = C0.copy(), deg0.copy()
-    Sd = dev(S)
-    for it in range(iters + 1):
-        lab_o, d1, d2, _ = orc.assign(S, C, deg)
-        lab = torch.empty(S.shape[0], dtype=torch.int32, device="cuda")
-        H.hpc_objective(ctx, Sd, dev(C), dev(deg), labels_out=lab)
-        ctx.check_status()
-        diff = np.flatnonzero(host(lab) != lab_o)
-        if diff.size:
-            assert ((d2[diff] - d1[diff]) <= TIE * d1[diff]).all(), "labels differ away from ties"
-            return it
-        Co, dego = orc.update(S, lab_o, C, deg)
-        g = gpu_lloyd(ctx, S, C, deg, max_iter=1, rel_tol=0.0)
-        assert_centroids(g["C"], Co, f"lockstep step {it}")
-        np.testing.assert_array_equal(g["degenerate"], dego)
-        C, deg = Co, dego
-    return None
-
-
 def lloyd_case(ctx, S, k, seed):
     d = S.shape[1]
     init = orc.kmeanspp(S, np.zeros((k, d), np.float32), np.ones(k, np.uint8), seed=seed)
@@ -278,23 +221,9 @@ def lloyd_case(ctx, S, k, seed):
         assert_centroids(g["C"], o["C"], "lloyd")
         assert_labels(g["labels"], S, o["C"], o["degenerate"], "lloyd")
     else:
-        # only a near tie (in a label or in the stop test) may explain it
-        step = lockstep_divergence(ctx, S, C0, deg0, max(g["iters"], o["iters"]))
-        if step is None:
-            tr = o["f_trace"]
-            it = min(g["iters"], o["iters"])
-            ratio = (tr[it - 1] - tr[it]) / tr[it - 1]
-            assert abs(ratio - 1e-4) <= 1e-6, "trajectories differ without a near tie"
-            step = it
-        # up to the step where they part, the two runs agree within the
-        # contract: the same number of updates from the same start
-        if step > 0:
-            gs = gpu_lloyd(ctx, S, C0, deg0, max_iter=step, rel_tol=0.0)
-            os_ = orc.lloyd(S, C0, deg0, max_iter=step, rel_tol=0.0)
-            assert gs["iters"] == os_["iters"] == step
-            assert_centroids(gs["C"], os_["C"], f"lloyd up to step {step}")
-            np.testing.assert_array_equal(gs["degenerate"], os_["degenerate"])
-            assert gs["f"] == pytest.approx(os_["f"], rel=RTOL)
+        # only a near tie (in a label or in the stop test) may explain it;
+        # up to the step where they part, the two runs agree
+        check_parted_run(ctx, S, C0, deg0, g, o)
     # the reported objective is the objective of the returned centroids
     assert g["f"] == pytest.approx(orc.objective(S, g["C"], g["degenerate"]), rel=RTOL)
     return g, o
@@ -442,6 +371,40 @@ def test_lloyd_tensor_cores_near_ties(ctx):
     lab_o, d1, d2, _ = orc.assign(S, C)
     strict = (d2 - d1) > 1e-12 * d1
     np.testing.assert_array_equal(g["labels"][strict], lab_o[strict])
+
+
+@pytest.mark.parametrize("d,k", [(64, 128), (64, 300), (128, 200)])
+def test_lloyd_tensor_cores_three_way_ties(ctx, d, k):
+    # rows at the centre of three centroids at equal distance (up to the
+    # rounding of the FP32 rows and centroids): every row has a third
+    # candidate inside the split-BF16 window, so it is settled against every
+    # centroid, and FP32 cannot order the three, so FP64 decides.  One update
+    # must equal the oracle's update on the oracle's labels.
+    rng = np.random.default_rng(44 + d + k)
+    m = rng.uniform(50, 60, d)
+    Q, _ = np.linalg.qr(rng.standard_normal((d, 3)))
+    near = [m + 5.0 * Q[:, j] for j in range(3)]
+    far = [m + 30.0 * rng.standard_normal(d) for _ in range(k - 3)]
+    C = np.stack(near + far).astype(np.float32)
+    n = 4096
+    S = (m + 2e-6 * rng.standard_normal((n, d))).astype(np.float32)
+    deg = np.zeros(k, np.uint8)
+    lab_o, d1, d2, _ = orc.assign(S, C, deg)
+    assert ((d2 - d1) > 1e-12 * d1).all()     # strict in FP64
+    Co, dego = orc.update(S, lab_o, C, deg)
+    ctx.set_tensor_cores(1)
+    ctx.set_search_stats(True)
+    ctx.search_stats(reset=True)
+    try:
+        assert ctx.lloyd_schedule(n, d, k)["form"] == "split_bf16"
+        g = gpu_lloyd(ctx, S, C, deg, max_iter=1, rel_tol=0.0)
+        st = ctx.search_stats(reset=True)
+    finally:
+        ctx.set_search_stats(False)
+        ctx.set_tensor_cores(2)
+    assert st["all_centroids"] > 0 and st["fp64"] > 0, st
+    np.testing.assert_array_equal(g["degenerate"], dego)
+    assert_centroids(g["C"], Co, "one update")
 
 
 def test_lloyd_edge_cases(ctx):
