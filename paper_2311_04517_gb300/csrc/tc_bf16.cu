@@ -23,18 +23,21 @@
 // ties to the lowest index) after the CTA's pass, by all its warps.
 //
 // Data path per 128-row tile (one persistent CTA per SM):
-//   warps 0-1 (converters): coalesced 16-byte loads of the FP32 rows (an L2
-//     bulk prefetch two tiles ahead), split into x_h | x_l, written as the
-//     MMA's A operand (K-major, 128-byte swizzle) into one of two
-//     shared-memory stages;
-//   warp 2 (TMEM owner, MMA issuer, one thread): 3 d / 16 x 3 kind::f16
+//   warp 0 (TMEM owner, MMA issuer, one thread): 3 d / 16 x 3 kind::f16
 //     MMAs per 256-column bank against B = (c_h | c_l) resident in shared
-//     memory; TMEM holds two banks (two tiles in flight for up to 256
-//     centroids, the two halves of one tile for up to 512);
-//   warps 3-18 (four fold warpgroups): warpgroup e folds a quarter of a
+//     memory, the A operand from one of two shared-memory stages; TMEM holds
+//     two banks (two tiles in flight for up to 256 centroids, the two halves
+//     of one tile for up to 512); asks the L2 for the rows of the tile four
+//     tiles ahead (bulk prefetch);
+//   warps 1-16 (four fold warpgroups): warpgroup e folds a quarter of a
 //     tile's columns into the three smallest (value, index) keys per row
 //     (7 to 9 index bits) and leaves them in a rotating exchange buffer;
-//   warps 19-26 (two finisher warpgroups): warpgroup f takes every second
+//     each warp then converts eight rows of a later tile: coalesced 16-byte
+//     loads of the FP32 rows (issued before the fold, so that their latency
+//     hides behind it), split into x_h | x_l and written as the MMA's A
+//     operand (K-major, 128-byte swizzle), so that the conversion is spread
+//     over sixteen warps;
+//   warps 17-24 (two finisher warpgroups): warpgroup f takes every second
 //     tile, merges the four partial top-3 of each row and finishes the row
 //     (exact distance, margin test, exact stages, objective, labels, and in
 //     Lloyd the centroid sums), so that the fold warps, which release the
@@ -64,13 +67,13 @@
 namespace {
 
 constexpr int TB_M = 128;
-constexpr int TB_CONV = 2;                       // converter warps 0, 1
-constexpr int TB_MMAW = 2;                       // TMEM owner and MMA issuer
-constexpr int TB_EPI0 = 3;                       // first fold warp (four warpgroups)
-constexpr int TB_FIN0 = TB_EPI0 + 16;            // first finisher warp (two warpgroups)
+constexpr int TB_MMAW = 0;                       // TMEM owner and MMA issuer
+constexpr int TB_EPI0 = 1;                       // first fold warp (four warpgroups)
+constexpr int TB_NFOLD = 16;                     // fold warps
+constexpr int TB_FIN0 = TB_EPI0 + TB_NFOLD;      // first finisher warp (two warpgroups)
 constexpr int TB_NFIN = 2;                       // finisher warpgroups
-constexpr int TB_THREADS = (TB_FIN0 + 4 * TB_NFIN) * 32;  // 864
-constexpr uint32_t TB_SLOT = 4096;               // bytes of one row-ring slot
+constexpr int TB_THREADS = (TB_FIN0 + 4 * TB_NFIN) * 32;  // 800
+constexpr int TB_PREFETCH = 4;                   // tiles the L2 is asked for ahead
 constexpr size_t TB_SMEM_MAX = 226 * 1024;       // dynamic shared memory of one CTA (static: < 1 KB)
 constexpr uint64_t TB_WAIT_NS = 2000000000ull;
 constexpr uint64_t TB_DRAIN_NS = 500000000ull;
@@ -88,28 +91,20 @@ struct TbCfg {
   static constexpr int CPW = NP / 4;               // columns per epilogue warpgroup
   static constexpr int READERS = NP > 256 ? 8 : 16;
   static constexpr int IB = NP == 512 ? 9 : NP == 256 ? 8 : 7;
-  static constexpr int RS = TB_SLOT / (D * 4);    // rows per ring slot
-  static constexpr int CPT = TB_M / RS;            // ring slots per row tile
-  // what every layout holds besides the A stages, the exchange buffers and
-  // the ring: B, norms, flags, barriers (at most 64), alignment slack
-  static constexpr size_t FIXED = 2 * (size_t)BPART + (size_t)NP * 4 + 512 + 64 * 8 + 1024;
+  // what every layout holds besides the A stages and the exchange buffers:
+  // B, norms, flags, barriers (at most 32), alignment slack
+  static constexpr size_t FIXED = 2 * (size_t)BPART + (size_t)NP * 4 + 512 + 32 * 8 + 1024;
   static constexpr size_t XBUF = 4 * (size_t)TB_M * 12;  // one exchange buffer
-  static constexpr int NSTAGE =
-      FIXED + 4 * (size_t)ATILE + 2 * XBUF + 4 * (size_t)TB_SLOT <= TB_SMEM_MAX ? 2 : 1;
-  static constexpr size_t AFTER_A = FIXED + (size_t)NSTAGE * 2 * ATILE;
-  // four exchange buffers where eight ring slots fit beside them, else two
-  static constexpr int NX = AFTER_A + 4 * XBUF + 8 * (size_t)TB_SLOT <= TB_SMEM_MAX ? 4 : 2;
-  static constexpr size_t RING_ROOM = TB_SMEM_MAX - AFTER_A - NX * XBUF;
-  static constexpr int NR = RING_ROOM / TB_SLOT >= 16 ? 16 : (int)(RING_ROOM / TB_SLOT);
-  static_assert(NR >= 4, "row ring of at least four slots");
+  static constexpr int NSTAGE = FIXED + 4 * (size_t)ATILE + 2 * XBUF <= TB_SMEM_MAX ? 2 : 1;
+  static constexpr int NX =
+      FIXED + (size_t)NSTAGE * 2 * ATILE + 4 * XBUF <= TB_SMEM_MAX ? 4 : 2;
   static constexpr size_t AOP = 2 * (size_t)BPART;
-  static constexpr size_t RING = AOP + (size_t)NSTAGE * 2 * ATILE;
-  static constexpr size_t CN = RING + (size_t)NR * TB_SLOT;
+  static constexpr size_t CN = AOP + (size_t)NSTAGE * 2 * ATILE;
   static constexpr size_t XCH = CN + (size_t)NP * 4;
   static constexpr size_t DEADF = XCH + (size_t)NX * XBUF;
   static constexpr size_t BARS = DEADF + 512;
-  static constexpr int NBARS = 2 * NSTAGE + 4 + 2 * NX + 1 + 2 * NR;
-  static_assert(NBARS <= 64, "barrier room");
+  static constexpr int NBARS = 2 * NSTAGE + 4 + 2 * NX + 1;
+  static_assert(NBARS <= 32, "barrier room");
   static constexpr size_t TOTAL = BARS + NBARS * 8 + 1024;
   static_assert(TOTAL <= TB_SMEM_MAX, "shared memory of one CTA");
 };
@@ -117,11 +112,10 @@ struct TbCfg {
 // Shared-memory views of one CTA.
 struct TbSm {
   unsigned char *bh, *bl, *a;
-  const float *ring;  // [NR slots][RS rows][D floats]
   float *cn;
   float *xch;  // [NX][4 warpgroups][TB_M rows][3 keys]
   uint8_t *dead;
-  uint64_t *afull, *afree, *accf, *acce, *xready, *xdone, *drain, *rfull, *rfree;
+  uint64_t *afull, *afree, *accf, *acce, *xready, *xdone, *drain;
   volatile int *abort;
   uint32_t tmem;
 };
@@ -133,7 +127,6 @@ __device__ __forceinline__ TbSm tb_bind(unsigned char *base, volatile int *abort
   m.bh = base;
   m.bl = base + Cfg::BPART;
   m.a = base + Cfg::AOP;
-  m.ring = reinterpret_cast<const float *>(base + Cfg::RING);
   m.cn = reinterpret_cast<float *>(base + Cfg::CN);
   m.xch = reinterpret_cast<float *>(base + Cfg::XCH);
   m.dead = base + Cfg::DEADF;
@@ -145,8 +138,6 @@ __device__ __forceinline__ TbSm tb_bind(unsigned char *base, volatile int *abort
   m.xready = m.acce + 2;
   m.xdone = m.xready + Cfg::NX;
   m.drain = m.xdone + Cfg::NX;
-  m.rfull = m.drain + 1;
-  m.rfree = m.rfull + Cfg::NR;
   m.abort = abort;
   m.tmem = 0;
   return m;
@@ -156,16 +147,12 @@ template <int D, int NP>
 __device__ __forceinline__ void tb_init_barriers(const TbSm &m) {
   using Cfg = TbCfg<D, NP>;
   for (int s = 0; s < Cfg::NSTAGE; ++s) {
-    hpc_mbar_init(&m.afull[s], TB_CONV);
+    hpc_mbar_init(&m.afull[s], TB_NFOLD);
     hpc_mbar_init(&m.afree[s], 1);
   }
   for (int b = 0; b < 2; ++b) {
     hpc_mbar_init(&m.accf[b], 1);
     hpc_mbar_init(&m.acce[b], Cfg::READERS);
-  }
-  for (int r = 0; r < Cfg::NR; ++r) {
-    hpc_mbar_init(&m.rfull[r], 1);        // the copy's issuer (+ its bytes)
-    hpc_mbar_init(&m.rfree[r], TB_CONV);  // the converter warps
   }
   for (int b = 0; b < Cfg::NX; ++b) {
     hpc_mbar_init(&m.xready[b], 16);  // the fold warps
@@ -211,127 +198,101 @@ struct TbRows {
   int ntiles;
 };
 
-// ---- converters (warps 0, 1) ------------------------------------------------
-// Rows reach shared memory through a ring of NR slots of RS rows each, filled
-// by bulk copies that lane 0 of warp 0 issues NR - 1 slots ahead (and the L2
-// is asked for the rows two tiles ahead); each converter warp splits half of
-// every slot's rows into x_h | x_l (K-major, 128-byte swizzle) in the tile's A
-// stage.  Rows past the end are zeros.  Slot s of chunk q (q = tile sequence
-// number x CPT + chunk) is s = q mod NR, its use q / NR, so that the ring's
-// phases run on from one pass to the next.
-template <int D, int NP>
-__device__ __forceinline__ void tb_convert(const TbSm &m, const TbRows &R, uint32_t gbase, int *status) {
-  using Cfg = TbCfg<D, NP>;
-  constexpr int RS = Cfg::RS, CPT = Cfg::CPT, NR = Cfg::NR;
-  constexpr int F4 = D / 4;        // float4 per row
-  constexpr int HR = RS / TB_CONV;  // rows of a slot per converter warp
-  constexpr int PER = HR * F4 / 32;  // float4 per lane per slot
-  static_assert(HR * F4 % 32 == 0 && PER >= 1, "whole warps");
-  const int cw = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool issuer = cw == 0 && lane == 0;
-  const int nch = R.ntiles * CPT;
-  int issued = 0, consumed = 0;
-  // chunk c of this pass into its slot (issuer only)
-  auto issue = [&](int c) -> bool {
-    const int i = c / CPT, cc = c % CPT;
-    const uint32_t q = (gbase + (uint32_t)i) * CPT + (uint32_t)cc;
-    const int sl = (int)(q % NR);
-    const uint32_t use = q / NR;
-    if (use > 0 && !hpc_mbar_wait(&m.rfree[sl], (use - 1) & 1u, m.abort, status, TB_WAIT_NS))
-      return false;
-    const int64_t row0 = (R.tile0 + (int64_t)i * R.tstep) * TB_M + (int64_t)cc * RS;
-    const int64_t nv = max((int64_t)0, min((int64_t)RS, R.nrows - row0));
-    const uint32_t bytes = (uint32_t)nv * D * 4;
-    hpc_mbar_arrive_expect_tx(&m.rfull[sl], bytes);
-    if (bytes) hpc_bulk_load((void *)(m.ring + (size_t)sl * RS * D), R.rows + row0 * D, bytes, &m.rfull[sl]);
-    return true;
-  };
-  bool ok = true;
-  while (issuer && ok && issued < min(NR - 1, nch)) {
-    ok = issue(issued);
-    issued += ok ? 1 : 0;
-  }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  for (int i = 0; ok && i < R.ntiles; ++i) {
-    const uint32_t g = gbase + (uint32_t)i;
-    const int st = (int)(g % Cfg::NSTAGE);
-    const uint32_t use = g / Cfg::NSTAGE;
-    const int64_t row0 = (R.tile0 + (int64_t)i * R.tstep) * TB_M;
-    if (issuer && i + 2 < R.ntiles) {
-      const int64_t p0 = (R.tile0 + (int64_t)(i + 2) * R.tstep) * TB_M;
-      const int64_t nr = min((int64_t)TB_M, R.nrows - p0);
-      if (nr > 0) hpc_prefetch_l2_bulk(R.rows + p0 * D, (uint32_t)(nr * D * 4));
-    }
-    if (use > 0 && !wait_warp(&m.afree[st], (use - 1) & 1u, m.abort, status, TB_WAIT_NS)) break;
-    unsigned char *ah = m.a + (size_t)st * 2 * Cfg::ATILE;
-    unsigned char *al = ah + Cfg::ATILE;
-#pragma unroll 1
-    for (int cc = 0; cc < CPT; ++cc) {
-      if (issuer && issued < nch) {
-        ok = issue(issued);
-        issued += ok ? 1 : 0;
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      const uint32_t q = g * CPT + (uint32_t)cc;
-      const int sl = (int)(q % NR);
-      if (!wait_warp(&m.rfull[sl], (q / NR) & 1u, m.abort, status, TB_WAIT_NS)) {
-        ok = false;
-        break;
-      }
-      const float *src = m.ring + ((size_t)sl * RS + (size_t)cw * HR) * D;
-      const int r0 = cc * RS + cw * HR;  // the slot's first row of this warp, in the tile
-      float4 v[PER];
+// ---- row conversion (by the fold warps) ---------------------------------------
+// Fold warp wf (0 .. 15) converts rows 8 wf .. 8 wf + 7 of a row tile: it
+// loads them from global memory (the L2 holds them: the MMA thread asks for
+// every tile TB_PREFETCH tiles ahead) and splits them into x_h | x_l (K-major,
+// 128-byte swizzle) in the tile's A stage.  Rows past the end are zeros.
+template <int D>
+struct TbConv {
+  static constexpr int F4 = D / 4;               // float4 per row
+  static constexpr int PER = 8 * F4 / 32;        // float4 per lane per tile (4 or 8)
+  static constexpr int LP = PER < 4 ? PER : 4;   // loaded ahead of the fold
+};
+
+template <int D, int U0, int U1>
+__device__ __forceinline__ void tb_rows_load(const TbRows &R, int64_t row0, int wf, int lane,
+                                             float4 (&v)[U1 - U0]) {
+  constexpr int F4 = TbConv<D>::F4;
 #pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int e = u * 32 + lane;
-        v[u] = row0 + r0 + e / F4 < R.nrows ? *reinterpret_cast<const float4 *>(src + 4 * e)
-                                             : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      }
-      __syncwarp();
-      if (lane == 0) hpc_mbar_arrive(&m.rfree[sl]);  // the slot is in registers
-      ++consumed;
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int e = u * 32 + lane;
-        const int r = r0 + e / F4;
-        const int t = 4 * (e % F4);
-        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[u].x, v[u].y);
-        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[u].z, v[u].w);
-        const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[u].x - f01.x, v[u].y - f01.y);
-        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[u].z - f23.x, v[u].w - f23.y);
-        const uint32_t off = tb_koff((uint32_t)r, (uint32_t)t, TB_M);
-        *reinterpret_cast<uint2 *>(ah + off) = make_uint2(tb_bits(h01), tb_bits(h23));
-        *reinterpret_cast<uint2 *>(al + off) = make_uint2(tb_bits(l01), tb_bits(l23));
-      }
-    }
-    if (!ok) break;
-    hpc_fence_proxy_async();  // the stage's generic writes, visible to the tensor core
-    __syncwarp();
-    if (lane == 0) hpc_mbar_arrive(&m.afull[st]);
-  }
-  // after an abort: copies still in flight land before the CTA goes on
-  if (issuer && consumed < issued) {
-    int no_abort = 0;
-    for (int c = consumed; c < issued; ++c) {
-      const uint32_t q = (gbase + (uint32_t)(c / CPT)) * CPT + (uint32_t)(c % CPT);
-      if (!hpc_mbar_wait(&m.rfull[q % NR], (q / NR) & 1u, (volatile int *)&no_abort, status,
-                         TB_DRAIN_NS))
-        break;
-    }
+  for (int u = U0; u < U1; ++u) {
+    const int e = u * 32 + lane;
+    const int64_t row = row0 + 8 * wf + e / F4;
+    v[u - U0] = row < R.nrows ? __ldg(reinterpret_cast<const float4 *>(R.rows + row * D) + e % F4)
+                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   }
 }
 
-// ---- MMA issuer (warp 2, one thread) ------------------------------------------
+template <int D, int U0, int U1>
+__device__ __forceinline__ void tb_rows_store(unsigned char *ah, unsigned char *al, int wf, int lane,
+                                              const float4 (&v)[U1 - U0]) {
+  constexpr int F4 = TbConv<D>::F4;
+#pragma unroll
+  for (int u = U0; u < U1; ++u) {
+    const int e = u * 32 + lane;
+    const int r = 8 * wf + e / F4;
+    const int t = 4 * (e % F4);
+    const float4 x = v[u - U0];
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y);
+    const __nv_bfloat162 h23 = __floats2bfloat162_rn(x.z, x.w);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(x.x - f01.x, x.y - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(x.z - f23.x, x.w - f23.y);
+    const uint32_t off = tb_koff((uint32_t)r, (uint32_t)t, TB_M);
+    *reinterpret_cast<uint2 *>(ah + off) = make_uint2(tb_bits(h01), tb_bits(h23));
+    *reinterpret_cast<uint2 *>(al + off) = make_uint2(tb_bits(l01), tb_bits(l23));
+  }
+}
+
+// First row of the CTA's i-th tile.
+__device__ __forceinline__ int64_t tb_tile_row0(const TbRows &R, int i) {
+  return (R.tile0 + (int64_t)i * R.tstep) * TB_M;
+}
+
+// This warp's rows of tile i (sequence number g): waits until the MMA has
+// released the stage, writes the first LP float4 per lane from v (loaded
+// earlier) and the rest from memory, and marks the warp's part ready.
+template <int D, int NP>
+__device__ __forceinline__ bool tb_convert(const TbSm &m, const TbRows &R, int i, uint32_t g, int wf,
+                                           const float4 (&v)[TbConv<D>::LP], int *status) {
+  using Cfg = TbCfg<D, NP>;
+  using Cv = TbConv<D>;
+  const int lane = threadIdx.x & 31;
+  const int st = (int)(g % Cfg::NSTAGE);
+  const uint32_t use = g / Cfg::NSTAGE;
+  if (use > 0 && !wait_warp(&m.afree[st], (use - 1) & 1u, m.abort, status, TB_WAIT_NS)) return false;
+  unsigned char *ah = m.a + (size_t)st * 2 * Cfg::ATILE;
+  unsigned char *al = ah + Cfg::ATILE;
+  tb_rows_store<D, 0, Cv::LP>(ah, al, wf, lane, v);
+  if constexpr (Cv::PER > Cv::LP) {
+    float4 w[Cv::PER - Cv::LP];
+    tb_rows_load<D, Cv::LP, Cv::PER>(R, tb_tile_row0(R, i), wf, lane, w);
+    tb_rows_store<D, Cv::LP, Cv::PER>(ah, al, wf, lane, w);
+  }
+  hpc_fence_proxy_async();  // the stage's generic writes, visible to the tensor core
+  __syncwarp();
+  if (lane == 0) hpc_mbar_arrive(&m.afull[st]);
+  return true;
+}
+
+// ---- MMA issuer (warp 0, one thread) ------------------------------------------
+// Also asks the L2 for the rows of the tile TB_PREFETCH tiles ahead.
 template <int D, int NP>
 __device__ __forceinline__ void tb_mma(const TbSm &m, const TbRows &R, uint32_t gbase, int *status) {
   using Cfg = TbCfg<D, NP>;
   constexpr uint32_t idesc = hpc_umma_idesc(1u, 1u, Cfg::BANKW, TB_M);
   constexpr uint32_t SBO = 8u * 128u;
   const uint32_t BH = hpc_smem_u32(m.bh), BL = hpc_smem_u32(m.bl);
+  auto prefetch = [&](int i) {
+    if (i >= R.ntiles) return;
+    const int64_t p0 = tb_tile_row0(R, i);
+    const int64_t nr = min((int64_t)TB_M, R.nrows - p0);
+    if (nr > 0) hpc_prefetch_l2_bulk(R.rows + p0 * D, (uint32_t)(nr * D * 4));
+  };
+  for (int i = Cfg::NSTAGE; i < TB_PREFETCH; ++i) prefetch(i);
   for (int i = 0; i < R.ntiles; ++i) {
     const uint32_t g = gbase + (uint32_t)i;
+    prefetch(i + TB_PREFETCH);
     const int st = (int)(g % Cfg::NSTAGE);
     const uint32_t use = g / Cfg::NSTAGE;
     if (!hpc_mbar_wait(&m.afull[st], use & 1u, m.abort, status, TB_WAIT_NS)) break;
@@ -407,28 +368,46 @@ __device__ __forceinline__ void tb_fold4_top3(float &t1, float &t2, float &t3, f
   tb_merge3(t1, t2, t3, fminf(a, c), fminf(M, mb), fmaxf(M, mb));
 }
 
-// ---- fold warps (warps 3-18) -------------------------------------------------
+// ---- fold warps (warps 1-16) -------------------------------------------------
 // Warpgroup e folds columns [e NP/4, (e+1) NP/4) of every tile into the
 // three smallest (value, index) keys per row and leaves them in the tile's
-// exchange buffer (the finishers merge the four).
+// exchange buffer (the finishers merge the four).  Each fold warp also
+// converts its eight rows of the tile NSTAGE tiles ahead into that tile's A
+// stage (the first NSTAGE tiles before the loop): with two stages after the
+// fold, so that the accumulator bank is released first; with one stage
+// before it, so that the next tile's MMAs run during the fold.
 template <int D, int NP>
 __device__ __forceinline__ void tb_fold(const TbSm &m, const TbRows &R, uint32_t gbase, int kp,
                                         int *status) {
   using Cfg = TbCfg<D, NP>;
+  using Cv = TbConv<D>;
   constexpr int IB = Cfg::IB;
+  constexpr int NS = Cfg::NSTAGE;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = (warp - TB_EPI0) >> 2, q = warp & 3;
+  const int wf = warp - TB_EPI0;
+  const int e = wf >> 2, q = warp & 3;
   const int r_in = 32 * q + lane;
   const int col0 = e * Cfg::CPW;
   const int part = Cfg::PARTS == 2 ? col0 / 256 : 0;
   const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+  for (int i = 0; i < min(NS, R.ntiles); ++i) {
+    float4 v[Cv::LP];
+    tb_rows_load<D, 0, Cv::LP>(R, tb_tile_row0(R, i), wf, lane, v);
+    if (!tb_convert<D, NP>(m, R, i, gbase + (uint32_t)i, wf, v, status)) return;
+  }
   for (int i = 0; i < R.ntiles; ++i) {
     const uint32_t g = gbase + (uint32_t)i;
     const int bk = Cfg::PARTS == 2 ? part : (int)(g & 1u);
     const uint32_t v = Cfg::PARTS == 2 ? g : (g >> 1);
     const int xb = (int)(g % Cfg::NX);
     const uint32_t xu = g / Cfg::NX;
-    const bool ok = wait_warp(&m.accf[bk], v & 1u, m.abort, status, TB_WAIT_NS);
+    const bool ahead = i + NS < R.ntiles;
+    float4 rows_ahead[Cv::LP];
+    if (ahead) tb_rows_load<D, 0, Cv::LP>(R, tb_tile_row0(R, i + NS), wf, lane, rows_ahead);
+    bool ok = wait_warp(&m.accf[bk], v & 1u, m.abort, status, TB_WAIT_NS);
+    if constexpr (NS == 1) {
+      if (ok && ahead) ok = tb_convert<D, NP>(m, R, i + NS, g + NS, wf, rows_ahead, status);
+    }
     // the three smallest keys of this warpgroup's columns, as two chains
     float d1 = __int_as_float(0x7f7fffff), d2 = d1, d3 = d1, e1 = d1, e2 = d1, e3 = d1;
     if (ok) {
@@ -456,6 +435,9 @@ __device__ __forceinline__ void tb_fold(const TbSm &m, const TbRows &R, uint32_t
     __syncwarp();
     if (lane == 0) hpc_mbar_arrive(&m.acce[bk]);  // this warp's columns are in registers
     if (!ok) break;
+    if constexpr (NS > 1) {
+      if (ahead && !tb_convert<D, NP>(m, R, i + NS, g + NS, wf, rows_ahead, status)) break;
+    }
     if (xu > 0 && !wait_warp(&m.xdone[xb], (xu - 1) & 1u, m.abort, status, TB_WAIT_NS)) break;
     {
       float *xp = m.xch + ((size_t)(xb * 4 + e) * TB_M + r_in) * 3;
@@ -468,7 +450,7 @@ __device__ __forceinline__ void tb_fold(const TbSm &m, const TbRows &R, uint32_t
   }
 }
 
-// ---- finishers (warps 19-26) ----------------------------------------------------
+// ---- finishers (warps 17-24) ----------------------------------------------------
 // Finisher warpgroup f takes the tiles g with g mod TB_NFIN == f: merges the
 // four partial top-3 of each row, frees the exchange buffer, and calls
 // `fin(row0w, row, valid, j1, j2, d1, d2, v3)` with the whole warp (lane l
@@ -785,14 +767,12 @@ __device__ __forceinline__ void tb_settle_queue(const float *__restrict__ rows,
   }
 }
 
-// One pass of the pipeline over a CTA's tiles (all 608 threads call it).
+// One pass of the pipeline over a CTA's tiles (all threads of the CTA call it).
 template <int D, int NP, typename Fin>
 __device__ __forceinline__ void tb_pass(const TbSm &m, const TbRows &R, uint32_t gbase, int kp, int *status,
                         Fin fin) {
   const int warp = threadIdx.x >> 5;
-  if (warp < TB_CONV) {
-    tb_convert<D, NP>(m, R, gbase, status);
-  } else if (warp == TB_MMAW) {
+  if (warp == TB_MMAW) {
     if ((threadIdx.x & 31) == 0) tb_mma<D, NP>(m, R, gbase, status);
     __syncwarp();
   } else if (warp < TB_FIN0) {
