@@ -748,21 +748,125 @@ __device__ __forceinline__ int tb_exact(const float *__restrict__ rows, int64_t 
   return queued ? TB_QUEUED : ok ? TB_DONE : TB_BAD;
 }
 
-// Settles the rows of the CTA's queue (all warps of the CTA; a warp per row):
-// every centroid, FP32 then FP64 (tb_rescore); `done(row, j, dd)` is then
-// called by the whole warp.
-template <int D, typename Done>
-__device__ __forceinline__ void tb_settle_queue(const float *__restrict__ rows,
+// Settles the rows of the CTA's queue after its pass, when no MMA or copy
+// touches shared memory any more: the CTA stages the exact centroid block
+// (-2c rows of hpc_cstride(D) floats and the (||c||^2, 0) pairs; the row
+// padding puts the rows that 32 lanes read at once in different banks) in
+// shared memory, below the flags and barriers, and each warp takes a row at a
+// time: the row in the warp's shared-memory slot, lane l the centroids
+// l, l + 32, ..., FP32 direct form in dimension order (relative bound
+// (D + 3) u); if the two best are not separated by that bound, FP64 in the
+// oracle's operation order for the centroids whose FP32 value lies within it
+// of the best, ties to the lowest index.  `done(row, j, dd)` is then called
+// by the whole warp (dd: the objective's FP32 direct-form distance).
+template <int D, int NP, typename Done>
+__device__ __forceinline__ void tb_settle_queue(const TbSm &m, const float *__restrict__ rows,
                                                 const TbQueue &queue, const hpc_cent_smem &gcs,
                                                 unsigned long long *stats, Done done) {
+  using Cfg = TbCfg<D, NP>;
   constexpr int CS = hpc_cstride(D);
-  const int warp = threadIdx.x >> 5;
+  constexpr int NPL = NP / 32;  // centroids per lane
+  constexpr size_t CM_BYTES = (size_t)NP * CS * 4, NZ_BYTES = (size_t)NP * 8;
+  static_assert(CM_BYTES + NZ_BYTES + (size_t)(TB_THREADS / 32) * D * 4 <= Cfg::DEADF,
+                "the centroid block fits below the flags");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nq = min(*queue.count, queue.cap);
+  if (nq == 0) return;  // the same for the whole CTA
+  const int kp = gcs.kp;
+  float *cm = reinterpret_cast<float *>(m.bh);
+  float2 *cnz = reinterpret_cast<float2 *>(m.bh + CM_BYTES);
+  float *xs = reinterpret_cast<float *>(m.bh + CM_BYTES + NZ_BYTES) + (size_t)warp * D;
+  {
+    const float4 *src = reinterpret_cast<const float4 *>(gcs.cm);
+    float4 *dst = reinterpret_cast<float4 *>(cm);
+    for (int e = threadIdx.x; e < kp * CS / 4; e += TB_THREADS) dst[e] = __ldcg(src + e);
+    for (int j = threadIdx.x; j < kp; j += TB_THREADS) cnz[j] = __ldcg(gcs.cnz + j);
+  }
+  __syncthreads();
+  constexpr float rho = (float)(D + 3) * HPC_U32 * 1.001f;
   for (int qi = warp; qi < nq; qi += TB_THREADS / 32) {
     const int64_t row = queue.rows[qi];
     const float *xg = rows + row * D;
-    const int j = tb_rescore<D>(xg, gcs, stats);
+    for (int t = lane * 4; t < D; t += 128)
+      *reinterpret_cast<float4 *>(xs + t) = __ldg(reinterpret_cast<const float4 *>(xg + t));
+    __syncwarp();
+    float acc[NPL];
+    uint32_t live = 0u;  // bit u: centroid lane + 32 u is live
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+      const int j = lane + 32 * u;
+      if (j < kp && cnz[j].x < HPC_DEAD) live |= 1u << u;
+      acc[u] = 0.0f;
+    }
+#pragma unroll 2
+    for (int t = 0; t < D; t += 4) {
+      const float4 x = *reinterpret_cast<const float4 *>(xs + t);
+#pragma unroll
+      for (int u = 0; u < NPL; ++u) {
+        const float4 c = *reinterpret_cast<const float4 *>(cm + (size_t)(lane + 32 * u) * CS + t);
+        const float d0 = __fmaf_rn(0.5f, c.x, x.x), d1 = __fmaf_rn(0.5f, c.y, x.y);
+        const float d2 = __fmaf_rn(0.5f, c.z, x.z), d3 = __fmaf_rn(0.5f, c.w, x.w);
+        acc[u] = __fmaf_rn(d0, d0, acc[u]);
+        acc[u] = __fmaf_rn(d1, d1, acc[u]);
+        acc[u] = __fmaf_rn(d2, d2, acc[u]);
+        acc[u] = __fmaf_rn(d3, d3, acc[u]);
+      }
+    }
+    float a1 = __int_as_float(0x7f800000), a2 = a1;
+    int ja = 0x7fffffff;
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+      if (!((live >> u) & 1u)) continue;
+      if (acc[u] < a1) {
+        a2 = a1;
+        a1 = acc[u];
+        ja = lane + 32 * u;
+      } else {
+        a2 = fminf(a2, acc[u]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float b1 = __shfl_xor_sync(0xffffffffu, a1, o);
+      const int jb = __shfl_xor_sync(0xffffffffu, ja, o);
+      const float b2 = __shfl_xor_sync(0xffffffffu, a2, o);
+      hpc_merge_top2(a1, ja, a2, b1, jb, b2);
+    }
+    int j = ja < kp ? ja : 0;
+    if (!(a2 - a1 > rho * (a1 + a2))) {
+      if (stats && lane == 0) atomicAdd(stats + 3, 1ull);
+      // the centroids whose exact value may be at most the best's
+      const float thr = a1 * ((1.0f + rho) / (1.0f - rho)) * 1.0001f;
+      double b = __longlong_as_double(0x7ff0000000000000ll);
+      int jb = 0x7fffffff;
+#pragma unroll
+      for (int u = 0; u < NPL; ++u) {
+        if (!((live >> u) & 1u) || !(acc[u] <= thr)) continue;
+        const float *cj = cm + (size_t)(lane + 32 * u) * CS;
+        double acc64 = 0.0;
+        for (int t = 0; t < D; ++t) {
+          const double c = -0.5 * (double)cj[t];
+          const double diff = __dsub_rn((double)xs[t], c);
+          acc64 = __dadd_rn(acc64, __dmul_rn(diff, diff));
+        }
+        if (acc64 < b) {  // u increases: ties keep the lower index
+          b = acc64;
+          jb = lane + 32 * u;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, b, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
+        if (ob < b || (ob == b && oj < jb)) {
+          b = ob;
+          jb = oj;
+        }
+      }
+      if (jb < kp) j = jb;
+    }
     const float dd = tb_direct<D>(xg, gcs.cm + (size_t)j * CS);
+    __syncwarp();  // the row slot is read before the next row is staged
     done(row, j, dd);
   }
 }
@@ -1003,7 +1107,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     });
     __syncthreads();
     // the queued rows, every warp
-    tb_settle_queue<D>(tk.S, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
+    tb_settle_queue<D, NP>(m, tk.S, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
       if (lane == 0) hpc_sum2_add(fs_hi, fs_lo, dd);
       const int old = it > 0 ? tk.plab[row] : -1;
       if (old != j) move(row, j, old);
@@ -1175,7 +1279,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcb_objective_kernel(TcbArgs a)
     }
   });
   __syncthreads();
-  tb_settle_queue<D>(a.X, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
+  tb_settle_queue<D, NP>(m, a.X, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
     if ((threadIdx.x & 31) == 0) {
       hpc_sum2_add(fs_hi, fs_lo, dd);
       if (a.labels) a.labels[row] = j;
