@@ -46,12 +46,16 @@ from paper_2311_04517_gb300 import synth  # noqa: E402
 METRIC = "point-centroid distances/s"
 UNIT = "distances/s"
 FALLBACK_HBM = 6800.0
+FALLBACK_BF16_SUSTAINED = 1700.0   # TFLOP/s, the profiling recipe's sustained fallback
+TIMED_BUDGET_S = 45.0              # timed work of a default run
 
 
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default: about TIMED_BUDGET_S of timed work, at least 5 "
+                        "and at most 100, from the last warm-up step; 5 for --impl reference)")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
     p.add_argument("--workload", default="large")
@@ -93,24 +97,47 @@ SMS, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 ALU_PEAK_TFLOPS = 2.0 * SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
 
-def roofline_bound(label: str, bytes_: float, flops: float, avg_ms: float, simt: bool,
+# the tensor-core search forms: products per FP32 product and the dtype's
+# share of the BF16 rate (NVIDIA's dense figures: TF32 1.1 of BF16's 2.25
+# PFLOP/s); split forms emulate an FP32 product with three
+TENSOR_FORMS = {"tf32": (1, 1.1 / 2.25), "split_tf32": (3, 1.1 / 2.25), "split_bf16": (3, 1.0)}
+
+
+def tensor_peak(form: str):
+    """(TFLOP/s of the form's FP32-equivalent products, source) from the
+    measured sustained BF16 rate (the kernels run inside seconds-long steps)."""
+    f = ROOT / "MEASURED_PEAKS.json"
+    if f.exists():
+        bf16, src = float(json.loads(f.read_text())["bf16_tflops_sustained"]), "measured"
+    else:
+        bf16, src = FALLBACK_BF16_SUSTAINED, "fallback"
+    n, ratio = TENSOR_FORMS[form]
+    return bf16 * ratio / n, (f"{src} bf16_tflops_sustained x {ratio:.3g} / {n} "
+                              f"({n} {form.split('_')[-1]} product(s) per FP32 product)")
+
+
+def roofline_bound(label: str, bytes_: float, flops: float, avg_ms: float, form: str,
                    hbm_gbs: float, hbm_src: str, traffic, extra=None):
     """Roofline of one kernel: HBM (bytes_ per launch) unless its
     contraction's flops take longer at the arithmetic peak than the bytes at
-    the HBM peak.  CUDA-core kernels (simt) are held against the FP32 FMA
-    peak; the tensor-core kernels do their products on the tensor cores,
-    whose rate is far above both, and stay HBM-bound."""
+    the HBM peak.  The CUDA-core form (simt) is held against the FP32 FMA
+    peak; the tensor-core forms against the tensor rate of their products
+    (TENSOR_FORMS)."""
     t_hbm = bytes_ / (hbm_gbs * 1e9)
-    t_alu = flops / (ALU_PEAK_TFLOPS * 1e12)
+    if form == "simt":
+        peak, peak_src, bound = (ALU_PEAK_TFLOPS,
+                                 "152 SMs x 128 FP32 lanes x 2070 MHz, 2 flops per FMA", "alu")
+    else:
+        (peak, peak_src), bound = tensor_peak(form), "tensor"
+    t_arith = flops / (peak * 1e12)
     entry = {"kernel": label, "traffic": traffic, "algorithmic_bytes_per_launch": bytes_,
-             "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms}
+             "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms, "form": form}
     if extra:
         entry.update(extra)
-    if simt and t_alu > t_hbm:
+    if t_arith > t_hbm:
         achieved = flops / (avg_ms / 1e3) / 1e12
-        entry.update({"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
-                      "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz, 2 flops per FMA",
-                      "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS})
+        entry.update({"bound": bound, "achieved": achieved, "peak": peak,
+                      "peak_source": peak_src, "unit": "TFLOP/s", "frac": achieved / peak})
     else:
         achieved = bytes_ / (avg_ms / 1e3) / 1e9
         entry.update({"bound": "hbm", "achieved": achieved, "peak": hbm_gbs,
@@ -119,15 +146,15 @@ def roofline_bound(label: str, bytes_: float, flops: float, avg_ms: float, simt:
     return entry
 
 
-def roofline_entry(kernel: str, simt: bool, n: int, d: int, k_mean: float, avg_ms: float,
+def roofline_entry(kernel: str, form: str, n: int, d: int, k_mean: float, avg_ms: float,
                    hbm_gbs: float, hbm_src: str, traffic):
     """The full-data objective's roofline: 4 n d bytes and 2 n k d flops per
     launch (k_mean the groups' mean k)."""
     return roofline_bound(f"{kernel} (full-data objective, Eq. 1)", float(n) * d * 4,
-                          2.0 * n * k_mean * d, avg_ms, simt, hbm_gbs, hbm_src, traffic)
+                          2.0 * n * k_mean * d, avg_ms, form, hbm_gbs, hbm_src, traffic)
 
 
-def lloyd_roofline(kernel: str, simt: bool, passes_rows_k, d: int, launches: int, avg_ms: float,
+def lloyd_roofline(kernel: str, form: str, passes_rows_k, d: int, launches: int, avg_ms: float,
                    hbm_gbs: float, hbm_src: str, traffic):
     """The Lloyd launch's roofline: each assignment pass of worker w reads
     its sample (4 s_w d bytes) and evaluates s_w k_w distances of 2 d flops
@@ -136,7 +163,7 @@ def lloyd_roofline(kernel: str, simt: bool, passes_rows_k, d: int, launches: int
     rows = sum(float(p) * float(s_) for p, s_, _ in passes_rows_k)
     dists = sum(float(p) * float(s_) * float(k_) for p, s_, k_ in passes_rows_k)
     return roofline_bound(f"{kernel} (Lloyd iterations, Algorithm 1)", 4.0 * d * rows / launches,
-                          2.0 * d * dists / launches, avg_ms, simt, hbm_gbs, hbm_src, traffic,
+                          2.0 * d * dists / launches, avg_ms, form, hbm_gbs, hbm_src, traffic,
                           {"launches_timed": launches})
 
 
@@ -321,8 +348,13 @@ def bench_workload(args):
 
 
 def n_comp(args):
+    """Hybrid strategy: the first half of the rounds competitive (the
+    paper's T1 = T2); with the step count left to the bench, ten rounds past
+    the warm-up."""
     if args.n_competitive is not None:
         return args.n_competitive
+    if args.steps is None:
+        return args.warmup + 10
     return (args.warmup + args.steps) // 2
 
 
@@ -453,6 +485,7 @@ def run_reference(args):
         return
     import oracle as orc
     orc.build()
+    K = args.steps if args.steps is not None else 5
     wl = bench_workload(args)
     ws = synth.worker_setup(wl)
     strat = {"cooperative": orc.COOPERATIVE, "hybrid": orc.HYBRID}.get(args.strategy,
@@ -471,7 +504,7 @@ def run_reference(args):
                 orc.objective(X, C, deg)
                 kb.append(int(ws.k[b]))
             return dist_count(res["iters"], ws.s, ws.k, wl.n, kb)
-        sample = f"{args.steps} full oracle steps (round + full-data objective)"
+        sample = f"{K} full oracle steps (round + full-data objective)"
         bo = None
     else:
         n_host = min(wl.n, max(1, 200_000_000 // wl.d))
@@ -483,15 +516,15 @@ def run_reference(args):
         step(r)
     dist = 0.0
     t0 = time.perf_counter()
-    for r in range(args.warmup, args.warmup + args.steps):
+    for r in range(args.warmup, args.warmup + K):
         dist += step(r)
     el = time.perf_counter() - t0
     v = dist / el
     if bo is not None:
-        sample = bo.describe(args.steps, el) + f"; prefix rows: {how}"
+        sample = bo.describe(K, el) + f"; prefix rows: {how}"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": el * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": K, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / max(1, K), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(wl, args.strategy, args),
             "cpu_baseline": {"kind": "oracle", "cores": orc.num_threads(),
@@ -657,8 +690,7 @@ def run_mine(args):
     Xo = X[ra:rb]          # this rank's rows of the full-data objective
     groups = group_members(ws)
     f_sse = torch.zeros(len(groups), dtype=torch.float64, device=dev)
-    K, Wm = args.steps, args.warmup
-    iters_log = torch.zeros((K, Wl), dtype=torch.int32, device=dev)
+    Wm = args.warmup
     best_log = []
     fhat_host = torch.empty(Wl, dtype=torch.float64).pin_memory()
 
@@ -735,9 +767,23 @@ def run_mine(args):
         if ev is not None:
             ev[1].record()
 
+    t_warm = 0.0
     for r in range(Wm):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
         step(r)
+        torch.cuda.synchronize(dev)
+        t_warm = time.perf_counter() - t0
     ctx.check_status()
+    if args.steps is not None:
+        K = args.steps
+    else:
+        # about TIMED_BUDGET_S of timed steps (the slowest rank's estimate)
+        tw = torch.tensor([t_warm], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tw, op=dist.ReduceOp.MAX)
+        K = int(min(100, max(5, TIMED_BUDGET_S / max(float(tw.item()), 1e-6))))
+    iters_log = torch.zeros((K, Wl), dtype=torch.int32, device=dev)
     # the objective's search form per (d, k), measured on this data with the
     # incumbents the warm-up rounds produced (outside the timed steps)
     forms = {}
@@ -878,7 +924,7 @@ def run_mine(args):
                   H.HPC_SEARCH_TF32: "tc_objective_kernel" if kb0 <= 128
                   else "tw_objective_kernel",
                   H.HPC_SEARCH_SPLIT_BF16: "tcb_objective_kernel"}[form0]
-    obj_entry = roofline_entry(obj_kernel, form0 == H.HPC_SEARCH_SIMT, rb - ra, wl.d, k_mean,
+    obj_entry = roofline_entry(obj_kernel, H.SEARCH_NAMES[form0], rb - ra, wl.d, k_mean,
                                obj_avg_ms, hbm, src,
                                profiled_traffic("objective", wl.name, obj_kernel))
     # the Lloyd launches of the timed steps (their phase times: one launch
@@ -893,7 +939,7 @@ def run_mine(args):
     else:
         it_rows = [(int(iters[i][w]) + 1, int(ws.s[w0 + w]), int(ws.k[w0 + w]))
                    for i in range(K) for w in range(Wl)]
-    lloyd_entry = lloyd_roofline(lloyd_kernel_name, lsched["form"] == "simt", it_rows, wl.d,
+    lloyd_entry = lloyd_roofline(lloyd_kernel_name, lsched["form"], it_rows, wl.d,
                                  len(lloyd_ms) * chunks,
                                  float(np.sum(lloyd_ms)) / (len(lloyd_ms) * chunks), hbm, src,
                                  profiled_traffic("lloyd", wl.name, lloyd_kernel_name))

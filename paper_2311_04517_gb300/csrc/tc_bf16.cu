@@ -413,20 +413,24 @@ __device__ __forceinline__ void tb_fold(const TbSm &m, const TbRows &R, uint32_t
     if (ok) {
       hpc_tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < Cfg::CPW / 32; ++c) {
-        const int cb = col0 + 32 * c;
+      for (int c = 0; c < Cfg::CPW / 16; ++c) {
+        const int cb = col0 + 16 * c;
         if (cb >= kp) break;  // same for the whole warp
-        float acc[32];
-        hpc_tmem_ld32(m.tmem + lane_base + (uint32_t)(bk * Cfg::BANKW + cb - part * 256), acc);
+        float acc[16];
+        hpc_tmem_ld16(m.tmem + lane_base + (uint32_t)(bk * Cfg::BANKW + cb - part * 256), acc);
 #pragma unroll
-        for (int jj = 0; jj < 32; jj += 4) {
-          const float4 cn = *reinterpret_cast<const float4 *>(m.cn + cb + jj);
+        for (int jj = 0; jj < 16; jj += 8) {
+          const float4 ca = *reinterpret_cast<const float4 *>(m.cn + cb + jj);
+          const float4 cc = *reinterpret_cast<const float4 *>(m.cn + cb + jj + 4);
           const int j = cb + jj;
-          float &t1 = (jj & 4) ? e1 : d1, &t2 = (jj & 4) ? e2 : d2, &t3 = (jj & 4) ? e3 : d3;
-          tb_fold4_top3(t1, t2, t3, hpc_key_b<IB>(cn.x + acc[jj], j),
-                        hpc_key_b<IB>(cn.y + acc[jj + 1], j + 1),
-                        hpc_key_b<IB>(cn.z + acc[jj + 2], j + 2),
-                        hpc_key_b<IB>(cn.w + acc[jj + 3], j + 3));
+          tb_fold4_top3(d1, d2, d3, hpc_key_b<IB>(ca.x + acc[jj], j),
+                        hpc_key_b<IB>(ca.y + acc[jj + 1], j + 1),
+                        hpc_key_b<IB>(ca.z + acc[jj + 2], j + 2),
+                        hpc_key_b<IB>(ca.w + acc[jj + 3], j + 3));
+          tb_fold4_top3(e1, e2, e3, hpc_key_b<IB>(cc.x + acc[jj + 4], j + 4),
+                        hpc_key_b<IB>(cc.y + acc[jj + 5], j + 5),
+                        hpc_key_b<IB>(cc.z + acc[jj + 6], j + 6),
+                        hpc_key_b<IB>(cc.w + acc[jj + 7], j + 7));
         }
       }
       tb_merge3(d1, d2, d3, e1, e2, e3);
