@@ -412,17 +412,20 @@ __device__ __forceinline__ void tb_fold(const TbSm &m, const TbRows &R, uint32_t
     float d1 = __int_as_float(0x7f7fffff), d2 = d1, d3 = d1, e1 = d1, e2 = d1, e3 = d1;
     if (ok) {
       hpc_tc_fence_after();
+      // keys carry the column's index within this warpgroup's range (a
+      // constant of the unrolled code: one logic instruction a key); the
+      // finishers add the range's first column
 #pragma unroll
       for (int c = 0; c < Cfg::CPW / 16; ++c) {
         const int cb = col0 + 16 * c;
-        if (cb >= kp) break;  // same for the whole warp
+        if (cb >= kp) continue;  // the same for the whole warp
         float acc[16];
         hpc_tmem_ld16(m.tmem + lane_base + (uint32_t)(bk * Cfg::BANKW + cb - part * 256), acc);
 #pragma unroll
         for (int jj = 0; jj < 16; jj += 8) {
           const float4 ca = *reinterpret_cast<const float4 *>(m.cn + cb + jj);
           const float4 cc = *reinterpret_cast<const float4 *>(m.cn + cb + jj + 4);
-          const int j = cb + jj;
+          const int j = 16 * c + jj;
           tb_fold4_top3(d1, d2, d3, hpc_key_b<IB>(ca.x + acc[jj], j),
                         hpc_key_b<IB>(ca.y + acc[jj + 1], j + 1),
                         hpc_key_b<IB>(ca.z + acc[jj + 2], j + 2),
@@ -482,9 +485,11 @@ __device__ __forceinline__ void tb_finish(const TbSm &m, const TbRows &R, uint32
       d2 = xp[1];
       lo3 = xp[2];
 #pragma unroll
-      for (int o = 1; o < 4; ++o) {
+      for (int o = 1; o < 4; ++o) {  // warpgroup o's keys: its first column added
         const float *xo = xp + (size_t)o * TB_M * 3;
-        tb_merge3(d1, d2, lo3, xo[0], xo[1], xo[2]);
+        const int c0 = o * Cfg::CPW;
+        tb_merge3(d1, d2, lo3, __int_as_float(__float_as_int(xo[0]) | c0),
+                  __int_as_float(__float_as_int(xo[1]) | c0), __int_as_float(__float_as_int(xo[2]) | c0));
       }
     }
     __syncwarp();
@@ -498,36 +503,24 @@ __device__ __forceinline__ void tb_finish(const TbSm &m, const TbRows &R, uint32
   }
 }
 
-// ||x||^2 and the objective's FP32 direct-form distance to the centroid
-// whose -2c row is cm (two interleaved partial sums, relative error
-// <= (D/2 + 4) u), in one read of the row.  Centroid rows are read through
-// L2 (__ldcg): the exact block is rewritten between Lloyd iterations.
+// The objective's FP32 direct-form distance from row x to the centroid whose
+// -2c row is cm (two interleaved partial sums, relative error <= (D/2 + 4) u),
+// one thread.  Centroid rows are read through L2 (__ldcg): the exact block is
+// rewritten between Lloyd iterations.
 template <int D>
-__device__ __forceinline__ void tb_norm_direct(const float *__restrict__ x, const float *cm,
-                                               float *nx, float *dd) {
-  float2 sx = make_float2(0.0f, 0.0f), sd = make_float2(0.0f, 0.0f);
+__device__ __forceinline__ float tb_direct(const float *__restrict__ x, const float *cm) {
+  float2 sd = make_float2(0.0f, 0.0f);
   const float2 half = make_float2(0.5f, 0.5f);
 #pragma unroll 4
   for (int t = 0; t < D; t += 4) {
     const float4 xv = __ldg(reinterpret_cast<const float4 *>(x + t));
     const float4 cv = __ldcg(reinterpret_cast<const float4 *>(cm + t));
-    const float2 x01 = make_float2(xv.x, xv.y), x23 = make_float2(xv.z, xv.w);
-    sx = hpc_fma2(x01, x01, sx);
-    sx = hpc_fma2(x23, x23, sx);
-    const float2 e01 = hpc_fma2(half, make_float2(cv.x, cv.y), x01);
-    const float2 e23 = hpc_fma2(half, make_float2(cv.z, cv.w), x23);
+    const float2 e01 = hpc_fma2(half, make_float2(cv.x, cv.y), make_float2(xv.x, xv.y));
+    const float2 e23 = hpc_fma2(half, make_float2(cv.z, cv.w), make_float2(xv.z, xv.w));
     sd = hpc_fma2(e01, e01, sd);
     sd = hpc_fma2(e23, e23, sd);
   }
-  *nx = sx.x + sx.y;
-  *dd = sd.x + sd.y;
-}
-
-template <int D>
-__device__ __forceinline__ float tb_direct(const float *__restrict__ x, const float *cm) {
-  float nx, dd;
-  tb_norm_direct<D>(x, cm, &nx, &dd);
-  return dd;
+  return sd.x + sd.y;
 }
 
 // Exact assignment of one row by the whole warp (every lane passes the same
@@ -661,6 +654,67 @@ struct TbQueue {
 
 enum { TB_DONE = 1, TB_BAD = 0, TB_QUEUED = 2 };
 
+// FP32 direct-form distances (and, with NORM, squared norms) of the warp's
+// rows whose lanes are set in `todo` (lane l: row row0w + l, centroid jl),
+// by 8-lane groups over dimensions: each round, group g takes the g-th of
+// the next four rows, lane i of the group reads dimensions 4i + 32v ..
+// 4i + 32v + 3 of the row and of the centroid's -2c row (coalesced 128-byte
+// pieces), the group adds its lanes' partial sums by shuffles, and the row's
+// own lane picks them up.  Every lane calls it; lanes not in `todo` keep
+// their nx, dd.  Relative bounds as for any order of the D nonnegative
+// terms: (D + 3) u for the distance.
+template <int D, bool NORM>
+__device__ __forceinline__ void tb_group_direct(const float *__restrict__ rows, int64_t row0w,
+                                                unsigned todo, int jl, const float *cm, float &nx,
+                                                float &dd) {
+  constexpr int CS = hpc_cstride(D);
+  constexpr int V = D / 32;
+  const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
+  while (todo) {  // the same for the whole warp
+    unsigned t = todo;
+    for (int i = 0; i < g; ++i) t &= t - 1;
+    const int src = t ? __ffs(t) - 1 : -1;  // this group's row (lane), if any
+    const int j = __shfl_sync(0xffffffffu, jl, src < 0 ? 0 : src);
+    float pn = 0.0f, pd = 0.0f;
+    if (src >= 0) {
+      const float *xr = rows + (row0w + src) * D + 4 * sl;
+      const float *cr = cm + (size_t)j * CS + 4 * sl;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(xr + 32 * v));
+        const float4 c = __ldcg(reinterpret_cast<const float4 *>(cr + 32 * v));
+        if constexpr (NORM) {
+          pn = __fmaf_rn(x.x, x.x, pn);
+          pn = __fmaf_rn(x.y, x.y, pn);
+          pn = __fmaf_rn(x.z, x.z, pn);
+          pn = __fmaf_rn(x.w, x.w, pn);
+        }
+        const float e0 = __fmaf_rn(0.5f, c.x, x.x), e1 = __fmaf_rn(0.5f, c.y, x.y);
+        const float e2 = __fmaf_rn(0.5f, c.z, x.z), e3 = __fmaf_rn(0.5f, c.w, x.w);
+        pd = __fmaf_rn(e0, e0, pd);
+        pd = __fmaf_rn(e1, e1, pd);
+        pd = __fmaf_rn(e2, e2, pd);
+        pd = __fmaf_rn(e3, e3, pd);
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      pd += __shfl_xor_sync(0xffffffffu, pd, o);
+      if constexpr (NORM) pn += __shfl_xor_sync(0xffffffffu, pn, o);
+    }
+    // lane l's row went to group popc(todo below l) when that is under 4
+    const int rank = __popc(todo & ((1u << lane) - 1u));
+    const bool mine = ((todo >> lane) & 1u) && rank < 4;
+    const float rd = __shfl_sync(0xffffffffu, pd, 8 * (rank < 4 ? rank : 0));
+    const float rn = NORM ? __shfl_sync(0xffffffffu, pn, 8 * (rank < 4 ? rank : 0)) : 0.0f;
+    if (mine) {
+      dd = rd;
+      if constexpr (NORM) nx = rn;
+    }
+    for (int i = 0; i < 4; ++i) todo &= todo - 1;
+  }
+}
+
 // The exact stages of one row (whole warp; lane l's row is row0w + l).
 // Returns TB_DONE with the exact nearest centroid in *j_out and its FP32
 // direct-form distance in *dd_out, TB_QUEUED when the row went to the CTA's
@@ -677,7 +731,7 @@ __device__ __forceinline__ int tb_exact(const float *__restrict__ rows, int64_t 
   if (!found) j1 = 0;
   const float *xg = rows + (valid ? row : 0) * D;
   float nx = 0.0f, dd = 0.0f;
-  if (valid) tb_norm_direct<D>(xg, gcs.cm + (size_t)j1 * CS, &nx, &dd);
+  tb_group_direct<D, true>(rows, row0w, __ballot_sync(0xffffffffu, valid), j1, gcs.cm, nx, dd);
   const float rad = sqrtf(nx) * 1.0001f + gcs.cmax * 1.0001f;
   float win = 2.0f * TB_E_REL * rad * rad;
   win += 1.0001f * ldexpf(1.0f, IB - 22) * (fabsf(d1) + fabsf(d2));  // keys
@@ -689,12 +743,13 @@ __device__ __forceinline__ int tb_exact(const float *__restrict__ rows, int64_t 
   constexpr float rho = (float)(D + 3) * HPC_U32 * 1.001f;  // FP32 direct-form bound
   bool full = false;
   const bool near = ok && !(d2 - d1 > win);
+  // the two nearest by the tensor-core values, exactly; every other
+  // centroid's tensor-core key is at least lo3, the third smallest, so its
+  // distance is at least ||x||^2 + lo3 - E (less lo3's own key error)
+  const bool has2 = near && d2 < HPC_DEAD * 0.5f && j2 != j1;
+  float ex2 = __int_as_float(0x7f800000), unused = 0.0f;
+  tb_group_direct<D, false>(rows, row0w, __ballot_sync(0xffffffffu, has2), j2, gcs.cm, unused, ex2);
   if (near) {
-    // the two nearest by the tensor-core values, exactly; every other
-    // centroid's tensor-core key is at least lo3, the third smallest, so its
-    // distance is at least ||x||^2 + lo3 - E (less lo3's own key error)
-    const bool has2 = d2 < HPC_DEAD * 0.5f && j2 != j1;
-    const float ex2 = has2 ? tb_direct<D>(xg, gcs.cm + (size_t)j2 * CS) : __int_as_float(0x7f800000);
     const float E = 0.5f * win + 1.0001f * ldexpf(1.0f, IB - 23) * fabsf(lo3);
     const float others = lo3 >= HPC_DEAD * 0.5f
                              ? __int_as_float(0x7f800000)
