@@ -698,7 +698,7 @@ static int round_enqueue(hpc_ctx *c, const hpc_round_plan &p, uint32_t *round_de
     if (int rc = hpc_lloyd_run(c->L, lh)) return plan_fail(c, rc, "lloyd launch");
     if (timed)
       if (int rc = timing_mark(c, ev++, 2)) return rc;
-    c->launches += 2;
+    c->launches += 2 + (kh.W > 1 && kh.W <= HPC_KPP_SPLIT_MAX ? 1 : 0);
   }
   return HPC_OK;
 }

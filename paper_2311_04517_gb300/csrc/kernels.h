@@ -15,6 +15,9 @@ struct hpc_gridbar;
 
 // Largest batch of independent problems one launch takes.
 #define HPC_MAX_TASKS 4096
+// batched seeding launches of up to this many workers are re-split on the
+// device over the workers with a centroid to seed (one more launch)
+#define HPC_KPP_SPLIT_MAX 128
 
 struct hpc_launch {
   cudaStream_t stream;

@@ -88,8 +88,11 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
   __shared__ unsigned long long s_tgt[HPC_MAX_CAND];
   __shared__ int s_lstar;
 
-  // this block's task (one worker's sample) and its place in the task's group
-  const hpc_kpp_task tk = a.W == 1 ? a.single : a.tasks[a.block_task[blockIdx.x]];
+  // this block's task (one worker's sample) and its place in the task's
+  // group; blocks the split left without a task have nothing to do
+  const int bt = a.W == 1 ? 0 : a.block_task[blockIdx.x];
+  if (bt < 0) return;
+  const hpc_kpp_task tk = a.W == 1 ? a.single : a.tasks[bt];
   const uint32_t round = a.round_dev ? *a.round_dev : a.round;
   const int k = tk.k, d = a.d, L = a.L;
   const int64_t s = tk.s;
@@ -310,6 +313,89 @@ __global__ void __launch_bounds__(THREADS) kmeanspp_kernel(KppArgs a) {
   }
 }
 
+// The blocks of a batched seeding launch, given to the workers that have a
+// centroid to seed.  After the first round a round reseeds few centroids in
+// few workers (those whose clusters emptied), and each of them first takes
+// the D^2 pass over its sample against every live centroid; the host's plan,
+// made before the flags are known, spreads the launch over every worker in
+// proportion to s k and would leave those workers a few blocks each.  This
+// one-block kernel runs before the seeding launch on the same stream (and in
+// a recorded round), reads the flags, and splits the launch's G blocks over
+// the workers with a degenerate slot in proportion to s (k + (L + 1) n),
+// n their degenerate slots: one block each first, at most one block per
+// `rows_per_block` rows and `cap` blocks; the other blocks get no task.  The
+// seeding decisions do not depend on the split (exact fixed-point sums, one
+// global target search).
+
+__global__ void kpp_split_kernel(hpc_kpp_task *tasks, int *block_task, int W, int G,
+                                 int rows_per_block, int64_t cap, int L) {
+  __shared__ double s_work[HPC_KPP_SPLIT_MAX];
+  __shared__ int s_cap[HPC_KPP_SPLIT_MAX], s_nb[HPC_KPP_SPLIT_MAX], s_b0[HPC_KPP_SPLIT_MAX + 1];
+  for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    const int k = tasks[w].k;
+    const uint8_t *deg = tasks[w].deg;
+    const int64_t s = tasks[w].s;
+    int nd = 0;
+    for (int j = 0; j < k; ++j) nd += deg[j] != 0;
+    s_work[w] = nd > 0 && s > 0 ? (double)s * (double)(k + (L + 1) * nd) : 0.0;
+    s_cap[w] = (int)min(cap, (s + rows_per_block - 1) / rows_per_block);
+    s_nb[w] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int needy = 0;
+    double tot = 0.0;
+    for (int w = 0; w < W; ++w)
+      if (s_work[w] > 0.0) {
+        ++needy;
+        tot += s_work[w];
+      }
+    int used = 0;
+    if (needy > 0 && needy <= G) {
+      const int extra = G - needy;
+      for (int w = 0; w < W; ++w) {
+        if (s_work[w] <= 0.0) continue;
+        const int nb = min(s_cap[w], 1 + (int)floor((double)extra * (s_work[w] / tot)));
+        s_nb[w] = max(nb, 1);
+        used += s_nb[w];
+      }
+      // the rest one at a time: to the worker with the most work per block
+      // that can still take one
+      while (used < G) {
+        int best = -1;
+        double bl = 0.0;
+        for (int w = 0; w < W; ++w) {
+          if (s_work[w] <= 0.0 || s_nb[w] >= s_cap[w]) continue;
+          const double l = s_work[w] / s_nb[w];
+          if (best < 0 || l > bl) {
+            best = w;
+            bl = l;
+          }
+        }
+        if (best < 0) break;
+        ++s_nb[best];
+        ++used;
+      }
+    }
+    s_b0[0] = 0;
+    for (int w = 0; w < W; ++w) {
+      s_b0[w + 1] = s_b0[w] + s_nb[w];
+      tasks[w].block0 = s_b0[w];
+      tasks[w].nblocks = s_nb[w];
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+    int owner = -1;
+    for (int w = 0; w < W; ++w)
+      if (b >= s_b0[w] && b < s_b0[w + 1]) {
+        owner = w;
+        break;
+      }
+    block_task[b] = owner;
+  }
+}
+
 size_t kpp_smem_bytes(int D, int k, int L) {
   return ((size_t)k * D + (size_t)L * D) * 4 + (size_t)k + 16;
 }
@@ -355,6 +441,12 @@ int kpp_plan_t(const hpc_launch &Lc, KppLaunch &h) {
 template <int D>
 int kpp_run_t(const hpc_launch &Lc, const KppLaunch &h) {
   auto kern = kmeanspp_kernel<D, kpp_threads<D>()>;
+  if (h.W > 1 && h.W <= HPC_KPP_SPLIT_MAX) {
+    kpp_split_kernel<<<1, 128, 0, Lc.stream>>>(const_cast<hpc_kpp_task *>(h.tasks_dev),
+                                               const_cast<int *>(h.block_task_dev), h.W, (int)h.grid,
+                                               kpp_threads<D>(), h.chunk_cap, h.L);
+    if (cudaGetLastError() != cudaSuccess) return HPC_ERR_CUDA;
+  }
   KppArgs a;
   a.W = h.W;
   a.single = h.tasks[0];
