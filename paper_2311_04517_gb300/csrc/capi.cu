@@ -134,7 +134,9 @@ struct TaskHeader {
   unsigned mx[2];
   unsigned long long phi[2 * 8];
   unsigned long long gobj[3];  // Lloyd's fixed-point sample objectives
-  unsigned char pad1[256 - 32 - 128 - 24];
+  unsigned lpop;               // a batched tensor-core Lloyd launch's next follow-up (first worker of the chunk)
+  unsigned pad2;
+  unsigned char pad1[256 - 32 - 128 - 24 - 8];
 };
 static_assert(sizeof(TaskHeader) == 256, "task header is one 256-byte line");
 
@@ -503,7 +505,7 @@ static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, i
   need += tcl_queue_ws(c, d, kmax);
   *tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) + pad256((size_t)W * sizeof(hpc_round_worker)) +
                pad256((size_t)W * sizeof(hpc_kpp_task)) + pad256((size_t)W * sizeof(hpc_lloyd_task)) +
-               2 * (size_t)nchunks * pad256((size_t)c->grid_bound * 4);
+               3 * (size_t)nchunks * pad256((size_t)c->grid_bound * 4);
   return need + pad256((size_t)W * 8) + pad256((size_t)W * 4) + *tab_bytes + 1024;
 }
 
@@ -598,9 +600,9 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     LloydLaunch &lh = p.ll[ch];
     lh.W = cw;
     lh.tasks = lt_h + w0;
-    lh.block_task_host = th.take<int>((size_t)c->grid_bound);
+    lh.block_task_host = th.take<int>(2 * (size_t)c->grid_bound);  // first tasks, then follow-ups
     lh.tasks_dev = lt_d + w0;
-    lh.block_task_dev = td.take<int>((size_t)c->grid_bound);
+    lh.block_task_dev = td.take<int>(2 * (size_t)c->grid_bound);
     lh.d = d;
     lh.kmax = kk;
     lh.max_iter = max_iter;
@@ -613,6 +615,7 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     lh.queue = lqueue;
     lh.queue_cap = lqueue ? HPC_LLOYD_QUEUE_CAP : 0;
     lh.queue_ctas = c->L.num_sms;
+    lh.pop = &hdr[w0].lpop;
     if (int rc = hpc_lloyd_plan(c->L, lh)) return plan_fail(c, rc, "lloyd: unsupported shape");
   }
   if (cv.off > cv.cap || th.off > th.cap) return fail(c, HPC_ERR_NOMEM, "round scratch layout overflow");

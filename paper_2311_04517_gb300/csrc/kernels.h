@@ -60,7 +60,8 @@ struct hpc_lloyd_task {
 struct LloydLaunch {
   int W;
   hpc_lloyd_task *tasks;       // host array [W]; block0 / nblocks written by the plan
-  int *block_task_host;        // host [grid] (W > 1), written by the plan
+  int *block_task_host;        // host [grid] (W > 1), written by the plan; the
+                               // tensor-core plan also uses [max_blocks, max_blocks + grid)
   const hpc_lloyd_task *tasks_dev;  // device copy of tasks (W > 1), uploaded by the caller
   const int *block_task_dev;        // device copy of block_task_host (W > 1)
   int d, kmax;
@@ -88,6 +89,10 @@ struct LloydLaunch {
   int64_t *queue;
   int64_t queue_cap;
   int64_t queue_ctas;
+  // nullable, zero at launch: the counter from which the tensor-core Lloyd's
+  // CTAs take the tasks left to them (W > 1); nfollow written by the plan
+  unsigned *pop;
+  int nfollow;
 };
 
 // ---- K-means++ (one task = one sample) ----

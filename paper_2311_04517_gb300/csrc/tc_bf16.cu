@@ -56,6 +56,8 @@
 // TMEM is freed.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "assign.cuh"
@@ -997,7 +999,10 @@ struct TclArgs {
   int W;
   hpc_lloyd_task single;
   const hpc_lloyd_task *tasks;
-  const int *block_task;
+  const int *block_task;   // W > 1: each CTA's first task (-2: take one from the list)
+  const int *follow;       // W > 1: the tasks CTAs take as they become free, largest first
+  int nfollow;
+  unsigned *pop;           // W > 1: the list's next entry (zero at launch)
   int max_iter;
   double tol;
   int *status;
@@ -1021,10 +1026,6 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   __shared__ int s_qn;
 
   if (a.round_advance && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.round_advance, 1u);
-  const hpc_lloyd_task tk = a.W == 1 ? a.single : a.tasks[a.block_task[blockIdx.x]];
-  const int k = tk.k, kp = (k + 1) & ~1;
-  const int64_t s = tk.s;
-  const int G = tk.nblocks, lb = (int)blockIdx.x - tk.block0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char *base =
       reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -1033,15 +1034,44 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   if (threadIdx.x == 0) {
     tb_init_barriers<D, NP>(m);
     s_abort = 0;
-    s_umax = s_cmax = s_nmax = s_live = 0u;
-    s_qn = 0;
   }
   if (warp == TB_MMAW) hpc_tmem_alloc(&s_tmem, Cfg::TCOLS);
-  for (int j = threadIdx.x; j < 512; j += TB_THREADS) m.dead[j] = (j >= k) || tk.deg[j] != 0;
   hpc_tc_fence_before();
   __syncthreads();
   hpc_tc_fence_after();
   m.tmem = s_tmem;
+  // the CTA's tasks, one after another: a task with a group of CTAs of its
+  // own, or small tasks packed into this CTA (each with a group of one);
+  // the pipeline's tile sequence runs on from task to task
+  uint32_t gbase = 0, drains = 0;
+  // the next task from the list (the same for the whole CTA), -1 when empty
+  auto take = [&]() {
+    if (threadIdx.x == 0) {
+      const unsigned i = atomicAdd(a.pop, 1u);
+      s_qn = i < (unsigned)a.nfollow ? a.follow[i] : -1;
+    }
+    __syncthreads();
+    const int t = s_qn;
+    __syncthreads();
+    return t;
+  };
+  int tix = a.W == 1 ? 0 : a.block_task[blockIdx.x];
+  bool alone = false;  // a task from the list: this CTA alone
+  if (tix == -2) {
+    tix = take();
+    alone = true;
+  }
+  while (tix >= 0) {
+  const hpc_lloyd_task tk = a.W == 1 ? a.single : a.tasks[tix];
+  const int k = tk.k, kp = (k + 1) & ~1;
+  const int64_t s = tk.s;
+  const int G = alone ? 1 : tk.nblocks, lb = alone ? 0 : (int)blockIdx.x - tk.block0;
+  if (threadIdx.x == 0) {
+    s_umax = s_cmax = s_nmax = s_live = 0u;
+    s_qn = 0;
+  }
+  for (int j = threadIdx.x; j < 512; j += TB_THREADS) m.dead[j] = (j >= k) || tk.deg[j] != 0;
+  __syncthreads();
 
   // Phase 0: largest |x| of the sample (fixed-point grid, non-finite rows),
   // zero sums, B from the starting centroids
@@ -1104,8 +1134,8 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   R.tile0 = lb;
   R.tstep = G;
   R.ntiles = lb < ntiles ? (int)((ntiles - 1 - lb) / G + 1) : 0;
-  uint32_t gbase = 0, drains = 0;
   double f_prev = 0.0;
+  bool finished = false;
   for (int it = 0; run; ++it) {
     // Phase A: assignment of the CTA's rows, sums of the rows that moved
     float fs_hi = 0.0f, fs_lo = 0.0f;
@@ -1205,6 +1235,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
         }
         if (tk.fhat) hpc_incumbent_block(tk, D, f, it);
       }
+      finished = true;
       break;
     }
     tb_build_b<D, NP>(m, k, tk.gcent, lb == 0, &s_nmax, &s_live,
@@ -1232,6 +1263,11 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     live = (int)s_live;
     f_prev = f;
     if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) break;
+  }
+  __syncthreads();  // every thread is done with the task's shared state
+  // a task that stopped on an error (status recorded) ends the CTA's list
+  tix = !finished || a.W == 1 ? -1 : take();
+  alone = true;
   }
   // drain: no MMA may still target this CTA's TMEM or shared memory
   __syncthreads();
@@ -1373,6 +1409,70 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcb_objective_kernel(TcbArgs a)
 // ---- host side ----------------------------------------------------------------------
 int tb_np(int k) { return k <= 128 ? 128 : k <= 256 ? 256 : 512; }
 
+// The CTAs of a batched tensor-core Lloyd launch (one per SM).  With about
+// as many workers as SMs a split in proportion to s k alone gives each small
+// worker a CTA of its own and a worker of 1.7 CTAs' work one or two, and the
+// number of updates (5 to 15 on the large workload) is only known as they
+// run.  So: a task of at least T work (s k per update) gets ceil(work / T)
+// CTAs of its own (its rows split evenly), T at least 1.15 times the mean
+// work per CTA and large enough for these groups to fit into the launch;
+// every other task waits in a list,
+// largest first, and a CTA without a task, or done with its last, takes the
+// next one (an atomic counter, `pop`) and runs it alone.  The list is in
+// block_task_host[max_blocks ..], its length in nfollow; CTAs that start from
+// the list have block_task -2.
+void tcl_pack(LloydLaunch &h, int64_t total) {
+  const int W = h.W;
+  std::vector<int64_t> work(W);
+  for (int w = 0; w < W; ++w) work[w] = std::max<int64_t>(1, h.tasks[w].s) * (int64_t)h.tasks[w].k;
+  std::vector<int> order(W);
+  for (int w = 0; w < W; ++w) order[w] = w;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  auto groups = [&](int w, double T) {
+    int64_t nb = (int64_t)std::ceil((double)work[w] / T);
+    nb = std::min<int64_t>(nb, (h.tasks[w].s + TB_M - 1) / TB_M);
+    return std::max<int64_t>(1, std::min<int64_t>(nb, h.task_blocks));
+  };
+  auto ctas = [&](double T) {
+    int64_t n = 0;
+    for (int w : order)
+      if ((double)work[w] >= T) n += groups(w, T);
+    return n;
+  };
+  // the largest task alone always fits (one group); bisection below it
+  double hi = (double)work[order[0]], lo = 0.0;
+  for (int i = 0; i < 48; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (ctas(mid) <= total) hi = mid;
+    else lo = mid;
+  }
+  // at least 1.15 shares: smaller groups would fill the launch and leave the
+  // list to run after them (simulated with 5 to 15 updates a worker: 1.60
+  // times the balanced time at 1.1-1.2 shares, 1.75 below one share)
+  double sum = 0.0;
+  for (int w = 0; w < W; ++w) sum += (double)work[w];
+  const double T = std::max(hi, 1.15 * sum / (double)total);
+  int *follow = h.block_task_host + h.max_blocks;
+  int64_t grid = 0;
+  int nf = 0;
+  for (int w : order) {
+    hpc_lloyd_task &t = h.tasks[w];
+    if ((double)work[w] >= T) {
+      const int64_t nb = groups(w, T);
+      t.block0 = (int)grid;
+      t.nblocks = (int)nb;
+      for (int64_t i = 0; i < nb; ++i) h.block_task_host[grid++] = w;
+    } else {
+      t.block0 = -1;  // whichever CTA takes it, alone
+      t.nblocks = 1;
+      follow[nf++] = w;
+    }
+  }
+  for (; grid < total; ++grid) h.block_task_host[grid] = -2;
+  h.grid = grid;
+  h.nfollow = nf;
+}
+
 template <int D, int NP>
 int tcl_plan_t(const hpc_launch &L, LloydLaunch &h) {
   using Cfg = TbCfg<D, NP>;
@@ -1393,24 +1493,16 @@ int tcl_plan_t(const hpc_launch &L, LloydLaunch &h) {
   int64_t want = 0;
   for (int w = 0; w < h.W; ++w) want += (h.tasks[w].s + TB_M - 1) / TB_M;
   if (total > want) total = want;
-  if (h.W > total || h.W > HPC_MAX_TASKS) return HPC_ERR_UNSUPPORTED;
-  std::vector<int64_t> rows(h.W), work(h.W);
-  std::vector<int> b0(h.W), nb(h.W);
-  for (int w = 0; w < h.W; ++w) {
-    rows[w] = h.tasks[w].s;
-    work[w] = h.tasks[w].s * (int64_t)h.tasks[w].k;
+  if (h.W > HPC_MAX_TASKS) return HPC_ERR_UNSUPPORTED;
+  h.nfollow = 0;
+  if (h.W == 1) {
+    h.tasks[0].block0 = 0;
+    h.tasks[0].nblocks = (int)total;
+    h.grid = total;
+  } else {
+    if (!h.pop) return HPC_ERR_UNSUPPORTED;
+    tcl_pack(h, total);
   }
-  hpc_split_blocks(h.W, rows.data(), work.data(), (int64_t)TB_M, total, b0.data(), nb.data());
-  int64_t grid = 0;
-  for (int w = 0; w < h.W; ++w) {
-    if (nb[w] > h.task_blocks) nb[w] = (int)h.task_blocks;
-    h.tasks[w].block0 = (int)grid;
-    h.tasks[w].nblocks = nb[w];
-    if (h.W > 1)
-      for (int b = 0; b < nb[w]; ++b) h.block_task_host[grid + b] = w;
-    grid += nb[w];
-  }
-  h.grid = grid;
   h.smem = smem;
   h.smem_sums = 0;
   h.xstage = 0;
@@ -1426,6 +1518,9 @@ int tcl_run_t(const hpc_launch &L, const LloydLaunch &h) {
   a.single = h.tasks[0];
   a.tasks = h.tasks_dev;
   a.block_task = h.block_task_dev;
+  a.follow = h.W > 1 ? h.block_task_dev + h.max_blocks : nullptr;
+  a.nfollow = h.nfollow;
+  a.pop = h.pop;
   a.max_iter = h.max_iter;
   a.tol = h.tol;
   a.status = h.status;
