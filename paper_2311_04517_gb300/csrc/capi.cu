@@ -506,7 +506,7 @@ static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, i
   *tab_bytes = pad256((size_t)W * sizeof(hpc_sample_task)) + pad256((size_t)W * sizeof(hpc_round_worker)) +
                pad256((size_t)W * sizeof(hpc_kpp_task)) + pad256((size_t)W * sizeof(hpc_lloyd_task)) +
                3 * (size_t)nchunks * pad256((size_t)c->grid_bound * 4);
-  return need + pad256((size_t)W * 8) + pad256((size_t)W * 4) + *tab_bytes + 1024;
+  return need + pad256((size_t)W * 8) + 2 * pad256((size_t)W * 4) + *tab_bytes + 1024;
 }
 
 // Carves the round's scratch from cv, writes the descriptor tables into
@@ -523,6 +523,9 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
   TaskHeader *hdr = cv.take<TaskHeader>((size_t)W);
   double *fw = cv.take<double>((size_t)W);
   int32_t *itw = cv.take<int32_t>((size_t)W);
+  // each worker's updates in its latest run: the same place every round
+  // (the layout is the same), read by the next round's Lloyd plan
+  int32_t *uprev = cv.take<int32_t>((size_t)W);
   Carver th{tab_host, 0, tab_bytes}, td{tab_dev, 0, tab_bytes};
   hpc_sample_task *st_h = th.take<hpc_sample_task>((size_t)W);
   hpc_sample_task *st_d = td.take<hpc_sample_task>((size_t)W);
@@ -566,6 +569,7 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
     lt.deg_inc = b->degenerate + b->K_off[w];
     lt.f_new = b->f_new ? b->f_new + w : nullptr;
     lt.iters_rep = b->iters ? b->iters + w : nullptr;
+    lt.uprev = uprev + w;
     lt.accepted = b->accepted ? b->accepted + w : nullptr;
     lt.t_done = b->t_done ? reinterpret_cast<unsigned long long *>(b->t_done) + w : nullptr;
   }
@@ -701,7 +705,8 @@ static int round_enqueue(hpc_ctx *c, const hpc_round_plan &p, uint32_t *round_de
     if (int rc = hpc_lloyd_run(c->L, lh)) return plan_fail(c, rc, "lloyd launch");
     if (timed)
       if (int rc = timing_mark(c, ev++, 2)) return rc;
-    c->launches += 2 + (kh.W > 1 && kh.W <= HPC_KPP_SPLIT_MAX ? 1 : 0);
+    c->launches += 2 + (kh.W > 1 && kh.W <= HPC_KPP_SPLIT_MAX ? 1 : 0) +
+                   (lh.W > 1 && lh.form == HPC_SEARCH_SPLIT_BF16 ? 1 : 0);
   }
   return HPC_OK;
 }

@@ -80,6 +80,7 @@ __device__ __forceinline__ void hpc_incumbent_block(const hpc_lloyd_task &tk, in
     if (acc) *tk.fhat = f / (double)tk.s;
     if (tk.f_new) *tk.f_new = f;
     if (tk.iters_rep) *tk.iters_rep = iters;
+    if (tk.uprev) *tk.uprev = iters;
     if (tk.accepted) *tk.accepted = acc ? 1 : 0;
     // when this worker's run ended (Section 6.4's baseline convergence time
     // is the time until any worker reaches a given sample objective)

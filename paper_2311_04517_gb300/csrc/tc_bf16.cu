@@ -1001,7 +1001,7 @@ struct TclArgs {
   const hpc_lloyd_task *tasks;
   const int *block_task;   // W > 1: each CTA's first task (-2: take one from the list)
   const int *follow;       // W > 1: the tasks CTAs take as they become free, largest first
-  int nfollow;
+  const int *nfollow;      // W > 1: their number (device)
   unsigned *pop;           // W > 1: the list's next entry (zero at launch)
   int max_iter;
   double tol;
@@ -1048,7 +1048,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   auto take = [&]() {
     if (threadIdx.x == 0) {
       const unsigned i = atomicAdd(a.pop, 1u);
-      s_qn = i < (unsigned)a.nfollow ? a.follow[i] : -1;
+      s_qn = i < (unsigned)*a.nfollow ? a.follow[i] : -1;
     }
     __syncthreads();
     const int t = s_qn;
@@ -1412,65 +1412,126 @@ int tb_np(int k) { return k <= 128 ? 128 : k <= 256 ? 256 : 512; }
 // The CTAs of a batched tensor-core Lloyd launch (one per SM).  With about
 // as many workers as SMs a split in proportion to s k alone gives each small
 // worker a CTA of its own and a worker of 1.7 CTAs' work one or two, and the
-// number of updates (5 to 15 on the large workload) is only known as they
-// run.  So: a task of at least T work (s k per update) gets ceil(work / T)
-// CTAs of its own (its rows split evenly), T at least 1.15 times the mean
-// work per CTA and large enough for these groups to fit into the launch;
-// every other task waits in a list,
-// largest first, and a CTA without a task, or done with its last, takes the
-// next one (an atomic counter, `pop`) and runs it alone.  The list is in
-// block_task_host[max_blocks ..], its length in nfollow; CTAs that start from
-// the list have block_task -2.
-void tcl_pack(LloydLaunch &h, int64_t total) {
-  const int W = h.W;
-  std::vector<int64_t> work(W);
-  for (int w = 0; w < W; ++w) work[w] = std::max<int64_t>(1, h.tasks[w].s) * (int64_t)h.tasks[w].k;
-  std::vector<int> order(W);
-  for (int w = 0; w < W; ++w) order[w] = w;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
-  auto groups = [&](int w, double T) {
-    int64_t nb = (int64_t)std::ceil((double)work[w] / T);
-    nb = std::min<int64_t>(nb, (h.tasks[w].s + TB_M - 1) / TB_M);
-    return std::max<int64_t>(1, std::min<int64_t>(nb, h.task_blocks));
-  };
-  auto ctas = [&](double T) {
-    int64_t n = 0;
-    for (int w : order)
-      if ((double)work[w] >= T) n += groups(w, T);
-    return n;
-  };
-  // the largest task alone always fits (one group); bisection below it
-  double hi = (double)work[order[0]], lo = 0.0;
-  for (int i = 0; i < 48; ++i) {
-    const double mid = 0.5 * (lo + hi);
-    if (ctas(mid) <= total) hi = mid;
-    else lo = mid;
+// number of updates (5 to 15 on the large workload; fewer for larger
+// samples) is only known as they run.  So the work of a task is s k (u + 1),
+// u its updates in its previous run (0 before the first): a task of at least
+// M = 0.85 times the mean work per CTA gets round(work / M) CTAs of its own
+// (its rows split evenly; fewer while the launch has too few); every other
+// task waits in a list, largest first, and a CTA without a task, or done with
+// its last, takes the next one (an atomic counter) and runs it alone.
+// (Simulated with update counts like the large workload's: 1.52 times the
+// balanced time, against 1.81 for groups of ceil(work / 1.15 mean) CTAs;
+// whole CTAs per task bound it.)  Computed by one thread, on the host for the
+// plan and on the device before every launch (the previous run's updates
+// are there).
+// Writes block_task[0, total) (a task, or -2: start from the list),
+// follow[0, nf), nb[] and b0[] per task; returns nf.
+constexpr int TCL_PACK_MAX = 128;  // workers of one launch (a round's chunk)
+
+__host__ __device__ int tcl_pack_core(int W, const double *work, const int64_t *cap, int64_t total,
+                                      int *block_task, int *follow, int *nb, int *b0) {
+  int order[TCL_PACK_MAX];
+  for (int w = 0; w < W; ++w) {  // largest first, lower index on ties (insertion)
+    int i = w;
+    while (i > 0 && work[order[i - 1]] < work[w]) {
+      order[i] = order[i - 1];
+      --i;
+    }
+    order[i] = w;
   }
-  // at least 1.15 shares: smaller groups would fill the launch and leave the
-  // list to run after them (simulated with 5 to 15 updates a worker: 1.60
-  // times the balanced time at 1.1-1.2 shares, 1.75 below one share)
   double sum = 0.0;
-  for (int w = 0; w < W; ++w) sum += (double)work[w];
-  const double T = std::max(hi, 1.15 * sum / (double)total);
-  int *follow = h.block_task_host + h.max_blocks;
+  for (int w = 0; w < W; ++w) sum += work[w];
+  // groups for the tasks of at least M = 0.85 times the mean work per CTA,
+  // round(work / M) CTAs each; while they are more than the launch has, the
+  // group with the least work per CTA gives one up
+  const double M = 0.85 * sum / (double)total;
+  int64_t used = 0;
+  for (int j = 0; j < W; ++j) {
+    const int w = order[j];
+    if (work[w] >= M) {
+      int64_t n = (int64_t)floor(work[w] / M + 0.5);
+      n = n < cap[w] ? n : cap[w];
+      nb[w] = (int)(n < 1 ? 1 : n);
+      used += nb[w];
+    } else {
+      nb[w] = 0;
+    }
+  }
+  while (used > total) {
+    int best = -1;
+    for (int j = 0; j < W; ++j) {
+      const int w = order[j];
+      if (nb[w] > 1 && (best < 0 || work[w] / nb[w] < work[best] / nb[best])) best = w;
+    }
+    if (best < 0) {  // one CTA each and still too many: the smallest groups join the list
+      for (int j = W - 1; j >= 0 && used > total; --j)
+        if (nb[order[j]] == 1) {
+          nb[order[j]] = 0;
+          --used;
+        }
+      break;
+    }
+    --nb[best];
+    --used;
+  }
   int64_t grid = 0;
   int nf = 0;
-  for (int w : order) {
-    hpc_lloyd_task &t = h.tasks[w];
-    if ((double)work[w] >= T) {
-      const int64_t nb = groups(w, T);
-      t.block0 = (int)grid;
-      t.nblocks = (int)nb;
-      for (int64_t i = 0; i < nb; ++i) h.block_task_host[grid++] = w;
+  for (int j = 0; j < W; ++j) {
+    const int w = order[j];
+    if (nb[w] > 0) {
+      b0[w] = (int)grid;
+      for (int i = 0; i < nb[w]; ++i) block_task[grid++] = w;
     } else {
-      t.block0 = -1;  // whichever CTA takes it, alone
-      t.nblocks = 1;
+      nb[w] = 1;
+      b0[w] = -1;  // whichever CTA takes it, alone
       follow[nf++] = w;
     }
   }
-  for (; grid < total; ++grid) h.block_task_host[grid] = -2;
-  h.grid = grid;
-  h.nfollow = nf;
+  for (; grid < total; ++grid) block_task[grid] = -2;
+  return nf;
+}
+
+// The device side: the tasks' work from the previous round's updates, the
+// plan written into the launch's tables (block_task, the list and its length
+// in block_task[2 max_blocks - 1], the tasks' groups).
+__global__ void tcl_repack_kernel(hpc_lloyd_task *tasks, int *block_task, int W, int64_t total,
+                                  int64_t max_blocks, int64_t task_blocks) {
+  if (threadIdx.x != 0) return;
+  double work[TCL_PACK_MAX];
+  int64_t cap[TCL_PACK_MAX];
+  int nb[TCL_PACK_MAX], b0[TCL_PACK_MAX];
+  for (int w = 0; w < W; ++w) {
+    const int64_t sw = tasks[w].s > 0 ? tasks[w].s : 1;
+    const int u = tasks[w].uprev ? *tasks[w].uprev : 0;
+    work[w] = (double)sw * (double)tasks[w].k * (double)((u > 0 ? (u < 1000 ? u : 1000) : 0) + 1);
+    const int64_t c = (sw + TB_M - 1) / TB_M;
+    cap[w] = c < task_blocks ? c : task_blocks;
+  }
+  const int nf = tcl_pack_core(W, work, cap, total, block_task, block_task + max_blocks, nb, b0);
+  block_task[2 * max_blocks - 1] = nf;
+  for (int w = 0; w < W; ++w) {
+    tasks[w].block0 = b0[w];
+    tasks[w].nblocks = nb[w];
+  }
+}
+
+void tcl_pack(LloydLaunch &h, int64_t total) {
+  double work[TCL_PACK_MAX];
+  int64_t cap[TCL_PACK_MAX];
+  int nb[TCL_PACK_MAX], b0[TCL_PACK_MAX];
+  for (int w = 0; w < h.W; ++w) {
+    const int64_t sw = std::max<int64_t>(1, h.tasks[w].s);
+    work[w] = (double)sw * (double)h.tasks[w].k;
+    cap[w] = std::min<int64_t>((sw + TB_M - 1) / TB_M, h.task_blocks);
+  }
+  h.nfollow = tcl_pack_core(h.W, work, cap, total, h.block_task_host, h.block_task_host + h.max_blocks,
+                            nb, b0);
+  h.block_task_host[2 * h.max_blocks - 1] = h.nfollow;
+  for (int w = 0; w < h.W; ++w) {
+    h.tasks[w].block0 = b0[w];
+    h.tasks[w].nblocks = nb[w];
+  }
+  h.grid = total;
 }
 
 template <int D, int NP>
@@ -1500,7 +1561,7 @@ int tcl_plan_t(const hpc_launch &L, LloydLaunch &h) {
     h.tasks[0].nblocks = (int)total;
     h.grid = total;
   } else {
-    if (!h.pop) return HPC_ERR_UNSUPPORTED;
+    if (!h.pop || h.W > TCL_PACK_MAX || h.max_blocks < TCL_PACK_MAX + 2) return HPC_ERR_UNSUPPORTED;
     tcl_pack(h, total);
   }
   h.smem = smem;
@@ -1519,8 +1580,14 @@ int tcl_run_t(const hpc_launch &L, const LloydLaunch &h) {
   a.tasks = h.tasks_dev;
   a.block_task = h.block_task_dev;
   a.follow = h.W > 1 ? h.block_task_dev + h.max_blocks : nullptr;
-  a.nfollow = h.nfollow;
+  a.nfollow = h.W > 1 ? h.block_task_dev + 2 * h.max_blocks - 1 : nullptr;
   a.pop = h.pop;
+  if (h.W > 1) {  // the plan for this round, from the previous round's updates
+    tcl_repack_kernel<<<1, 32, 0, L.stream>>>(const_cast<hpc_lloyd_task *>(h.tasks_dev),
+                                              const_cast<int *>(h.block_task_dev), h.W, h.grid,
+                                              h.max_blocks, h.task_blocks);
+    if (cudaGetLastError() != cudaSuccess) return HPC_ERR_CUDA;
+  }
   a.max_iter = h.max_iter;
   a.tol = h.tol;
   a.status = h.status;
