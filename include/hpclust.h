@@ -174,6 +174,26 @@ int hpc_autotune_objective(hpc_ctx *ctx, const float *X, int64_t n, int32_t d, c
 int hpc_lloyd_schedule(hpc_ctx *ctx, int64_t s, int32_t d, int32_t k, int32_t *out,
                        int32_t nout);
 
+/* The CTA plan of a batched split-BF16 Lloyd launch (the paper has no
+ * counterpart: the spread of Algorithm 3-5's workers over the GPU).  Host
+ * only (no context, no device): what the launch's one-thread planner
+ * computes before every launch of a round, from each worker's sample size
+ * s[w], centroid count k[w] and updates in its previous run u[w] (host
+ * arrays of W <= 128; negative u counts as 0, u above 1000 as 1000).  The
+ * work of worker w is s k (u + 1); workers of at least 0.85 times the mean
+ * work per CTA get groups of round(work / (0.85 mean)) CTAs of their own
+ * (at most one per 128 rows; while the groups need more than `ctas`, the
+ * group with the least work per CTA gives one up), the others wait in a
+ * list, largest first, from which CTAs take one as they become free.
+ * Output (host): cta_task[ctas] the worker each CTA starts with (-2: it
+ * takes from the list), list[W] the list (its length returned through
+ * *nlist), nblocks[W] each worker's CTAs (1 for listed workers).
+ * Errors: HPC_ERR_ARG (W outside 1..128, ctas < 1, a NULL array, s < 1 or
+ * k < 1). */
+int hpc_lloyd_cta_plan(int32_t W, const int64_t *s, const int32_t *k, const int32_t *u,
+                       int32_t ctas, int32_t *cta_task, int32_t *list, int32_t *nlist,
+                       int32_t *nblocks);
+
 /* Per-phase timing of rounds (the paper has no counterpart: measurement
  * only).  With timing on, every round enqueued on the context (hpc_round,
  * hpc_round_enqueue) records CUDA events on the context's stream around

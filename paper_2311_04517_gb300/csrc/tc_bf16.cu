@@ -1428,6 +1428,12 @@ int tb_np(int k) { return k <= 128 ? 128 : k <= 256 ? 256 : 512; }
 // follow[0, nf), nb[] and b0[] per task; returns nf.
 constexpr int TCL_PACK_MAX = 128;  // workers of one launch (a round's chunk)
 
+// a task's work: s k (u + 1), u its updates in the previous run (clamped)
+__host__ __device__ inline double tcl_work(int64_t s, int k, int u) {
+  const int uc = u > 0 ? (u < 1000 ? u : 1000) : 0;
+  return (double)(s > 0 ? s : 1) * (double)k * (double)(uc + 1);
+}
+
 __host__ __device__ int tcl_pack_core(int W, const double *work, const int64_t *cap, int64_t total,
                                       int *block_task, int *follow, int *nb, int *b0) {
   int order[TCL_PACK_MAX];
@@ -1502,8 +1508,7 @@ __global__ void tcl_repack_kernel(hpc_lloyd_task *tasks, int *block_task, int W,
   int nb[TCL_PACK_MAX], b0[TCL_PACK_MAX];
   for (int w = 0; w < W; ++w) {
     const int64_t sw = tasks[w].s > 0 ? tasks[w].s : 1;
-    const int u = tasks[w].uprev ? *tasks[w].uprev : 0;
-    work[w] = (double)sw * (double)tasks[w].k * (double)((u > 0 ? (u < 1000 ? u : 1000) : 0) + 1);
+    work[w] = tcl_work(sw, tasks[w].k, tasks[w].uprev ? *tasks[w].uprev : 0);
     const int64_t c = (sw + TB_M - 1) / TB_M;
     cap[w] = c < task_blocks ? c : task_blocks;
   }
@@ -1521,7 +1526,7 @@ void tcl_pack(LloydLaunch &h, int64_t total) {
   int nb[TCL_PACK_MAX], b0[TCL_PACK_MAX];
   for (int w = 0; w < h.W; ++w) {
     const int64_t sw = std::max<int64_t>(1, h.tasks[w].s);
-    work[w] = (double)sw * (double)h.tasks[w].k;
+    work[w] = tcl_work(sw, h.tasks[w].k, 0);
     cap[w] = std::min<int64_t>((sw + TB_M - 1) / TB_M, h.task_blocks);
   }
   h.nfollow = tcl_pack_core(h.W, work, cap, total, h.block_task_host, h.block_task_host + h.max_blocks,
@@ -1659,6 +1664,21 @@ size_t hpc_tcl_gcent_bytes(int d, int k) {
   const int kp = (k + 1) & ~1;
   const int D = d <= 64 ? 64 : 128;
   return (((size_t)kp * hpc_cstride(D) * 4 + (size_t)kp * 8) + 255) & ~(size_t)255;
+}
+
+int hpc_tcl_cta_plan(int W, const int64_t *s, const int32_t *k, const int32_t *u, int64_t ctas,
+                     int32_t *cta_task, int32_t *list, int32_t *nlist, int32_t *nblocks) {
+  if (W < 1 || W > TCL_PACK_MAX || ctas < 1) return HPC_ERR_ARG;
+  double work[TCL_PACK_MAX];
+  int64_t cap[TCL_PACK_MAX];
+  int b0[TCL_PACK_MAX];
+  for (int w = 0; w < W; ++w) {
+    if (s[w] < 1 || k[w] < 1) return HPC_ERR_ARG;
+    work[w] = tcl_work(s[w], k[w], u ? u[w] : 0);
+    cap[w] = (s[w] + TB_M - 1) / TB_M;
+  }
+  *nlist = tcl_pack_core(W, work, cap, ctas, cta_task, list, nblocks, b0);
+  return HPC_OK;
 }
 
 int hpc_tcl_plan(const hpc_launch &L, LloydLaunch &h) {
