@@ -865,42 +865,75 @@ def run_mine(args):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        # Each step copies X in row chunks; the objective of the current best
-        # incumbents runs on every chunk as soon as it has arrived (it is a sum
-        # over rows), behind the copy; the round then runs on the complete X.
-        # Work per step: one full copy, one full objective per group, one round.
+        # Each step copies its X in row chunks; the objective of the current
+        # best incumbents runs on every chunk as soon as it has arrived (it is
+        # a sum over rows); the round then runs on the complete X.  With room
+        # for a second copy of X on the device, the copies alternate between
+        # two buffers and step i + 1's copy runs during step i's work (its
+        # buffer is free once step i - 1's round is done); otherwise a step's
+        # copy waits for the previous step.  Work per step: one full copy,
+        # one full objective per group, one round.
         nck = 8
         rows = (wl.n + nck - 1) // nck
         rows = (rows + 3) // 4 * 4                      # 16-byte aligned chunk starts
+        bufs = [X]
+        free_b, _ = torch.cuda.mem_get_info(dev)
+        if free_b > X.numel() * 4 + (8 << 30):
+            bufs.append(torch.empty_like(X))
+        nb = len(bufs)
         f_chunks = torch.zeros((len(groups), nck), dtype=torch.float64, device=dev)
         main = torch.cuda.current_stream(dev)
         copy_stream = torch.cuda.Stream(dev)
-        arrived = [torch.cuda.Event() for _ in range(nck)]
-        for i in range(E):
-            cb = best_centroids()
-            e_best.append([kb for kb, _, _ in cb])
-            f_chunks.zero_()
-            copy_stream.wait_stream(main)               # X is free once the last step is done
+        arrived = [[torch.cuda.Event() for _ in range(nck)] for _ in range(nb)]
+        freed = [torch.cuda.Event() for _ in range(nb)]
+
+        def issue_copy(i):
+            bi = i % nb
+            if nb == 1:
+                copy_stream.wait_stream(main)           # X is free once the last step is done
+            else:
+                copy_stream.wait_event(freed[bi])       # the last round on this buffer is done
             with torch.cuda.stream(copy_stream):
                 for c in range(nck):
                     a, b_ = c * rows, min(wl.n, (c + 1) * rows)
                     if a < b_:
-                        X[a:b_].copy_(X_host[a:b_], non_blocking=True)
-                    arrived[c].record(copy_stream)
+                        bufs[bi][a:b_].copy_(X_host[a:b_], non_blocking=True)
+                    arrived[bi][c].record(copy_stream)
+
+        def round_on(buf, r):
+            if nb == 1:
+                run_round(r)
+            elif shared:
+                job.b.X = buf
+                job.round(strategy, seed, r, ranges, n_competitive=n_comp(args))
+            else:
+                H.hpc_round(ctx, buf, batch, strategy, seed, r)
+
+        issue_copy(0)
+        for i in range(E):
+            if nb == 2 and i + 1 < E:
+                issue_copy(i + 1)
+            bi = i % nb
+            cb = best_centroids()
+            e_best.append([kb for kb, _, _ in cb])
+            f_chunks.zero_()
             for c in range(nck):
                 # the chunk's rows within this rank's block of the objective
                 a, b_ = max(ra, c * rows), min(rb, (c + 1) * rows)
-                main.wait_event(arrived[c])
+                main.wait_event(arrived[bi][c])
                 if a >= b_:
                     continue
                 for gi, (kb, C, deg) in enumerate(cb):
-                    H.hpc_objective(ctx, X[a:b_], C, deg, f_out=f_chunks[gi, c:c + 1])
-            run_round(r0 + i)
+                    H.hpc_objective(ctx, bufs[bi][a:b_], C, deg, f_out=f_chunks[gi, c:c + 1])
+            round_on(bufs[bi], r0 + i)
+            freed[bi].record(main)
             e_iters[i].copy_(batch.iters, non_blocking=True)
             # per-chunk objectives are read back and added on the host
             res_host[:len(groups) * nck].copy_(f_chunks.view(-1), non_blocking=True)
             res_host[len(groups) * nck:].copy_(batch.fhat, non_blocking=True)
             C_host.copy_(batch.C, non_blocking=True)
+            if nb == 1 and i + 1 < E:
+                issue_copy(i + 1)
         e1.record()
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1)
@@ -908,11 +941,13 @@ def run_mine(args):
         e_dist = sum(dist_count(ei[i], ws.s[lw], ws.k[lw], rb - ra, e_best[i]) for i in range(E))
         e_ms, e_dist = job_totals(e_ms, e_dist, dev)
         e_value = e_dist / (e_ms / 1e3)
-        e2e = {"value": e_value, "unit": UNIT,
+        if shared:
+            job.b.X = X
+        e2e = {"value": e_value, "unit": UNIT, "device_buffers": nb,
                "h2d_bytes_per_step": int(X_host.numel() * 4),
                "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4 +
                                          (Wl * 8 if wl.W > 1 else 0))}
-        del X_host
+        del X_host, bufs
 
     hbm, src = peaks()
     obj_avg_ms = float(np.mean(obj_ms)) / len(groups)  # one launch per group per step
