@@ -862,9 +862,7 @@ def run_mine(args):
         e_iters = torch.zeros((E, Wl), dtype=torch.int32, device=dev)
         e_best = []
         r0 = Wm + K + Wm_extra
-        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
         # Each step copies its X in row chunks; the objective of the current
         # best incumbents runs on every chunk as soon as it has arrived (it is
         # a sum over rows); the round then runs on the complete X.  With room
@@ -909,13 +907,20 @@ def run_mine(args):
             else:
                 H.hpc_round(ctx, buf, batch, strategy, seed, r)
 
-        issue_copy(0)
-        for i in range(E):
-            if nb == 2 and i + 1 < E:
-                issue_copy(i + 1)
+        def e2e_steps(n_steps, r_first, timed):
+            issue_copy(0)
+            for i in range(n_steps):
+                if nb == 2 and i + 1 < n_steps:
+                    issue_copy(i + 1)
+                e2e_step(i, r_first + i, timed)
+                if nb == 1 and i + 1 < n_steps:
+                    issue_copy(i + 1)
+
+        def e2e_step(i, r, timed):
             bi = i % nb
             cb = best_centroids()
-            e_best.append([kb for kb, _, _ in cb])
+            if timed:
+                e_best.append([kb for kb, _, _ in cb])
             f_chunks.zero_()
             for c in range(nck):
                 # the chunk's rows within this rank's block of the objective
@@ -925,15 +930,22 @@ def run_mine(args):
                     continue
                 for gi, (kb, C, deg) in enumerate(cb):
                     H.hpc_objective(ctx, bufs[bi][a:b_], C, deg, f_out=f_chunks[gi, c:c + 1])
-            round_on(bufs[bi], r0 + i)
+            round_on(bufs[bi], r)
             freed[bi].record(main)
-            e_iters[i].copy_(batch.iters, non_blocking=True)
+            if timed:
+                e_iters[i].copy_(batch.iters, non_blocking=True)
             # per-chunk objectives are read back and added on the host
             res_host[:len(groups) * nck].copy_(f_chunks.view(-1), non_blocking=True)
             res_host[len(groups) * nck:].copy_(batch.fhat, non_blocking=True)
             C_host.copy_(batch.C, non_blocking=True)
-            if nb == 1 and i + 1 < E:
-                issue_copy(i + 1)
+
+        # one untimed step first: the call path's first use on this context
+        # sets up its scratch and pinned staging (the timed steps above ran
+        # the recorded graph)
+        e2e_steps(1, r0, False)
+        torch.cuda.synchronize()
+        e0.record()
+        e2e_steps(E, r0 + 1, True)
         e1.record()
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1)
@@ -1015,9 +1027,9 @@ def run_mine(args):
     ctx.set_search_stats(True)
     ctx.search_stats(reset=True)
     if shared:
-        run_round(Wm + K + Wm_extra + (E or 0))
+        run_round(Wm + K + Wm_extra + (E + 1 if E > 0 else 0))
     else:
-        H.hpc_round(ctx, X, batch, strategy, seed, Wm + K + Wm_extra + (E or 0))
+        H.hpc_round(ctx, X, batch, strategy, seed, Wm + K + Wm_extra + (E + 1 if E > 0 else 0))
     for kb, Cb, db in best_centroids():
         H.hpc_objective(ctx, Xo, Cb, db)
     line["search_stats_one_step"] = ctx.search_stats(reset=True)

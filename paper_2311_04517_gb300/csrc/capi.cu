@@ -46,6 +46,7 @@ struct hpc_ctx {
   // pinned staging ring for the per-round descriptor tables: slot i is
   // rewritten only after the copy issued from it last time has run
   void *stage_host[4];
+  void *stage_dev[4];  // the same pinned slot, mapped into the device's address space
   size_t stage_bytes[4];
   cudaEvent_t stage_ev[4];
   bool stage_used[4];
@@ -399,8 +400,23 @@ __global__ void selftest_timeout_kernel(hpc_gridbar *bar, int *status, uint64_t 
   hpc_grid_sync(bar, status, 2u, limit_ns);
 }
 
+// Round set-up on the device: the round's tables are read from the pinned
+// staging slot (mapped into the device's address space, loads that bypass
+// the caches) and the task headers are cleared.  One kernel instead of a
+// host-to-device copy and a memset keeps the round's stream off the copy
+// engines, where a large copy issued on another stream (the next batch of
+// data) would hold the round back until it has finished.
+__global__ void round_setup_kernel(uint4 *tab, const uint4 *src, size_t n16, uint4 *hdr,
+                                   size_t hdr16) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
+    tab[i] = __ldcv(src + i);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < hdr16; i += stride)
+    hdr[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Pinned host slot `slot` of the staging ring, at least `bytes` long; waits
-// for the copy issued from it last time.
+// for the launch that read it last time.
 int stage_acquire(hpc_ctx *c, int slot, size_t bytes, char **out) {
   cudaError_t e;
   if (c->stage_used[slot]) {
@@ -411,12 +427,20 @@ int stage_acquire(hpc_ctx *c, int slot, size_t bytes, char **out) {
   if (c->stage_bytes[slot] < bytes) {
     if (c->stage_host[slot]) cudaFreeHost(c->stage_host[slot]);
     c->stage_host[slot] = nullptr;
+    c->stage_dev[slot] = nullptr;
     c->stage_bytes[slot] = 0;
     const size_t want = std::max(bytes, (size_t)1 << 16);
-    if ((e = cudaHostAlloc(&c->stage_host[slot], want, cudaHostAllocDefault)) != cudaSuccess) {
+    if ((e = cudaHostAlloc(&c->stage_host[slot], want, cudaHostAllocMapped)) != cudaSuccess) {
       cudaGetLastError();
       c->stage_host[slot] = nullptr;
       return fail(c, HPC_ERR_NOMEM, "pinned staging allocation failed");
+    }
+    if ((e = cudaHostGetDevicePointer(&c->stage_dev[slot], c->stage_host[slot], 0)) !=
+        cudaSuccess) {
+      cudaFreeHost(c->stage_host[slot]);
+      c->stage_host[slot] = nullptr;
+      c->stage_dev[slot] = nullptr;
+      return cuda_fail(c, e, "staging device pointer");
     }
     c->stage_bytes[slot] = want;
   }
@@ -665,14 +689,28 @@ static int timing_mark(hpc_ctx *c, int i, int kind) {
   return HPC_OK;
 }
 
-static int round_enqueue(hpc_ctx *c, const hpc_round_plan &p, uint32_t *round_dev, uint32_t round) {
+// Enqueues a built round.  `tab_src` (device-visible pinned memory,
+// `tab_bytes` long, a multiple of 16) holds the tables that the set-up
+// kernel copies to `tab_dev`; null when they are already there.
+static int round_enqueue(hpc_ctx *c, const hpc_round_plan &p, uint32_t *round_dev, uint32_t round,
+                         char *tab_dev, const char *tab_src, size_t tab_bytes) {
   const bool timed = c->timing && 2 + 2 * (int)p.kl.size() <= HPC_TIMING_EVENTS;
   int ev = 0;
   c->tev_n = 0;
   if (timed)
     if (int rc = timing_mark(c, ev++, -1)) return rc;
-  cudaError_t e = cudaMemsetAsync(p.hdr, 0, (size_t)p.W * sizeof(TaskHeader), c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "round set-up");
+  {
+    const size_t n16 = tab_src ? tab_bytes / 16 : 0;
+    const size_t hdr16 = (size_t)p.W * sizeof(TaskHeader) / 16;
+    const size_t units = std::max(n16, hdr16);
+    const int blocks = (int)std::min<size_t>((size_t)c->L.num_sms, (units + 1023) / 1024 + 1);
+    round_setup_kernel<<<blocks, 256, 0, c->stream>>>(
+        reinterpret_cast<uint4 *>(tab_dev), reinterpret_cast<const uint4 *>(tab_src), n16,
+        reinterpret_cast<uint4 *>(p.hdr), hdr16);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "round set-up");
+    c->launches += 1;
+  }
   hpc_base_args base{};
   base.wk = p.rw_d;
   base.W = p.W;
@@ -1458,11 +1496,11 @@ int hpc_round(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch 
   if (int rc = round_build(c, X, n, d, b, strategy, seed, round, max_iter, rel_tol, n_candidates,
                            cv, tab_host, tab_dev, tab_bytes, p, mode))
     return rc;
-  // one table copy from the pinned staging slot, then the launches
-  cudaError_t e = cudaMemcpyAsync(tab_dev, tab_host, tab_bytes, cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "round tables");
-  if (int rc = stage_release(c, slot)) return rc;
-  return round_enqueue(c, p, nullptr, round);
+  // the set-up launch reads the tables from the pinned staging slot
+  const int rc = round_enqueue(c, p, nullptr, round, tab_dev, (const char *)c->stage_dev[slot],
+                               tab_bytes);
+  if (int rr = stage_release(c, slot)) return rc ? rc : rr;
+  return rc;
 }
 
 int hpc_round_prepare(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch *b,
@@ -1517,7 +1555,7 @@ int hpc_round_enqueue(hpc_ctx *c) {
   if (!c) return HPC_ERR_ARG;
   if (!c->plan || c->plan->W < 1) return fail(c, HPC_ERR_ARG, "no prepared round");
   cudaSetDevice(c->device);
-  return round_enqueue(c, *c->plan, c->plan_round, 0);
+  return round_enqueue(c, *c->plan, c->plan_round, 0, nullptr, nullptr, 0);
 }
 
 }  // extern "C"
