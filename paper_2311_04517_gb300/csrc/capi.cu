@@ -37,6 +37,10 @@ struct hpc_ctx {
   int *dwords;
   void *ws;
   size_t ws_bytes;
+  // each worker's updates in its latest run, read by the next round's Lloyd
+  // CTA plan (hpc_round; a prepared round keeps its own): zero when allocated
+  int32_t *upd;
+  int64_t upd_cap;
   int64_t launches;
   int use_tc;  // 0 never, 1 wherever built, 2 (default): where measured faster
   // objective search forms chosen by hpc_autotune_objective / set by the
@@ -113,6 +117,28 @@ int ensure_ws(hpc_ctx *c, size_t bytes) {
     return fail(c, HPC_ERR_NOMEM, "scratch allocation failed");
   }
   c->ws_bytes = want;
+  return HPC_OK;
+}
+
+// The context's per-worker update counts, at least W of them; new ones are
+// zero (no run yet).
+int ensure_upd(hpc_ctx *c, int64_t W) {
+  if (W <= c->upd_cap) return HPC_OK;
+  cudaError_t e;
+  if (c->upd) {
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+    cudaFree(c->upd);
+    c->upd = nullptr;
+    c->upd_cap = 0;
+  }
+  const int64_t want = std::max<int64_t>(W, 128);
+  if ((e = cudaMalloc(&c->upd, (size_t)want * sizeof(int32_t))) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, HPC_ERR_NOMEM, "update-count allocation failed");
+  }
+  if ((e = cudaMemsetAsync(c->upd, 0, (size_t)want * sizeof(int32_t), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "memset");
+  c->upd_cap = want;
   return HPC_OK;
 }
 
@@ -539,7 +565,7 @@ static size_t round_scratch_bytes(const hpc_ctx *c, const hpc_batch *b, int d, i
 static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_batch *b,
                        int strategy, uint64_t seed, uint32_t round, int max_iter, double rel_tol,
                        int L, Carver &cv, char *tab_host, char *tab_dev, size_t tab_bytes,
-                       hpc_round_plan &p, int tc_mode) {
+                       int32_t *uprev, hpc_round_plan &p, int tc_mode) {
   const int W = b->W;
   const int nchunks = (W + HPC_ROUND_CHUNK - 1) / HPC_ROUND_CHUNK;
   int64_t smax = 0;
@@ -547,9 +573,8 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
   TaskHeader *hdr = cv.take<TaskHeader>((size_t)W);
   double *fw = cv.take<double>((size_t)W);
   int32_t *itw = cv.take<int32_t>((size_t)W);
-  // each worker's updates in its latest run: the same place every round
-  // (the layout is the same), read by the next round's Lloyd plan
-  int32_t *uprev = cv.take<int32_t>((size_t)W);
+  // uprev: each worker's updates in its latest run (W of them, kept between
+  // rounds by the caller), read by this round's Lloyd plan and rewritten by it
   Carver th{tab_host, 0, tab_bytes}, td{tab_dev, 0, tab_bytes};
   hpc_sample_task *st_h = th.take<hpc_sample_task>((size_t)W);
   hpc_sample_task *st_d = td.take<hpc_sample_task>((size_t)W);
@@ -787,6 +812,7 @@ int hpc_destroy(hpc_ctx *c) {
   cudaStreamSynchronize(c->stream);
   if (c->ws) cudaFree(c->ws);
   if (c->dwords) cudaFree(c->dwords);
+  if (c->upd) cudaFree(c->upd);
   for (int i = 0; i < 4; ++i) {
     if (c->stage_host[i]) cudaFreeHost(c->stage_host[i]);
     if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
@@ -1484,6 +1510,7 @@ int hpc_round(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch 
   size_t tab_bytes = 0;
   const size_t need = round_scratch_bytes(c, b, d, n_candidates, &tab_bytes);
   if (int rc = ensure_ws(c, need)) return rc;
+  if (int rc = ensure_upd(c, b->W)) return rc;
   Carver cv{reinterpret_cast<char *>(c->ws), 0, c->ws_bytes};
   char *tab_dev = cv.take<char>(tab_bytes);
   char *tab_host = nullptr;
@@ -1494,7 +1521,7 @@ int hpc_round(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hpc_batch 
   if (int rc = prec_lloyd_mode(c, prec, d, kmax, &mode)) return rc;
   hpc_round_plan p;
   if (int rc = round_build(c, X, n, d, b, strategy, seed, round, max_iter, rel_tol, n_candidates,
-                           cv, tab_host, tab_dev, tab_bytes, p, mode))
+                           cv, tab_host, tab_dev, tab_bytes, c->upd, p, mode))
     return rc;
   // the set-up launch reads the tables from the pinned staging slot
   const int rc = round_enqueue(c, p, nullptr, round, tab_dev, (const char *)c->stage_dev[slot],
@@ -1529,6 +1556,7 @@ int hpc_round_prepare(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hp
   Carver cv{reinterpret_cast<char *>(c->plan_mem), 0, c->plan_bytes};
   c->plan_round = cv.take<uint32_t>(1);
   char *tab_dev = cv.take<char>(tab_bytes);
+  int32_t *uprev = cv.take<int32_t>((size_t)b->W);  // no run yet: zero below
   p.host.assign(tab_bytes, 0);
   int kmax = 0, mode = 0;
   for (int w = 0; w < b->W; ++w) kmax = std::max(kmax, (int)b->k[w]);
@@ -1537,11 +1565,12 @@ int hpc_round_prepare(hpc_ctx *c, const float *X, int64_t n, int32_t d, const hp
     return rc;
   }
   if (int rc = round_build(c, X, n, d, b, strategy, seed, round0, max_iter, rel_tol, n_candidates,
-                           cv, p.host.data(), tab_dev, tab_bytes, p, mode)) {
+                           cv, p.host.data(), tab_dev, tab_bytes, uprev, p, mode)) {
     p.W = 0;
     return rc;
   }
-  if ((e = cudaMemcpyAsync(tab_dev, p.host.data(), tab_bytes, cudaMemcpyHostToDevice, c->stream)) ||
+  if ((e = cudaMemsetAsync(uprev, 0, (size_t)b->W * sizeof(int32_t), c->stream)) ||
+      (e = cudaMemcpyAsync(tab_dev, p.host.data(), tab_bytes, cudaMemcpyHostToDevice, c->stream)) ||
       (e = cudaMemcpyAsync(c->plan_round, &round0, sizeof(uint32_t), cudaMemcpyHostToDevice,
                            c->stream)) ||
       (e = cudaStreamSynchronize(c->stream))) {
