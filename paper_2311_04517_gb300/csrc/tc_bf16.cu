@@ -1024,6 +1024,9 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   __shared__ unsigned s_umax, s_cmax, s_nmax, s_live;
   __shared__ uint32_t s_tmem;
   __shared__ int s_qn;
+  // the current task's descriptor: its fields are read from here where used
+  // rather than held in registers through the task
+  __shared__ hpc_lloyd_task s_tk;
 
   if (a.round_advance && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.round_advance, 1u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1062,7 +1065,9 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     alone = true;
   }
   while (tix >= 0) {
-  const hpc_lloyd_task tk = a.W == 1 ? a.single : a.tasks[tix];
+  if (threadIdx.x == 0) s_tk = a.W == 1 ? a.single : a.tasks[tix];
+  __syncthreads();
+  const hpc_lloyd_task &tk = s_tk;
   const int k = tk.k, kp = (k + 1) & ~1;
   const int64_t s = tk.s;
   const int G = alone ? 1 : tk.nblocks, lb = alone ? 0 : (int)blockIdx.x - tk.block0;
