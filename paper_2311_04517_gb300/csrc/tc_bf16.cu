@@ -1027,6 +1027,12 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   // the current task's descriptor: its fields are read from here where used
   // rather than held in registers through the task
   __shared__ hpc_lloyd_task s_tk;
+  // per-task values read where used (thread 0 writes them): the fixed-point
+  // grids of the sums (2^-Fs) and of the objective (oscale = 2^Fo), the
+  // previous objective
+  __shared__ int s_Fs;
+  __shared__ float s_oscale;
+  __shared__ double s_fprev;
 
   if (a.round_advance && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.round_advance, 1u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1074,6 +1080,8 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   if (threadIdx.x == 0) {
     s_umax = s_cmax = s_nmax = s_live = 0u;
     s_qn = 0;
+    s_done = 0;
+    s_fprev = 0.0;
   }
   for (int j = threadIdx.x; j < 512; j += TB_THREADS) m.dead[j] = (j >= k) || tk.deg[j] != 0;
   __syncthreads();
@@ -1108,30 +1116,35 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   });
   __syncthreads();
   if (threadIdx.x == 0) atomicMax(tk.gmaxabs, s_umax);
-  float cmax = sqrtf(__uint_as_float(s_nmax));
-  int live = (int)s_live;
+  // the exact centroid block as the latest build left it (max norm and live
+  // count from shared memory, so that nothing of it stays in registers
+  // through the pass)
+  auto gcs_now = [&]() {
+    return tb_gcs<D>(tk.gcent, k, sqrtf(__uint_as_float(s_nmax)), (int)s_live);
+  };
+  const int live0 = (int)s_live;
   bool run = hpc_grid_sync(tk.bar, a.status, (unsigned)G);
   const unsigned mabs = run ? __ldcg(tk.gmaxabs) : 0u;
   if (run && (mabs >= 0x7f800000u || s_cmax >= 0x7f800000u)) {
     if (threadIdx.x == 0) hpc_status_set(a.status, HPC_ERR_NONFINITE);
     run = false;
   }
-  if (run && live == 0) {
+  if (run && live0 == 0) {
     if (threadIdx.x == 0) hpc_status_set(a.status, HPC_ERR_DEGENERATE_ALL);
     run = false;
   }
-  int Fs = 126;
-  if (mabs != 0u) Fs = min(126, 62 - hpc_bit_length(s) - hpc_frexp_exp(__uint_as_float(mabs)));
-  const float qscale = hpc_pow2f(Fs);
-  int Fo = 126;
-  {
+  if (threadIdx.x == 0) {
+    int Fs = 126;
+    if (mabs != 0u) Fs = min(126, 62 - hpc_bit_length(s) - hpc_frexp_exp(__uint_as_float(mabs)));
+    int Fo = 126;
     const unsigned mm = max(mabs, s_cmax);
     if (mm != 0u && mm < 0x7f800000u)
       Fo = min(126, 59 - hpc_bit_length(s) - hpc_bit_length(D) - 2 * hpc_frexp_exp(__uint_as_float(mm)));
     Fo = max(Fo, -126);
+    s_Fs = Fs;
+    s_oscale = hpc_pow2f(Fo);
   }
-  const float oscale = hpc_pow2f(Fo);
-  const double oinv = hpc_pow2d(-Fo);
+  __syncthreads();
 
   TbRows R;
   R.rows = tk.S;
@@ -1139,12 +1152,9 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   R.tile0 = lb;
   R.tstep = G;
   R.ntiles = lb < ntiles ? (int)((ntiles - 1 - lb) / G + 1) : 0;
-  double f_prev = 0.0;
-  bool finished = false;
   for (int it = 0; run; ++it) {
     // Phase A: assignment of the CTA's rows, sums of the rows that moved
     float fs_hi = 0.0f, fs_lo = 0.0f;
-    const hpc_cent_smem gcs = tb_gcs<D>(tk.gcent, k, cmax, live);
     // a row that moved from centroid jo (-1: first assignment) to jn: the
     // whole warp adds its fixed-point coordinates to jn's sums and takes them
     // from jo's, lanes over dimensions
@@ -1162,6 +1172,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
         xv[0] = q2.x;
         xv[1] = q2.y;
       }
+      const float qscale = hpc_pow2f(s_Fs);
 #pragma unroll
       for (int u = 0; u < PER; ++u) {
         const long long qv = __float2ll_rn(xv[u] * qscale);
@@ -1181,7 +1192,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
       int j = 0;
       float dd = 0.0f;
       const bool ok = tb_exact<D, Cfg::IB>(tk.S, row0w, row, valid, j1, j2, d1, d2, lo3,
-                                                    gcs, a.status, a.stats, queue, &j, &dd) ==
+                                           gcs_now(), a.status, a.stats, queue, &j, &dd) ==
                       TB_DONE;
       if (ok) hpc_sum2_add(fs_hi, fs_lo, dd);
       int old = -1;
@@ -1201,7 +1212,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     });
     __syncthreads();
     // the queued rows, every warp
-    tb_settle_queue<D, NP>(m, tk.S, queue, gcs, a.stats, [&](int64_t row, int j, float dd) {
+    tb_settle_queue<D, NP>(m, tk.S, queue, gcs_now(), a.stats, [&](int64_t row, int j, float dd) {
       if (lane == 0) hpc_sum2_add(fs_hi, fs_lo, dd);
       const int old = it > 0 ? tk.plab[row] : -1;
       if (old != j) move(row, j, old);
@@ -1215,6 +1226,7 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     __syncthreads();
     if (s_abort) break;
     // the objective partial on the grid 2^-Fo, summed over the block in integers
+    const float oscale = s_oscale;
     const unsigned long long bq = hpc_block_sum_u64(
         (unsigned long long)(__float2ll_rn(fs_hi * oscale) + __float2ll_rn(fs_lo * oscale)),
         reinterpret_cast<unsigned long long *>(s_dsum));
@@ -1223,8 +1235,11 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
     if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) break;
     // Phase B: objective, stop test, new centroids (every CTA, identical)
     if (threadIdx.x == 0) {
-      const double fo = (double)(long long)__ldcg(tk.gobj + buf) * oinv;
+      // 1 / oscale is an exact power of two
+      const double fo = (double)(long long)__ldcg(tk.gobj + buf) / (double)s_oscale;
+      const double f_prev = s_fprev;
       s_f = fo;
+      s_fprev = fo;
       s_done = (it > 0 && (f_prev == 0.0 || (f_prev - fo) < a.tol * f_prev)) || it == a.max_iter;
       s_nmax = 0u;
       s_live = 0u;
@@ -1240,7 +1255,6 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
         }
         if (tk.fhat) hpc_incumbent_block(tk, D, f, it);
       }
-      finished = true;
       break;
     }
     tb_build_b<D, NP>(m, k, tk.gcent, lb == 0, &s_nmax, &s_live,
@@ -1257,20 +1271,19 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
 #pragma unroll
       for (int u = 0; u < PER; ++u) {
         const long long q = (long long)__ldcg(tk.gsum + (size_t)j * D + t0 + u);
-        c[u] = hpc_mean_f32(q, cnt, Fs);
+        c[u] = hpc_mean_f32(q, cnt, s_Fs);
         if (lb == 0) tk.C[(int64_t)j * D + t0 + u] = c[u];
       }
       return true;
     });
     if (lb == 0 && threadIdx.x == 0) tk.gobj[(it + 2) % 3] = 0ull;
     __syncthreads();
-    cmax = sqrtf(__uint_as_float(s_nmax));
-    live = (int)s_live;
-    f_prev = f;
     if (!hpc_grid_sync(tk.bar, a.status, (unsigned)G)) break;
   }
   __syncthreads();  // every thread is done with the task's shared state
-  // a task that stopped on an error (status recorded) ends the CTA's list
+  // a task that stopped on an error (status recorded) ends the CTA's list;
+  // s_done is set only by a run that finished
+  const bool finished = s_done != 0;
   tix = !finished || a.W == 1 ? -1 : take();
   alone = true;
   }
