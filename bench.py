@@ -955,7 +955,10 @@ def run_mine(args):
         e_value = e_dist / (e_ms / 1e3)
         if shared:
             job.b.X = X
-        e2e = {"value": e_value, "unit": UNIT, "device_buffers": nb,
+        # its own steps (later rounds than the timed ones: fewer Lloyd updates
+        # as the incumbents improve, so the copy of X weighs more)
+        e2e = {"value": e_value, "unit": UNIT, "device_buffers": nb, "steps": E,
+               "ms_per_step": e_ms / E, "lloyd_iters_mean": float(ei.mean()),
                "h2d_bytes_per_step": int(X_host.numel() * 4),
                "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4 +
                                          (Wl * 8 if wl.W > 1 else 0))}
