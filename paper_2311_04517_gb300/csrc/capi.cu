@@ -48,7 +48,7 @@ struct hpc_ctx {
   std::vector<std::pair<int64_t, int>> forms;
   int force_form;  // >= 0 while hpc_autotune_objective times one form
   // pinned staging ring for the per-round descriptor tables: slot i is
-  // rewritten only after the copy issued from it last time has run
+  // rewritten only after the launch that read it last time has run
   void *stage_host[4];
   void *stage_dev[4];  // the same pinned slot, mapped into the device's address space
   size_t stage_bytes[4];
@@ -692,10 +692,11 @@ static int round_build(hpc_ctx *c, const float *X, int64_t n, int d, const hpc_b
   return HPC_OK;
 }
 
-// One round: a memset of the task headers and 1 + 2 * chunks launches (the
-// sampling launch also selects every worker's base; each Lloyd task applies
-// the incumbent rule when its run is done); no host synchronisation, no
-// allocation (a stream capture can record it).  The round index is `round`,
+// One round: the set-up launch (tables, task headers), the sampling launch
+// (which also selects every worker's base) and per chunk of workers the
+// K-means++ and Lloyd launches, each with its planning launch when batched
+// (each Lloyd task applies the incumbent rule when its run is done); no host
+// synchronisation, no allocation (a stream capture can record it).  The round index is `round`,
 // or *round_dev when that is given (a prepared round, whose last Lloyd
 // launch then advances it).
 // Records timing event i of a round on the context's stream; inside a

@@ -54,9 +54,9 @@ struct hpc_lloyd_task {
   int32_t *iters_rep;
   uint8_t *accepted;
   unsigned long long *t_done;  // nullable: the time (globaltimer ns) the run ended
-  // nullable: the worker's updates in its latest run (round scratch that
-  // keeps its value from round to round), written at the end of a run and
-  // read by the split-BF16 Lloyd's plan of the next round
+  // nullable: the worker's updates in its latest run (a buffer of the
+  // caller's that keeps its value from round to round), written at the end
+  // of a run and read by the split-BF16 Lloyd's plan of the next round
   int32_t *uprev;
 };
 // Lloyd zeroes gsum / gcount itself; bar and gmaxabs must be zero at launch.
