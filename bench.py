@@ -167,6 +167,40 @@ def lloyd_roofline(kernel: str, form: str, passes_rows_k, d: int, launches: int,
                           {"launches_timed": launches})
 
 
+def plan_balance(s, k, u_prev, u_now, ctas: int) -> dict:
+    """The batched split-BF16 Lloyd's CTA plan as the device makes it from
+    one step's update counts, timed with the next step's counts in units of
+    distances (s k (u + 1) per worker): a set's CTAs run its workers one
+    after another, each worker's work spread over them; a free CTA takes the
+    next worker of the list (the earliest free first). Returns the plan's
+    shape and its makespan over the balanced time (all work spread evenly
+    over the CTAs); the kernel's time per distance is the launch's time over
+    that makespan."""
+    import heapq
+
+    from paper_2311_04517_gb300 import hpclust as H
+    s = np.asarray(s, np.int64)
+    k = np.asarray(k, np.int64)
+    plan = H.lloyd_cta_plan(s, k, np.asarray(u_prev, np.int32), int(ctas))
+    work = s.astype(np.float64) * k * (np.clip(np.asarray(u_now, np.int64), 0, None) + 1)
+    ct, nb, nxt = plan["cta_task"], plan["nblocks"], plan["next"]
+    free = []
+    for c, t in enumerate(ct):
+        f = 0.0
+        while t >= 0:
+            f += float(work[t] / nb[t])
+            t = int(nxt[t])
+        free.append((f, c))
+    heapq.heapify(free)
+    for t in plan["list"]:
+        f0, c = heapq.heappop(free)
+        heapq.heappush(free, (f0 + float(work[t]), c))
+    makespan = max(f for f, _ in free)
+    return {"sets": len({int(t) for t in ct if t >= 0}), "set_ctas": int((ct >= 0).sum()),
+            "list": int(len(plan["list"])),
+            "makespan_over_balanced": float(makespan / (work.sum() / int(ctas)))}
+
+
 def peaks():
     f = ROOT / "MEASURED_PEAKS.json"
     if f.exists():
@@ -993,6 +1027,14 @@ def run_mine(args):
                                  len(lloyd_ms) * chunks,
                                  float(np.sum(lloyd_ms)) / (len(lloyd_ms) * chunks), hbm, src,
                                  profiled_traffic("lloyd", wl.name, lloyd_kernel_name))
+    # how far the last step's CTA plan was from an even spread of the work
+    lplan = None
+    if lsched["form"] == "split_bf16" and 1 < Wl <= 128 and K >= 2 and not Wm_extra:
+        try:
+            lplan = plan_balance(ws.s[w0:w0 + Wl], ws.k[w0:w0 + Wl], iters[K - 2], iters[K - 1],
+                                 int(lsched["blocks"]))
+        except Exception as exc:  # a diagnostic only
+            lplan = {"error": str(exc)}
     phase_ms = {k: float(np.mean([p[k] for p in phase_log])) for k in phase_log[0]}
     phase_ms["objective"] = float(np.mean(obj_ms))
     # the roofline line names the kernel that takes the larger share of a step
@@ -1013,6 +1055,7 @@ def run_mine(args):
             "roofline_other": other,
             "phase_ms_per_step": phase_ms,
             "lloyd_schedule": lsched,
+            "lloyd_plan_last_step": lplan,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(t0, t1),

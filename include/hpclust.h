@@ -180,19 +180,23 @@ int hpc_lloyd_schedule(hpc_ctx *ctx, int64_t s, int32_t d, int32_t k, int32_t *o
  * computes before every launch of a round, from each worker's sample size
  * s[w], centroid count k[w] and updates in its previous run u[w] (host
  * arrays of W <= 128; negative u counts as 0, u above 1000 as 1000).  The
- * work of worker w is s k (u + 1); workers of at least 0.85 times the mean
- * work per CTA get groups of round(work / (0.85 mean)) CTAs of their own
- * (at most one per 128 rows; while the groups need more than `ctas`, the
- * group with the least work per CTA gives one up), the others wait in a
- * list, largest first, from which CTAs take one as they become free.
- * Output (host): cta_task[ctas] the worker each CTA starts with (-2: it
- * takes from the list), list[W] the list (its length returned through
- * *nlist), nblocks[W] each worker's CTAs (1 for listed workers).
+ * work of worker w is s k (u + 1).  The workers are dealt into
+ * max(1, min(W, ctas / 16)) sets, largest first each to the set with the
+ * least work so far (lowest index on ties); every set gets one CTA, then
+ * the remaining CTAs go one at a time to the set with the most work per CTA
+ * among those with fewer CTAs than the 128-row tiles of their smallest
+ * sample; the sets take contiguous CTA ranges in set order.  A set runs its
+ * workers one after another, each on all of its CTAs.
+ * Output (host): cta_task[ctas] the first worker of each CTA's set (-2: no
+ * set; such a CTA takes workers from the list), list[W] the workers CTAs
+ * take one at a time as they become free (its length returned through
+ * *nlist; 0 with this plan), next[W] the worker a set runs after worker w
+ * (-1 after its last), nblocks[W] each worker's CTAs (its set's).
  * Errors: HPC_ERR_ARG (W outside 1..128, ctas < 1, a NULL array, s < 1 or
  * k < 1). */
 int hpc_lloyd_cta_plan(int32_t W, const int64_t *s, const int32_t *k, const int32_t *u,
                        int32_t ctas, int32_t *cta_task, int32_t *list, int32_t *nlist,
-                       int32_t *nblocks);
+                       int32_t *next, int32_t *nblocks);
 
 /* Per-phase timing of rounds (the paper has no counterpart: measurement
  * only).  With timing on, every round enqueued on the context (hpc_round,

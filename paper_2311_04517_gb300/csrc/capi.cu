@@ -965,9 +965,9 @@ int hpc_objective_form(hpc_ctx *c, int64_t n, int32_t d, int32_t k) {
 
 int hpc_lloyd_cta_plan(int32_t W, const int64_t *s, const int32_t *k, const int32_t *u,
                        int32_t ctas, int32_t *cta_task, int32_t *list, int32_t *nlist,
-                       int32_t *nblocks) {
-  if (!s || !k || !u || !cta_task || !list || !nlist || !nblocks) return HPC_ERR_ARG;
-  return hpc_tcl_cta_plan(W, s, k, u, ctas, cta_task, list, nlist, nblocks);
+                       int32_t *next, int32_t *nblocks) {
+  if (!s || !k || !u || !cta_task || !list || !nlist || !next || !nblocks) return HPC_ERR_ARG;
+  return hpc_tcl_cta_plan(W, s, k, u, ctas, cta_task, list, nlist, next, nblocks);
 }
 
 int hpc_lloyd_schedule(hpc_ctx *c, int64_t s, int32_t d, int32_t k, int32_t *out, int32_t nout) {

@@ -229,7 +229,8 @@ bool hpc_tcl_supported(int d, int kmax);
 size_t hpc_tcl_gcent_bytes(int d, int k);
 int hpc_tcl_plan(const hpc_launch &L, LloydLaunch &h);
 int hpc_tcl_cta_plan(int W, const int64_t *s, const int32_t *k, const int32_t *u, int64_t ctas,
-                     int32_t *cta_task, int32_t *list, int32_t *nlist, int32_t *nblocks);
+                     int32_t *cta_task, int32_t *list, int32_t *nlist, int32_t *next,
+                     int32_t *nblocks);
 int hpc_tcl_run(const hpc_launch &L, const LloydLaunch &h);
 // Split-BF16 tensor-core full-data objective (same shapes); needs
 // h.cent_scratch of hpc_tcl_gcent_bytes(d, k) + 256 bytes.

@@ -1002,6 +1002,7 @@ struct TclArgs {
   const int *block_task;   // W > 1: each CTA's first task (-2: take one from the list)
   const int *follow;       // W > 1: the tasks CTAs take as they become free, largest first
   const int *nfollow;      // W > 1: their number (device)
+  const int *next;         // W > 1: the task a set runs after this one (-1: none)
   unsigned *pop;           // W > 1: the list's next entry (zero at launch)
   int max_iter;
   double tol;
@@ -1049,9 +1050,9 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   __syncthreads();
   hpc_tc_fence_after();
   m.tmem = s_tmem;
-  // the CTA's tasks, one after another: a task with a group of CTAs of its
-  // own, or small tasks packed into this CTA (each with a group of one);
-  // the pipeline's tile sequence runs on from task to task
+  // the CTA's tasks, one after another: those of its set, each on all of
+  // the set's CTAs, then any from the list, alone; the pipeline's tile
+  // sequence runs on from task to task
   uint32_t gbase = 0, drains = 0;
   // the next task from the list (the same for the whole CTA), -1 when empty
   auto take = [&]() {
@@ -1284,8 +1285,10 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcl_lloyd_kernel(TclArgs a) {
   // a task that stopped on an error (status recorded) ends the CTA's list;
   // s_done is set only by a run that finished
   const bool finished = s_done != 0;
-  tix = !finished || a.W == 1 ? -1 : take();
-  alone = true;
+  // the set's next task (on all its CTAs), else one from the list, alone
+  const int nxt = !finished || a.W == 1 || alone ? -1 : a.next[tix];
+  tix = !finished || a.W == 1 ? -1 : nxt >= 0 ? nxt : take();
+  alone = nxt < 0;
   }
   // drain: no MMA may still target this CTA's TMEM or shared memory
   __syncthreads();
@@ -1427,24 +1430,30 @@ __global__ void __launch_bounds__(TB_THREADS, 1) tcb_objective_kernel(TcbArgs a)
 // ---- host side ----------------------------------------------------------------------
 int tb_np(int k) { return k <= 128 ? 128 : k <= 256 ? 256 : 512; }
 
-// The CTAs of a batched tensor-core Lloyd launch (one per SM).  With about
-// as many workers as SMs a split in proportion to s k alone gives each small
-// worker a CTA of its own and a worker of 1.7 CTAs' work one or two, and the
-// number of updates (5 to 15 on the large workload; fewer for larger
-// samples) is only known as they run.  So the work of a task is s k (u + 1),
-// u its updates in its previous run (0 before the first): a task of at least
-// M = 0.85 times the mean work per CTA gets round(work / M) CTAs of its own
-// (its rows split evenly; fewer while the launch has too few); every other
-// task waits in a list, largest first, and a CTA without a task, or done with
-// its last, takes the next one (an atomic counter) and runs it alone.
-// (Simulated with update counts like the large workload's: 1.52 times the
-// balanced time, against 1.81 for groups of ceil(work / 1.15 mean) CTAs;
-// whole CTAs per task bound it.)  Computed by one thread, on the host for the
-// plan and on the device before every launch (the previous run's updates
-// are there).
-// Writes block_task[0, total) (a task, or -2: start from the list),
-// follow[0, nf), nb[] and b0[] per task; returns nf.
+// The CTAs of a batched tensor-core Lloyd launch (one per SM).  A launch
+// runs up to 128 workers on 152 CTAs, so the average worker is about 1.2
+// CTAs of work, and a CTA serves one worker at a time: whole CTAs per worker
+// (a group for the larger ones, the smaller ones one after another on a CTA
+// each) left the launch at about 1.5 times the balanced time even with the
+// update counts known.  So the workers are dealt into sets, each a
+// contiguous range of CTAs that runs its workers one after another, every
+// worker on all of the set's CTAs (its rows split evenly, its barriers over
+// the set): the workers, largest first, go to the set with the least work
+// so far (TCL_SET_CTAS CTAs a set on average), then the CTAs to the sets,
+// one at a time to the set with the most work per CTA (at most as many as
+// the tiles of its smallest worker).  The work of a worker is s k (u + 1),
+// u its updates in its previous run (0 before the first).  (Simulated with
+// update counts like the large workload's, predicted from the previous
+// round: 1.07-1.09 times the balanced time, against 1.7-1.8 for the groups
+// and list.)  Computed by one thread, on the host for the plan and on the
+// device before every launch (the previous run's updates are there).
+// Writes block_task[0, total) (each CTA's first worker, -2: none, it takes
+// from the list), next[0, W) (the worker its set runs after this one, -1
+// after the last), nb[] and b0[] per worker (its set's CTAs), and the list
+// follow[0, nf) of workers run alone by free CTAs (empty with this plan);
+// returns nf.
 constexpr int TCL_PACK_MAX = 128;  // workers of one launch (a round's chunk)
+constexpr int TCL_SET_CTAS = 16;   // CTAs of a set, on average
 
 // a task's work: s k (u + 1), u its updates in the previous run (clamped)
 __host__ __device__ inline double tcl_work(int64_t s, int k, int u) {
@@ -1453,7 +1462,8 @@ __host__ __device__ inline double tcl_work(int64_t s, int k, int u) {
 }
 
 __host__ __device__ int tcl_pack_core(int W, const double *work, const int64_t *cap, int64_t total,
-                                      int *block_task, int *follow, int *nb, int *b0) {
+                                      int *block_task, int *follow, int *next, int *nb, int *b0) {
+  (void)follow;
   int order[TCL_PACK_MAX];
   for (int w = 0; w < W; ++w) {  // largest first, lower index on ties (insertion)
     int i = w;
@@ -1463,61 +1473,65 @@ __host__ __device__ int tcl_pack_core(int W, const double *work, const int64_t *
     }
     order[i] = w;
   }
-  double sum = 0.0;
-  for (int w = 0; w < W; ++w) sum += work[w];
-  // groups for the tasks of at least M = 0.85 times the mean work per CTA,
-  // round(work / M) CTAs each; while they are more than the launch has, the
-  // group with the least work per CTA gives one up
-  const double M = 0.85 * sum / (double)total;
-  int64_t used = 0;
-  for (int j = 0; j < W; ++j) {
-    const int w = order[j];
-    if (work[w] >= M) {
-      int64_t n = (int64_t)floor(work[w] / M + 0.5);
-      n = n < cap[w] ? n : cap[w];
-      nb[w] = (int)(n < 1 ? 1 : n);
-      used += nb[w];
-    } else {
-      nb[w] = 0;
-    }
+  int64_t ns = total / TCL_SET_CTAS;
+  ns = ns < 1 ? 1 : ns > W ? W : ns;
+  const int nsets = (int)ns;
+  double sum[TCL_PACK_MAX];
+  int first[TCL_PACK_MAX], last[TCL_PACK_MAX];
+  int64_t g[TCL_PACK_MAX], gmax[TCL_PACK_MAX];
+  for (int j = 0; j < nsets; ++j) {
+    sum[j] = 0.0;
+    first[j] = last[j] = -1;
+    g[j] = 0;
+    gmax[j] = total;
   }
-  while (used > total) {
-    int best = -1;
-    for (int j = 0; j < W; ++j) {
-      const int w = order[j];
-      if (nb[w] > 1 && (best < 0 || work[w] / nb[w] < work[best] / nb[best])) best = w;
-    }
-    if (best < 0) {  // one CTA each and still too many: the smallest groups join the list
-      for (int j = W - 1; j >= 0 && used > total; --j)
-        if (nb[order[j]] == 1) {
-          nb[order[j]] = 0;
-          --used;
-        }
-      break;
-    }
-    --nb[best];
-    --used;
+  // workers, largest first, to the set with the least work (lowest index on
+  // ties), appended to its sequence
+  for (int i = 0; i < W; ++i) {
+    const int w = order[i];
+    int b = 0;
+    for (int j = 1; j < nsets; ++j)
+      if (sum[j] < sum[b]) b = j;
+    sum[b] += work[w];
+    next[w] = -1;
+    if (last[b] >= 0) next[last[b]] = w;
+    else first[b] = w;
+    last[b] = w;
+    if (cap[w] < gmax[b]) gmax[b] = cap[w] > 0 ? cap[w] : 1;
+  }
+  // CTAs: one each, then one at a time to the set with the most work per
+  // CTA that may take another
+  int64_t used = 0;
+  for (int j = 0; j < nsets; ++j) {
+    g[j] = 1;
+    ++used;
+  }
+  while (used < total) {
+    int b = -1;
+    for (int j = 0; j < nsets; ++j)
+      if (g[j] < gmax[j] && (b < 0 || sum[j] / (double)g[j] > sum[b] / (double)g[b])) b = j;
+    if (b < 0) break;
+    ++g[b];
+    ++used;
   }
   int64_t grid = 0;
-  int nf = 0;
-  for (int j = 0; j < W; ++j) {
-    const int w = order[j];
-    if (nb[w] > 0) {
+  for (int j = 0; j < nsets; ++j) {
+    for (int64_t i = 0; i < g[j]; ++i) block_task[grid + i] = first[j];
+    for (int w = first[j]; w >= 0; w = next[w]) {
       b0[w] = (int)grid;
-      for (int i = 0; i < nb[w]; ++i) block_task[grid++] = w;
-    } else {
-      nb[w] = 1;
-      b0[w] = -1;  // whichever CTA takes it, alone
-      follow[nf++] = w;
+      nb[w] = (int)g[j];
     }
+    grid += g[j];
   }
   for (; grid < total; ++grid) block_task[grid] = -2;
-  return nf;
+  return 0;
 }
 
 // The device side: the tasks' work from the previous round's updates, the
-// plan written into the launch's tables (block_task, the list and its length
-// in block_task[2 max_blocks - 1], the tasks' groups).
+// plan written into the launch's tables (block_task; after it the list, from
+// block_task[max_blocks], the next links, from block_task[max_blocks +
+// TCL_PACK_MAX], and the list's length in block_task[2 max_blocks - 1]; the
+// tasks' sets).
 __global__ void tcl_repack_kernel(hpc_lloyd_task *tasks, int *block_task, int W, int64_t total,
                                   int64_t max_blocks, int64_t task_blocks) {
   if (threadIdx.x != 0) return;
@@ -1530,7 +1544,8 @@ __global__ void tcl_repack_kernel(hpc_lloyd_task *tasks, int *block_task, int W,
     const int64_t c = (sw + TB_M - 1) / TB_M;
     cap[w] = c < task_blocks ? c : task_blocks;
   }
-  const int nf = tcl_pack_core(W, work, cap, total, block_task, block_task + max_blocks, nb, b0);
+  const int nf = tcl_pack_core(W, work, cap, total, block_task, block_task + max_blocks,
+                               block_task + max_blocks + TCL_PACK_MAX, nb, b0);
   block_task[2 * max_blocks - 1] = nf;
   for (int w = 0; w < W; ++w) {
     tasks[w].block0 = b0[w];
@@ -1548,7 +1563,7 @@ void tcl_pack(LloydLaunch &h, int64_t total) {
     cap[w] = std::min<int64_t>((sw + TB_M - 1) / TB_M, h.task_blocks);
   }
   h.nfollow = tcl_pack_core(h.W, work, cap, total, h.block_task_host, h.block_task_host + h.max_blocks,
-                            nb, b0);
+                            h.block_task_host + h.max_blocks + TCL_PACK_MAX, nb, b0);
   h.block_task_host[2 * h.max_blocks - 1] = h.nfollow;
   for (int w = 0; w < h.W; ++w) {
     h.tasks[w].block0 = b0[w];
@@ -1584,7 +1599,8 @@ int tcl_plan_t(const hpc_launch &L, LloydLaunch &h) {
     h.tasks[0].nblocks = (int)total;
     h.grid = total;
   } else {
-    if (!h.pop || h.W > TCL_PACK_MAX || h.max_blocks < TCL_PACK_MAX + 2) return HPC_ERR_UNSUPPORTED;
+    if (!h.pop || h.W > TCL_PACK_MAX || h.max_blocks < 2 * TCL_PACK_MAX + 2)
+      return HPC_ERR_UNSUPPORTED;
     tcl_pack(h, total);
   }
   h.smem = smem;
@@ -1604,6 +1620,7 @@ int tcl_run_t(const hpc_launch &L, const LloydLaunch &h) {
   a.block_task = h.block_task_dev;
   a.follow = h.W > 1 ? h.block_task_dev + h.max_blocks : nullptr;
   a.nfollow = h.W > 1 ? h.block_task_dev + 2 * h.max_blocks - 1 : nullptr;
+  a.next = h.W > 1 ? h.block_task_dev + h.max_blocks + TCL_PACK_MAX : nullptr;
   a.pop = h.pop;
   if (h.W > 1) {  // the plan for this round, from the previous round's updates
     tcl_repack_kernel<<<1, 32, 0, L.stream>>>(const_cast<hpc_lloyd_task *>(h.tasks_dev),
@@ -1685,7 +1702,8 @@ size_t hpc_tcl_gcent_bytes(int d, int k) {
 }
 
 int hpc_tcl_cta_plan(int W, const int64_t *s, const int32_t *k, const int32_t *u, int64_t ctas,
-                     int32_t *cta_task, int32_t *list, int32_t *nlist, int32_t *nblocks) {
+                     int32_t *cta_task, int32_t *list, int32_t *nlist, int32_t *next,
+                     int32_t *nblocks) {
   if (W < 1 || W > TCL_PACK_MAX || ctas < 1) return HPC_ERR_ARG;
   double work[TCL_PACK_MAX];
   int64_t cap[TCL_PACK_MAX];
@@ -1695,7 +1713,7 @@ int hpc_tcl_cta_plan(int W, const int64_t *s, const int32_t *k, const int32_t *u
     work[w] = tcl_work(s[w], k[w], u ? u[w] : 0);
     cap[w] = (s[w] + TB_M - 1) / TB_M;
   }
-  *nlist = tcl_pack_core(W, work, cap, ctas, cta_task, list, nblocks, b0);
+  *nlist = tcl_pack_core(W, work, cap, ctas, cta_task, list, next, nblocks, b0);
   return HPC_OK;
 }
 

@@ -106,7 +106,7 @@ def load() -> ctypes.CDLL:
         "hpc_set_objective_form": ([P, i32, i32, i32], ctypes.c_int),
         "hpc_peak_probe": ([i32, i32, P, ctypes.POINTER(f64), ctypes.POINTER(f64)], ctypes.c_int),
         "hpc_objective_form": ([P, i64, i32, i32], ctypes.c_int),
-        "hpc_lloyd_cta_plan": ([i32, P, P, P, i32, P, P, P, P], ctypes.c_int),
+        "hpc_lloyd_cta_plan": ([i32, P, P, P, i32, P, P, P, P, P], ctypes.c_int),
         "hpc_lloyd_schedule": ([P, i64, i32, i32, ctypes.POINTER(ctypes.c_int32), i32],
                                ctypes.c_int),
         "hpc_set_phase_timing": ([P, i32], ctypes.c_int),
@@ -552,8 +552,9 @@ def hpc_costmodel_plan(pred, supported, margin: float):
 
 def lloyd_cta_plan(s, k, u, ctas: int) -> dict:
     """The CTA plan of a batched split-BF16 Lloyd launch (host only; see
-    hpc_lloyd_cta_plan in include/hpclust.h): the worker each CTA starts
-    with (-2: it takes from the list), the list, and each worker's CTAs."""
+    hpc_lloyd_cta_plan in include/hpclust.h): the first worker of each
+    CTA's set (-2: none, it takes from the list), the list, the worker each
+    set runs after each worker (-1: none), and each worker's CTAs."""
     import numpy as np
     L = load()
     s = np.ascontiguousarray(s, dtype=np.int64)
@@ -563,11 +564,13 @@ def lloyd_cta_plan(s, k, u, ctas: int) -> dict:
     cta_task = np.empty(max(int(ctas), 1), np.int32)
     lst = np.empty(max(W, 1), np.int32)
     nb = np.empty(max(W, 1), np.int32)
+    nxt = np.empty(max(W, 1), np.int32)
     nlist = ctypes.c_int32(0)
     rc = L.hpc_lloyd_cta_plan(W, s.ctypes.data, k.ctypes.data, u.ctypes.data, int(ctas),
                               cta_task.ctypes.data, lst.ctypes.data, ctypes.addressof(nlist),
-                              nb.ctypes.data)
+                              nxt.ctypes.data, nb.ctypes.data)
     if rc != 0:
         raise HPCError(rc, "hpc_lloyd_cta_plan")
-    return {"cta_task": cta_task[:int(ctas)], "list": lst[:nlist.value], "nblocks": nb[:W]}
+    return {"cta_task": cta_task[:int(ctas)], "list": lst[:nlist.value], "next": nxt[:W],
+            "nblocks": nb[:W]}
 

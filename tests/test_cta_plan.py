@@ -1,14 +1,17 @@
 """Host logic of the batched split-BF16 Lloyd launch's CTA plan
 (hpc_lloyd_cta_plan, the same code the launch's one-thread planner runs on
-the device before every launch): every worker runs exactly once, either on
-a contiguous group of CTAs of its own or alone from the list; the list is
-largest first; the groups' CTAs per worker follow round(work / (0.85
-mean)); the launch's CTAs are all used."""
+the device before every launch): the workers are dealt, largest first, to
+the set with the least work; every set gets a contiguous range of CTAs, one
+each and then one at a time to the set with the most work per CTA (at most
+its smallest worker's tiles); a set runs its workers one after another
+through the next links; every worker runs exactly once."""
 import numpy as np
 import pytest
 
 from paper_2311_04517_gb300 import hpclust as H
 from paper_2311_04517_gb300 import synth
+
+SET_CTAS = 16
 
 
 def work_of(s, k, u):
@@ -16,47 +19,78 @@ def work_of(s, k, u):
     return np.maximum(np.asarray(s, np.float64), 1) * np.asarray(k, np.float64) * (uc + 1)
 
 
+def expected_sets(work, tiles, ctas):
+    """The plan restated: greedy deal, then greedy CTAs."""
+    W = len(work)
+    order = sorted(range(W), key=lambda w: (-work[w], w))
+    ns = max(1, min(W, ctas // SET_CTAS))
+    sums, members = [0.0] * ns, [[] for _ in range(ns)]
+    for w in order:
+        b = min(range(ns), key=lambda j: (sums[j], j))
+        sums[b] += work[w]
+        members[b].append(w)
+    gmax = [max(1, min(min(tiles[w] for w in m), ctas)) for m in members]
+    g = [1] * ns
+    used = ns
+    while used < ctas:
+        cand = [j for j in range(ns) if g[j] < gmax[j]]
+        if not cand:
+            break
+        b = cand[0]
+        for j in cand[1:]:
+            if sums[j] / g[j] > sums[b] / g[b]:
+                b = j
+        g[b] += 1
+        used += 1
+    return members, g
+
+
 def check_plan(s, k, u, ctas):
     W = len(s)
     p = H.lloyd_cta_plan(s, k, u, ctas)
-    ct, lst, nb = p["cta_task"], p["list"], p["nblocks"]
+    ct, lst, nxt, nb = p["cta_task"], p["list"], p["next"], p["nblocks"]
     work = work_of(s, k, u)
+    tiles = [-(-int(x) // 128) for x in s]
     assert len(ct) == ctas and ((ct >= 0) | (ct == -2)).all()
+    assert len(lst) == 0
+    members, g = expected_sets(work, tiles, ctas)
     runs = np.zeros(W, np.int64)
-    for w in range(W):
-        cs = np.flatnonzero(ct == w)
-        if cs.size:  # a group: contiguous CTAs, as many as nblocks
-            assert cs.size == nb[w] and (np.diff(cs) == 1).all()
-            assert nb[w] <= -(-int(s[w]) // 128)
+    c = 0
+    for m, gj in zip(members, g):
+        # a contiguous range of CTAs, all starting with the set's first worker
+        assert (ct[c:c + gj] == m[0]).all()
+        seq, w = [], m[0]
+        while w >= 0:
+            assert len(seq) <= W, "no cycle"
+            seq.append(w)
+            w = int(nxt[w])
+        assert seq == m, "the set runs its workers in the order dealt"
+        for w in seq:
+            assert nb[w] == gj and gj <= max(1, tiles[w])
             runs[w] += 1
-    for w in lst:
-        assert nb[w] == 1 and not (ct == w).any()
-        runs[w] += 1
+        c += gj
+    assert (ct[c:] == -2).all()
     assert (runs == 1).all(), "every worker exactly once"
-    assert (np.diff(work[lst]) <= 0).all(), "the list is largest first"
-    M = 0.85 * work.sum() / ctas
-    grouped = [w for w in range(W) if (ct == w).any()]
-    for w in grouped:
-        assert work[w] >= M
-        assert nb[w] <= max(1, int(np.floor(work[w] / M + 0.5)))
-    if len(lst):  # listed workers are below M, or were dropped as the smallest groups
-        assert work[lst].max() <= max(work[grouped].min() if grouped else np.inf, M)
-    # CTAs not in a group take from the list
-    assert ((ct == -2).sum() > 0) or len(lst) == 0 or (ct >= 0).sum() == ctas
     return p
 
 
-def test_large_workload_plan():
+def test_large_workload_plan_is_near_balanced():
+    import bench
     wl = synth.WORKLOADS["large"]
     ws = synth.worker_setup(wl)
+    s = np.asarray(ws.s, np.int64)
+    k = np.asarray(ws.k, np.int32)
     rng = np.random.default_rng(7)
-    for _ in range(20):
-        u = rng.integers(4, 18, len(ws.s))
-        p = check_plan(ws.s, ws.k, u, 152)
-        assert len(p["list"]) > 0 and (p["cta_task"] >= 0).sum() > 0
+    for _ in range(10):
+        u = np.clip(np.round(14 - 7 * s / s.max() + rng.normal(0, 1, len(s))), 3, 20).astype(np.int32)
+        p = check_plan(s, k, u, 152)
+        assert len({int(t) for t in p["cta_task"]}) == 152 // SET_CTAS
+        # with the counts the plan was made from: within 12% of an even spread
+        assert bench.plan_balance(s, k, u, u, 152)["makespan_over_balanced"] < 1.12
 
 
-@pytest.mark.parametrize("W,ctas", [(1, 152), (2, 3), (128, 152), (128, 40), (64, 304), (5, 5)])
+@pytest.mark.parametrize("W,ctas", [(1, 152), (2, 3), (128, 152), (128, 40), (64, 304), (5, 5),
+                                    (128, 1216)])
 def test_plan_shapes(W, ctas):
     rng = np.random.default_rng(W * 1000 + ctas)
     s = rng.integers(1, 2_000_000, W)
@@ -67,9 +101,17 @@ def test_plan_shapes(W, ctas):
 
 def test_one_worker_takes_every_cta_it_can_use():
     p = check_plan([10_000_000], [500], [7], 152)
-    assert (p["cta_task"] == 0).sum() == 152 and len(p["list"]) == 0
+    assert (p["cta_task"] == 0).sum() == 152 and p["next"][0] == -1
     p = check_plan([1000], [500], [7], 152)   # eight 128-row tiles: at most 8 CTAs
-    assert p["nblocks"][0] == 8
+    assert p["nblocks"][0] == 8 and (p["cta_task"] == -2).sum() == 144
+
+
+def test_small_samples_cap_their_set():
+    # a set is held to its smallest worker's tiles; the CTAs left over go to
+    # the other sets
+    s = [100_000] * 16 + [640]        # the last worker has five tiles
+    p = check_plan(s, [100] * 17, [5] * 17, 32)
+    assert p["nblocks"][16] <= 5
 
 
 def test_bad_arguments():
@@ -81,3 +123,32 @@ def test_bad_arguments():
         H.lloyd_cta_plan([0], [5], [0], 152)
     with pytest.raises(H.HPCError):
         H.lloyd_cta_plan([10], [5], [0], 0)
+
+
+def test_plan_balance_even_work_is_balanced():
+    # eight equal workers on sixteen CTAs: one set, every worker on its 16
+    # CTAs one after another, the balanced time exactly
+    import bench
+    s = np.full(8, 100_000, np.int64)
+    k = np.full(8, 500, np.int32)
+    u = np.full(8, 9, np.int32)
+    r = bench.plan_balance(s, k, u, u, 16)
+    assert r["sets"] == 1 and r["set_ctas"] == 16 and r["list"] == 0
+    assert r["makespan_over_balanced"] == pytest.approx(1.0, rel=1e-12)
+
+
+def test_plan_balance_sees_a_wrong_prediction():
+    # a worker that takes more updates than predicted lengthens its set
+    import bench
+    ws = synth.worker_setup(synth.WORKLOADS["large"])
+    s = np.asarray(ws.s, np.int64)
+    k = np.asarray(ws.k, np.int32)
+    u = np.clip(np.round(14 - 7 * s / s.max()), 3, 15).astype(np.int32)
+    r = bench.plan_balance(s, k, u, u, 152)
+    assert r["sets"] == 9 and r["set_ctas"] == 152 and r["list"] == 0
+    assert 1.0 <= r["makespan_over_balanced"] < 1.12
+    late = u.copy()
+    w = int(np.argmax(s))
+    late[w] = 3 * u[w]
+    assert bench.plan_balance(s, k, u, late, 152)["makespan_over_balanced"] > \
+        r["makespan_over_balanced"]

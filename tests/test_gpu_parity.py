@@ -530,6 +530,26 @@ def test_round_tensor_core_lloyd(ctx, strategy):
         check_round(ctx, X, Xd, batch, strategy, 19, rnd)
 
 
+def test_round_tensor_core_lloyd_sets(ctx):
+    # 36 workers on the launch's CTAs: nine sets of four, each set running
+    # its workers one after another on all of its CTAs (every worker's
+    # barriers and sums over the set), the plan remade on the device before
+    # every launch from the previous round's updates
+    X = zipf_mixture(60000, 64, 200, 47)
+    Xd = dev(X)
+    rng = np.random.default_rng(48)
+    W = 36
+    s = rng.integers(2500, 6000, W).tolist()
+    k = [(60, 120, 200)[w % 3] for w in range(W)]
+    plan = H.lloyd_cta_plan(s, k, [0] * W, 152)
+    firsts = {int(t) for t in plan["cta_task"] if t >= 0}
+    assert len(firsts) == 9 and (plan["next"] >= 0).sum() == W - 9
+    batch = H.Batch(64, s, k, [0] * W)
+    assert ctx.lloyd_schedule(max(s), 64, 200)["form"] == "split_bf16"
+    for rnd in range(3):
+        check_round(ctx, X, Xd, batch, 0, 23, rnd)
+
+
 def test_round_hybrid_switches_phase(ctx):
     # Algorithm 5 with N1 = 2: two competitive rounds, then cooperative ones
     X = mixture(20000, 6, 8, 31, sd=1.1)
