@@ -919,18 +919,28 @@ def run_mine(args):
         arrived = [[torch.cuda.Event() for _ in range(nck)] for _ in range(nb)]
         freed = [torch.cuda.Event() for _ in range(nb)]
 
+        # per-step and per-copy device times and the clocks of the e2e steps
+        diag = {"copy": [], "step": []}
+
+        def timing_event(stream):
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            return ev
+
         def issue_copy(i):
             bi = i % nb
             if nb == 1:
                 copy_stream.wait_stream(main)           # X is free once the last step is done
             else:
                 copy_stream.wait_event(freed[bi])       # the last round on this buffer is done
+            c0 = timing_event(copy_stream)
             with torch.cuda.stream(copy_stream):
                 for c in range(nck):
                     a, b_ = c * rows, min(wl.n, (c + 1) * rows)
                     if a < b_:
                         bufs[bi][a:b_].copy_(X_host[a:b_], non_blocking=True)
                     arrived[bi][c].record(copy_stream)
+            diag["copy"].append((c0, timing_event(copy_stream)))
 
         def round_on(buf, r):
             if nb == 1:
@@ -955,6 +965,7 @@ def run_mine(args):
             cb = best_centroids()
             if timed:
                 e_best.append([kb for kb, _, _ in cb])
+                diag["step"].append(timing_event(main))
             f_chunks.zero_()
             for c in range(nck):
                 # the chunk's rows within this rank's block of the objective
@@ -978,11 +989,27 @@ def run_mine(args):
         # the recorded graph)
         e2e_steps(1, r0, False)
         torch.cuda.synchronize()
+        eclk = ClockSampler(local)
+        eclk.start()
+        te0 = time.perf_counter()
         e0.record()
         e2e_steps(E, r0 + 1, True)
         e1.record()
         torch.cuda.synchronize()
+        te1 = time.perf_counter()
+        eclk.stop()
         e_ms = e0.elapsed_time(e1)
+        try:
+            marks = diag["step"] + [e1]
+            step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(E)]
+            copy_ms = [a.elapsed_time(b) for a, b in diag["copy"][-E:]]
+            e_diag = {"step_ms": {"min": float(min(step_ms)),
+                                  "median": float(statistics.median(step_ms)),
+                                  "max": float(max(step_ms))},
+                      "copy_ms_median": float(statistics.median(copy_ms)),
+                      "clocks": eclk.summary(te0, te1)}
+        except Exception as exc:  # a diagnostic only
+            e_diag = {"error": str(exc)}
         ei = e_iters.cpu().numpy()
         e_dist = sum(dist_count(ei[i], ws.s[lw], ws.k[lw], rb - ra, e_best[i]) for i in range(E))
         e_ms, e_dist = job_totals(e_ms, e_dist, dev)
@@ -992,7 +1019,7 @@ def run_mine(args):
         # its own steps (later rounds than the timed ones: fewer Lloyd updates
         # as the incumbents improve, so the copy of X weighs more)
         e2e = {"value": e_value, "unit": UNIT, "device_buffers": nb, "steps": E,
-               "ms_per_step": e_ms / E, "lloyd_iters_mean": float(ei.mean()),
+               "ms_per_step": e_ms / E, "lloyd_iters_mean": float(ei.mean()), **e_diag,
                "h2d_bytes_per_step": int(X_host.numel() * 4),
                "d2h_bytes_per_step": int(res_host.numel() * 8 + C_host.numel() * 4 +
                                          (Wl * 8 if wl.W > 1 else 0))}
