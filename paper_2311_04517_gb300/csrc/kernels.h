@@ -65,7 +65,7 @@ struct LloydLaunch {
   int W;
   hpc_lloyd_task *tasks;       // host array [W]; block0 / nblocks written by the plan
   int *block_task_host;        // host [grid] (W > 1), written by the plan; the
-                               // tensor-core plan also uses [max_blocks, max_blocks + grid)
+                               // tensor-core plan also uses [max_blocks, 2 max_blocks)
   const hpc_lloyd_task *tasks_dev;  // device copy of tasks (W > 1), uploaded by the caller
   const int *block_task_dev;        // device copy of block_task_host (W > 1)
   int d, kmax;
