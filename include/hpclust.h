@@ -180,18 +180,23 @@ int hpc_lloyd_schedule(hpc_ctx *ctx, int64_t s, int32_t d, int32_t k, int32_t *o
  * computes before every launch of a round, from each worker's sample size
  * s[w], centroid count k[w] and updates in its previous run u[w] (host
  * arrays of W <= 128; negative u counts as 0, u above 1000 as 1000).  The
- * work of worker w is s k (u + 1).  The workers are dealt into
- * max(1, min(W, ctas / 16)) sets, largest first each to the set with the
- * least work so far (lowest index on ties); every set gets one CTA, then
- * the remaining CTAs go one at a time to the set with the most work per CTA
- * among those with fewer CTAs than the 128-row tiles of their smallest
- * sample; the sets take contiguous CTA ranges in set order.  A set runs its
- * workers one after another, each on all of its CTAs.
+ * work of worker w is s k (u + 1).  Workers with fewer than 16 128-row
+ * tiles go to the list, largest first, which keeps L = round(ctas x its
+ * share of the work) CTAs (at least 1, at most its length, at most
+ * ctas - 1 while other workers remain, all of them when none do).  The
+ * other workers are dealt into max(1, min(their number, (ctas - L) / 16))
+ * sets, largest first each to the set with the least work so far (lowest
+ * index on ties); every set gets one CTA, then the remaining ctas - L go
+ * one at a time to the set with the most work per CTA among those with
+ * fewer CTAs than the tiles of their smallest sample; the sets take
+ * contiguous CTA ranges from CTA 0 in set order.  A set runs its workers
+ * one after another, each on all of its CTAs.
  * Output (host): cta_task[ctas] the first worker of each CTA's set (-2: no
  * set; such a CTA takes workers from the list), list[W] the workers CTAs
- * take one at a time as they become free (its length returned through
- * *nlist; 0 with this plan), next[W] the worker a set runs after worker w
- * (-1 after its last), nblocks[W] each worker's CTAs (its set's).
+ * take one at a time as they become free, sets done or without one (its
+ * length returned through *nlist), next[W] the worker a set runs after
+ * worker w (-1 after its last, and for listed workers), nblocks[W] each
+ * worker's CTAs (its set's; 1 for listed workers).
  * Errors: HPC_ERR_ARG (W outside 1..128, ctas < 1, a NULL array, s < 1 or
  * k < 1). */
 int hpc_lloyd_cta_plan(int32_t W, const int64_t *s, const int32_t *k, const int32_t *u,

@@ -1441,17 +1441,21 @@ int tb_np(int k) { return k <= 128 ? 128 : k <= 256 ? 256 : 512; }
 // the set): the workers, largest first, go to the set with the least work
 // so far (TCL_SET_CTAS CTAs a set on average), then the CTAs to the sets,
 // one at a time to the set with the most work per CTA (at most as many as
-// the tiles of its smallest worker).  The work of a worker is s k (u + 1),
-// u its updates in its previous run (0 before the first).  (Simulated with
+// the tiles of its smallest worker).  Workers with fewer 128-row tiles than
+// TCL_SET_CTAS could not use a set's CTAs: they wait in a list, largest
+// first, and CTAs without a set, or done with theirs, take them one at a
+// time and run them alone; the list keeps CTAs in proportion to its work
+// (at least one, at most one per listed worker, all with no set).  The
+// work of a worker is s k (u + 1), u its updates in its previous run (0
+// before the first).  (Simulated with
 // update counts like the large workload's, predicted from the previous
 // round: 1.07-1.09 times the balanced time, against 1.7-1.8 for the groups
 // and list.)  Computed by one thread, on the host for the plan and on the
 // device before every launch (the previous run's updates are there).
 // Writes block_task[0, total) (each CTA's first worker, -2: none, it takes
 // from the list), next[0, W) (the worker its set runs after this one, -1
-// after the last), nb[] and b0[] per worker (its set's CTAs), and the list
-// follow[0, nf) of workers run alone by free CTAs (empty with this plan);
-// returns nf.
+// after the last), nb[] and b0[] per worker (its set's CTAs; 1 and -1 for
+// listed workers), and the list follow[0, nf); returns nf.
 constexpr int TCL_PACK_MAX = 128;  // workers of one launch (a round's chunk)
 constexpr int TCL_SET_CTAS = 16;   // CTAs of a set, on average
 
@@ -1461,9 +1465,123 @@ __host__ __device__ inline double tcl_work(int64_t s, int k, int u) {
   return (double)(s > 0 ? s : 1) * (double)k * (double)(uc + 1);
 }
 
+// One candidate plan: workers with fewer tiles than `tiny` in the list
+// (largest first), the others dealt into sets over the CTAs the list leaves;
+// returns its estimated makespan (a set: its work over its CTAs; the list:
+// each worker, largest first, to the CTA free first).
+struct TclCand {
+  int nsets, nf;
+  int64_t lc;
+  double sum[TCL_PACK_MAX];
+  int first[TCL_PACK_MAX], next[TCL_PACK_MAX], follow[TCL_PACK_MAX];
+  int64_t g[TCL_PACK_MAX];
+};
+
+__host__ __device__ double tcl_candidate(int W, const int *order, const double *work,
+                                         const int64_t *cap, int64_t total, int64_t tiny,
+                                         TclCand &c) {
+  int nsw = 0;
+  double lwork = 0.0, all = 0.0;
+  c.nf = 0;
+  for (int i = 0; i < W; ++i) {
+    const int w = order[i];
+    all += work[w];
+    c.next[w] = -1;
+    if (cap[w] < tiny) {
+      c.follow[c.nf++] = w;
+      lwork += work[w];
+    } else {
+      ++nsw;
+    }
+  }
+  c.lc = 0;
+  if (c.nf > 0) {
+    c.lc = (int64_t)floor((double)total * lwork / all + 0.5);
+    if (c.lc < 1) c.lc = 1;
+    if (c.lc > c.nf) c.lc = c.nf;
+    if (nsw == 0) c.lc = total;  // no sets: every CTA takes from the list
+    else if (c.lc > total - 1) c.lc = total - 1;
+  }
+  const int64_t tset = total - c.lc;  // the sets' CTAs
+  int64_t ns = tset / TCL_SET_CTAS;
+  if (ns < 1) ns = 1;
+  if (ns > nsw) ns = nsw;
+  c.nsets = (int)ns;  // 0 when every worker is listed
+  int last[TCL_PACK_MAX];
+  int64_t gmax[TCL_PACK_MAX];
+  for (int j = 0; j < c.nsets; ++j) {
+    c.sum[j] = 0.0;
+    c.first[j] = last[j] = -1;
+    gmax[j] = tset;
+  }
+  // the set workers, largest first, to the set with the least work (lowest
+  // index on ties), appended to its sequence
+  for (int i = 0; i < W; ++i) {
+    const int w = order[i];
+    if (cap[w] < tiny) continue;
+    int b = 0;
+    for (int j = 1; j < c.nsets; ++j)
+      if (c.sum[j] < c.sum[b]) b = j;
+    c.sum[b] += work[w];
+    if (last[b] >= 0) c.next[last[b]] = w;
+    else c.first[b] = w;
+    last[b] = w;
+    if (cap[w] < gmax[b]) gmax[b] = cap[w];
+  }
+  // CTAs: one each, then one at a time to the set with the most work per
+  // CTA that may take another
+  int64_t used = c.nsets;
+  for (int j = 0; j < c.nsets; ++j) c.g[j] = 1;
+  while (used < tset) {
+    int b = -1;
+    for (int j = 0; j < c.nsets; ++j)
+      if (c.g[j] < gmax[j] && (b < 0 || c.sum[j] / (double)c.g[j] > c.sum[b] / (double)c.g[b]))
+        b = j;
+    if (b < 0) break;
+    ++c.g[b];
+    ++used;
+  }
+  // the estimate: every CTA's time; the list onto the CTA free first
+  double t[TCL_PACK_MAX + 1];  // the sets' CTAs (one value a set), then one for the rest
+  int64_t cnt[TCL_PACK_MAX + 1];
+  int nt = 0;
+  double mk = 0.0;
+  for (int j = 0; j < c.nsets; ++j) {
+    t[nt] = c.sum[j] / (double)c.g[j];
+    cnt[nt++] = c.g[j];
+    mk = t[nt - 1] > mk ? t[nt - 1] : mk;
+  }
+  if (total > used) {
+    t[nt] = 0.0;
+    cnt[nt++] = total - used;
+  }
+  // CTAs of equal free time are interchangeable: take one from the group
+  // free first, it moves on by the worker's work
+  double extra[TCL_PACK_MAX];  // CTAs that took list workers: their free time
+  int ne = 0;
+  for (int i = 0; i < c.nf; ++i) {
+    int bt = -1, be = -1;
+    for (int q = 0; q < nt; ++q)
+      if (cnt[q] > 0 && (bt < 0 || t[q] < t[bt])) bt = q;
+    for (int q = 0; q < ne; ++q)
+      if (be < 0 || extra[q] < extra[be]) be = q;
+    const double w = work[c.follow[i]];
+    if (be >= 0 && (bt < 0 || extra[be] <= t[bt])) {
+      extra[be] += w;
+      mk = extra[be] > mk ? extra[be] : mk;
+    } else if (bt >= 0) {
+      --cnt[bt];
+      extra[ne] = t[bt] + w;
+      mk = extra[ne] > mk ? extra[ne] : mk;
+      ++ne;
+    }
+  }
+  return mk;
+}
+
 __host__ __device__ int tcl_pack_core(int W, const double *work, const int64_t *cap, int64_t total,
-                                      int *block_task, int *follow, int *next, int *nb, int *b0) {
-  (void)follow;
+                                      int *block_task, int *follow, int *next, int *nb, int *b0,
+                                      TclCand *cand) {
   int order[TCL_PACK_MAX];
   for (int w = 0; w < W; ++w) {  // largest first, lower index on ties (insertion)
     int i = w;
@@ -1473,58 +1591,31 @@ __host__ __device__ int tcl_pack_core(int W, const double *work, const int64_t *
     }
     order[i] = w;
   }
-  int64_t ns = total / TCL_SET_CTAS;
-  ns = ns < 1 ? 1 : ns > W ? W : ns;
-  const int nsets = (int)ns;
-  double sum[TCL_PACK_MAX];
-  int first[TCL_PACK_MAX], last[TCL_PACK_MAX];
-  int64_t g[TCL_PACK_MAX], gmax[TCL_PACK_MAX];
-  for (int j = 0; j < nsets; ++j) {
-    sum[j] = 0.0;
-    first[j] = last[j] = -1;
-    g[j] = 0;
-    gmax[j] = total;
+  // every worker in sets, or the workers too small to use a set's CTAs (on
+  // average) in the list: the plan with the smaller estimated makespan
+  // (cand: room for two candidates, the caller's)
+  const double ma = tcl_candidate(W, order, work, cap, total, 0, cand[0]);
+  bool tiny = false;
+  for (int w = 0; w < W; ++w) tiny = tiny || cap[w] < TCL_SET_CTAS;
+  const TclCand *c = &cand[0];
+  if (tiny && tcl_candidate(W, order, work, cap, total, TCL_SET_CTAS, cand[1]) < ma) c = &cand[1];
+  for (int w = 0; w < W; ++w) {
+    next[w] = c->next[w];
+    nb[w] = 1;
+    b0[w] = -1;  // listed workers run alone wherever they are taken
   }
-  // workers, largest first, to the set with the least work (lowest index on
-  // ties), appended to its sequence
-  for (int i = 0; i < W; ++i) {
-    const int w = order[i];
-    int b = 0;
-    for (int j = 1; j < nsets; ++j)
-      if (sum[j] < sum[b]) b = j;
-    sum[b] += work[w];
-    next[w] = -1;
-    if (last[b] >= 0) next[last[b]] = w;
-    else first[b] = w;
-    last[b] = w;
-    if (cap[w] < gmax[b]) gmax[b] = cap[w] > 0 ? cap[w] : 1;
-  }
-  // CTAs: one each, then one at a time to the set with the most work per
-  // CTA that may take another
-  int64_t used = 0;
-  for (int j = 0; j < nsets; ++j) {
-    g[j] = 1;
-    ++used;
-  }
-  while (used < total) {
-    int b = -1;
-    for (int j = 0; j < nsets; ++j)
-      if (g[j] < gmax[j] && (b < 0 || sum[j] / (double)g[j] > sum[b] / (double)g[b])) b = j;
-    if (b < 0) break;
-    ++g[b];
-    ++used;
-  }
+  for (int i = 0; i < c->nf; ++i) follow[i] = c->follow[i];
   int64_t grid = 0;
-  for (int j = 0; j < nsets; ++j) {
-    for (int64_t i = 0; i < g[j]; ++i) block_task[grid + i] = first[j];
-    for (int w = first[j]; w >= 0; w = next[w]) {
+  for (int j = 0; j < c->nsets; ++j) {
+    for (int64_t i = 0; i < c->g[j]; ++i) block_task[grid + i] = c->first[j];
+    for (int w = c->first[j]; w >= 0; w = c->next[w]) {
       b0[w] = (int)grid;
-      nb[w] = (int)g[j];
+      nb[w] = (int)c->g[j];
     }
-    grid += g[j];
+    grid += c->g[j];
   }
   for (; grid < total; ++grid) block_task[grid] = -2;
-  return 0;
+  return c->nf;
 }
 
 // The device side: the tasks' work from the previous round's updates, the
@@ -1534,10 +1625,12 @@ __host__ __device__ int tcl_pack_core(int W, const double *work, const int64_t *
 // tasks' sets).
 __global__ void tcl_repack_kernel(hpc_lloyd_task *tasks, int *block_task, int W, int64_t total,
                                   int64_t max_blocks, int64_t task_blocks) {
+  // one thread; its arrays in shared memory rather than its stack
+  __shared__ TclCand cand[2];
+  __shared__ double work[TCL_PACK_MAX];
+  __shared__ int64_t cap[TCL_PACK_MAX];
+  __shared__ int nb[TCL_PACK_MAX], b0[TCL_PACK_MAX];
   if (threadIdx.x != 0) return;
-  double work[TCL_PACK_MAX];
-  int64_t cap[TCL_PACK_MAX];
-  int nb[TCL_PACK_MAX], b0[TCL_PACK_MAX];
   for (int w = 0; w < W; ++w) {
     const int64_t sw = tasks[w].s > 0 ? tasks[w].s : 1;
     work[w] = tcl_work(sw, tasks[w].k, tasks[w].uprev ? *tasks[w].uprev : 0);
@@ -1545,7 +1638,7 @@ __global__ void tcl_repack_kernel(hpc_lloyd_task *tasks, int *block_task, int W,
     cap[w] = c < task_blocks ? c : task_blocks;
   }
   const int nf = tcl_pack_core(W, work, cap, total, block_task, block_task + max_blocks,
-                               block_task + max_blocks + TCL_PACK_MAX, nb, b0);
+                               block_task + max_blocks + TCL_PACK_MAX, nb, b0, cand);
   block_task[2 * max_blocks - 1] = nf;
   for (int w = 0; w < W; ++w) {
     tasks[w].block0 = b0[w];
@@ -1562,8 +1655,9 @@ void tcl_pack(LloydLaunch &h, int64_t total) {
     work[w] = tcl_work(sw, h.tasks[w].k, 0);
     cap[w] = std::min<int64_t>((sw + TB_M - 1) / TB_M, h.task_blocks);
   }
+  std::vector<TclCand> cand(2);
   h.nfollow = tcl_pack_core(h.W, work, cap, total, h.block_task_host, h.block_task_host + h.max_blocks,
-                            h.block_task_host + h.max_blocks + TCL_PACK_MAX, nb, b0);
+                            h.block_task_host + h.max_blocks + TCL_PACK_MAX, nb, b0, cand.data());
   h.block_task_host[2 * h.max_blocks - 1] = h.nfollow;
   for (int w = 0; w < h.W; ++w) {
     h.tasks[w].block0 = b0[w];
@@ -1713,7 +1807,8 @@ int hpc_tcl_cta_plan(int W, const int64_t *s, const int32_t *k, const int32_t *u
     work[w] = tcl_work(s[w], k[w], u ? u[w] : 0);
     cap[w] = (s[w] + TB_M - 1) / TB_M;
   }
-  *nlist = tcl_pack_core(W, work, cap, ctas, cta_task, list, next, nblocks, b0);
+  std::vector<TclCand> cand(2);
+  *nlist = tcl_pack_core(W, work, cap, ctas, cta_task, list, next, nblocks, b0, cand.data());
   return HPC_OK;
 }
 

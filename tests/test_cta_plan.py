@@ -1,10 +1,12 @@
 """Host logic of the batched split-BF16 Lloyd launch's CTA plan
 (hpc_lloyd_cta_plan, the same code the launch's one-thread planner runs on
-the device before every launch): the workers are dealt, largest first, to
-the set with the least work; every set gets a contiguous range of CTAs, one
-each and then one at a time to the set with the most work per CTA (at most
-its smallest worker's tiles); a set runs its workers one after another
-through the next links; every worker runs exactly once."""
+the device before every launch): workers of fewer than 16 tiles wait in a
+largest-first list that keeps CTAs in proportion to its work; the others
+are dealt, largest first, to the set with the least work; every set gets a
+contiguous range of CTAs, one each and then one at a time to the set with
+the most work per CTA (at most its smallest worker's tiles); a set runs its
+workers one after another through the next links; every worker runs
+exactly once."""
 import numpy as np
 import pytest
 
@@ -19,20 +21,29 @@ def work_of(s, k, u):
     return np.maximum(np.asarray(s, np.float64), 1) * np.asarray(k, np.float64) * (uc + 1)
 
 
-def expected_sets(work, tiles, ctas):
-    """The plan restated: greedy deal, then greedy CTAs."""
+def candidate(work, tiles, ctas, tiny):
+    """One candidate plan restated: workers of fewer than `tiny` tiles in the
+    list, the greedy deal of the others, greedy CTAs; and its estimate."""
     W = len(work)
     order = sorted(range(W), key=lambda w: (-work[w], w))
-    ns = max(1, min(W, ctas // SET_CTAS))
+    listed = [w for w in order if tiles[w] < tiny]
+    rest = [w for w in order if tiles[w] >= tiny]
+    lc = 0
+    if listed:
+        lc = int(np.floor(ctas * sum(work[w] for w in listed) / sum(work) + 0.5))
+        lc = min(max(lc, 1), len(listed))
+        lc = ctas if not rest else min(lc, ctas - 1)
+    tset = ctas - lc
+    ns = min(max(1, tset // SET_CTAS), len(rest))
     sums, members = [0.0] * ns, [[] for _ in range(ns)]
-    for w in order:
+    for w in rest:
         b = min(range(ns), key=lambda j: (sums[j], j))
         sums[b] += work[w]
         members[b].append(w)
-    gmax = [max(1, min(min(tiles[w] for w in m), ctas)) for m in members]
+    gmax = [min(min(tiles[w] for w in m), tset) for m in members]
     g = [1] * ns
     used = ns
-    while used < ctas:
+    while used < tset:
         cand = [j for j in range(ns) if g[j] < gmax[j]]
         if not cand:
             break
@@ -42,7 +53,25 @@ def expected_sets(work, tiles, ctas):
                 b = j
         g[b] += 1
         used += 1
-    return members, g
+    # the estimate: sets' times, the list to the CTA free first
+    free = [sums[j] / g[j] for j in range(ns) for _ in range(g[j])] + [0.0] * (ctas - used)
+    mk = max([sums[j] / g[j] for j in range(ns)] + [0.0])
+    for w in listed:
+        i = int(np.argmin(free))
+        free[i] += work[w]
+        mk = max(mk, free[i])
+    return members, g, listed, mk
+
+
+def expected_sets(work, tiles, ctas):
+    """The plan restated: all in sets, or the small workers in the list,
+    whichever has the smaller estimate."""
+    a = candidate(work, tiles, ctas, 0)
+    if any(t < SET_CTAS for t in tiles):
+        b = candidate(work, tiles, ctas, SET_CTAS)
+        if b[3] < a[3]:
+            return b[:3]
+    return a[:3]
 
 
 def check_plan(s, k, u, ctas):
@@ -52,8 +81,9 @@ def check_plan(s, k, u, ctas):
     work = work_of(s, k, u)
     tiles = [-(-int(x) // 128) for x in s]
     assert len(ct) == ctas and ((ct >= 0) | (ct == -2)).all()
-    assert len(lst) == 0
-    members, g = expected_sets(work, tiles, ctas)
+    members, g, listed = expected_sets(work, tiles, ctas)
+    assert lst.tolist() == listed, "the list: the workers of fewer tiles, largest first"
+    assert all(tiles[w] < SET_CTAS for w in listed)
     runs = np.zeros(W, np.int64)
     c = 0
     for m, gj in zip(members, g):
@@ -70,6 +100,11 @@ def check_plan(s, k, u, ctas):
             runs[w] += 1
         c += gj
     assert (ct[c:] == -2).all()
+    if listed:
+        assert (ct == -2).sum() >= 1, "the list keeps a CTA"
+    for w in listed:
+        assert nb[w] == 1 and nxt[w] == -1 and not (ct == w).any()
+        runs[w] += 1
     assert (runs == 1).all(), "every worker exactly once"
     return p
 
@@ -90,7 +125,7 @@ def test_large_workload_plan_is_near_balanced():
 
 
 @pytest.mark.parametrize("W,ctas", [(1, 152), (2, 3), (128, 152), (128, 40), (64, 304), (5, 5),
-                                    (128, 1216)])
+                                    (128, 1216), (1, 1), (40, 152)])
 def test_plan_shapes(W, ctas):
     rng = np.random.default_rng(W * 1000 + ctas)
     s = rng.integers(1, 2_000_000, W)
@@ -107,11 +142,26 @@ def test_one_worker_takes_every_cta_it_can_use():
 
 
 def test_small_samples_cap_their_set():
-    # a set is held to its smallest worker's tiles; the CTAs left over go to
-    # the other sets
-    s = [100_000] * 16 + [640]        # the last worker has five tiles
-    p = check_plan(s, [100] * 17, [5] * 17, 32)
-    assert p["nblocks"][16] <= 5
+    # a set is held to its smallest worker's tiles (here 20); the CTAs left
+    # over go to the other sets
+    s = [100_000] * 16 + [2560]
+    p = check_plan(s, [100] * 17, [5] * 17, 64)
+    assert p["nblocks"][16] <= 20 and len(p["list"]) == 0
+
+
+def test_tiny_samples_wait_in_the_list():
+    # beside large workers, workers of fewer than 16 tiles would hold their
+    # sets to eight CTAs: they run alone from the list, which keeps CTAs in
+    # proportion to its work, and the sets keep the rest
+    s = [200_000] * 30 + [1000] * 10   # eight tiles each
+    p = check_plan(s, [100] * 40, [5] * 40, 152)
+    assert sorted(p["list"].tolist()) == list(range(30, 40))
+    assert (p["cta_task"] == -2).sum() >= 1
+    # only small workers: sets of up to eight CTAs each beat one CTA each
+    p = check_plan([1000] * 50, [100] * 50, [5] * 50, 152)
+    assert len(p["list"]) == 0 and p["nblocks"].max() == 8
+    # the list where it is better: many small workers, a few CTAs
+    p = check_plan([1000] * 50, [100] * 50, [5] * 50, 40)
 
 
 def test_bad_arguments():
