@@ -202,3 +202,17 @@ def test_plan_balance_sees_a_wrong_prediction():
     late[w] = 3 * u[w]
     assert bench.plan_balance(s, k, u, late, 152)["makespan_over_balanced"] > \
         r["makespan_over_balanced"]
+
+
+def test_plan_balance_with_a_list():
+    # sets and a list: the listed workers go to the CTAs free first, so the
+    # makespan is at least the largest listed worker and the sets' times
+    import bench
+    s = np.array([200_000] * 30 + [1000] * 10, np.int64)
+    k = np.full(40, 100, np.int32)
+    u = np.full(40, 5, np.int32)
+    r = bench.plan_balance(s, k, u, u, 152)
+    assert r["list"] == 10 and r["sets"] >= 1
+    work = s * 100.0 * 6
+    assert r["makespan_over_balanced"] * work.sum() / 152 >= work[30:].max() - 1e-6
+    assert 1.0 <= r["makespan_over_balanced"] < 1.5
